@@ -1,0 +1,397 @@
+"""Benchmark: adjoint (reverse-mode) energy gradients per second on the n=30, P=600
+workload (10 layers of RY/RZ + CZ brickwork, 200 random Pauli strings), complex64
+amplitudes with FP64 reductions, one gradient = one step of the whole hot path
+(forward sweep, H|psi> with fused energy, fused reverse sweep with per-parameter
+reductions).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--dtype c64|c128]
+
+Prints one JSON line (rank 0).  N > 1 runs independent replicas (one circuit per
+GPU, no collective on the data path) and reports the aggregate rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "adjoint gradients/s at n=30,P=600"
+UNIT = "gradients/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload(args):
+    from paper_2009_02823_gb300 import workloads as W
+    w = W.config(args.cfg, n=args.n, layers=args.layers)
+    return w
+
+
+def _config(args, w, extra=None):
+    cfg = {"workload": w.name, "n_qubits": w.n, "n_params": w.n_params, "n_gates": w.n_gates,
+           "hamiltonian_terms": len(w.terms), "amplitudes": f"{args.dtype} (FP64 reductions)",
+           "state_bytes": (8 if args.dtype == "c64" else 16) << w.n,
+           "l2": "inputs larger than L2 (state vectors >> 129 MB)",
+           "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                    power.append(float(f[3]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+def family_bytes(fam: str, w, S: int, plan: dict) -> float | None:
+    """Algorithmic bytes per launch of a kernel family (one state traversal = S bytes
+    read or written; Algorithm 1's cost unit, one gate primitive = O(2^n))."""
+    if fam == "adj_gate":    # read phi, lambda; write phi, lambda
+        return 4.0 * S
+    if fam == "fwd_gate":    # read + write psi (CNOT/CZ touch part of it; counted whole)
+        return 2.0 * S
+    if fam == "adj_fused":   # per reverse tile pass: read + write phi and lambda
+        return 4.0 * S
+    if fam == "fwd_fused":   # per forward tile pass: read + write psi
+        return 2.0 * S
+    if fam == "ham_group":   # read psi, read + write lambda
+        return 3.0 * S
+    if fam == "ham_diag":    # read psi, write lambda
+        return 2.0 * S
+    if fam == "ham_fused":
+        return 3.0 * S
+    return None
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2009_02823_gb300 import Circuit
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = _workload(args)
+    S = (8 if args.dtype == "c64" else 16) << w.n
+    stream = torch.cuda.current_stream()
+    circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream)
+    circ.set_hamiltonian(w.terms)
+    theta_h = np.ascontiguousarray(w.theta + 1e-3 * rank)
+    theta_d = torch.tensor(theta_h, dtype=torch.float64, device="cuda")
+    e_d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g_d = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
+
+    def step():
+        circ.energy_and_gradient_device(theta_d.data_ptr(), e_d.data_ptr(), g_d.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(dev)
+    circ.set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    dev_ms = t0.elapsed_time(t1)
+    stats = circ.kernel_stats()
+    circ.set_profiling(False)
+    ms_max = dev_ms
+    if dist:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the public host call: H2D theta, D2H energy + gradient per step
+    e2e_steps = max(2, min(args.steps, 3))
+    grad_h = np.zeros(w.n_params)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e_val, _g = circ.energy_and_gradient(theta_h, out=grad_h)
+    t_e = time.perf_counter() - t_e0
+    if dist:
+        t = torch.tensor([t_e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e = float(t.item())
+    e2e = {"value": world * e2e_steps / t_e, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * w.n_params, "d2h_bytes_per_step": 8 * (w.n_params + 1)}
+
+    # roofline of the dominant kernel family
+    plan = circ.plan()
+    peak, peak_kind = _peaks()
+    fam, (launches, tot_ms) = max(stats.items(), key=lambda kv: kv[1][1])
+    per = family_bytes(fam, w, S, plan)
+    roof = None
+    if per is not None and launches:
+        avg_s = tot_ms / launches / 1e3
+        ach = per / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": fam, "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
+                "traffic": None, "bytes_per_launch": per, "launches": launches,
+                "avg_launch_ms": round(tot_ms / launches, 4),
+                "share_of_step": round(tot_ms / max(sum(v[1] for v in stats.values()), 1e-9), 4)}
+    gpu_launches = int(sum(v[0] for v in stats.values()))
+
+    extra = {}
+    if rank == 0 and not args.no_ps:
+        extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline_sample(args, w, budget_s=args.cpu_budget)
+    else:
+        cpu = None
+    circ.close()
+    if rank != 0:
+        return None
+    line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+            "data": "synthetic (seeded; no dataset)", "config": _config(args, w, {"plan": plan}),
+            "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
+            "kernel_families_ms": {k: [v[0], round(v[1], 3)] for k, v in stats.items()},
+            "energy": e_val}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    line.update(extra)
+    return line
+
+
+def param_shift_baseline(args, circ, w, theta_h, adjoint_rate):
+    """GPU parameter-shift gradient (2 energy evaluations per parameter occurrence)
+    timed on a prefix of occurrences and extrapolated linearly: every shifted
+    evaluation is the same work (a full forward sweep plus <H>)."""
+    want = args.ps_evals // 2
+    occ, last = 0, 0
+    npar = {"RX": 1, "RY": 1, "RZ": 1, "U3": 3}
+    for i, g in enumerate(w.gates):
+        occ += npar.get(g[0], 0)
+        last = i + 1
+        if occ >= want:
+            break
+    total_occ = sum(npar.get(g[0], 0) for g in w.gates)
+    circ.gradient_parameter_shift(theta_h, 0, 1)  # warm
+    t0 = time.perf_counter()
+    circ.gradient_parameter_shift(theta_h, 0, last)
+    dt = time.perf_counter() - t0
+    per_eval = dt / (2 * occ)
+    full = per_eval * 2 * total_occ
+    return {"evals_timed": 2 * occ, "s_per_energy_eval": round(per_eval, 5),
+            "s_per_gradient_extrapolated": round(full, 3),
+            "gradients_per_s": 1.0 / full,
+            "adjoint_speedup": round(adjoint_rate * full, 2), "target_speedup": w.n_params / 4}
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def cpu_baseline_sample(args, w, budget_s=20.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same
+    workload: its Algorithm-1 primitives (apply gate, apply adjoint gate, derivative
+    matrix + clone + inner product, one Hamiltonian term) are timed at the workload's
+    n on the workload's own gates/terms, and the full Algorithm-1 gradient time is
+    extrapolated from the per-primitive times and the workload's gate and term counts."""
+    import ctypes
+
+    import oracle
+    L = oracle._load()
+    n = w.n
+    dim = 1 << n
+    t_start = time.perf_counter()
+    try:
+        psi = np.zeros(dim, dtype=np.complex128)
+        lam = np.zeros(dim, dtype=np.complex128)
+    except MemoryError:
+        return {"value": None, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                "sample": "host memory too small for the workload's state vectors"}
+    psi[0] = 1.0
+    lam[:] = psi
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    gt = oracle.gate_table(w.gates)
+    th = np.ascontiguousarray(w.theta)
+    coef, let = oracle.letter_table(w.terms, n)
+    kinds = {}
+    for i, g in enumerate(w.gates):
+        kinds.setdefault(g[0], i)
+    per = {}
+    # forward + adjoint application per kind (one launch each; the work is data-independent)
+    for kind, i in kinds.items():
+        t0 = time.perf_counter()
+        L.oracle_apply_gate(n, ptr(psi), ptr(gt[i]), ptr(th), 0)
+        t1 = time.perf_counter()
+        L.oracle_apply_gate(n, ptr(psi), ptr(gt[i]), ptr(th), 1)
+        t2 = time.perf_counter()
+        per[kind] = (t1 - t0, t2 - t1)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    # derivative step: clone + apply dU + inner product (Algorithm 1, lines 7-9)
+    t0 = time.perf_counter()
+    mu = psi.copy()
+    d = oracle.gate_derivative("RY", 0, [0.3])
+    L.oracle_apply_matrix_1q(n, ptr(mu), 0, ptr(np.ascontiguousarray(d.reshape(4))))
+    out = np.zeros(2)
+    L.oracle_inner_parts(n, ptr(lam), ptr(mu), ptr(out))
+    t_deriv = time.perf_counter() - t0
+    del mu
+    # Hamiltonian: time a few terms, scale by the term count
+    k_terms = max(1, min(3, len(w.terms)))
+    t0 = time.perf_counter()
+    L.oracle_apply_hamiltonian(n, k_terms, ptr(coef), ptr(let), ptr(psi), ptr(lam))
+    t_h = (time.perf_counter() - t0) / k_terms * len(w.terms)
+    # Algorithm 1 gradient: G forward + H + per gate (U^dag phi, U^dag lambda) + per slot deriv
+    total = t_h
+    n_slots = 0
+    for g in w.gates:
+        f, a = per.get(g[0], per.get("RY", (0.0, 0.0)))
+        total += f + 2 * a
+        n_slots += {"RX": 1, "RY": 1, "RZ": 1, "U3": 3}.get(g[0], 0)
+    total += n_slots * t_deriv
+    sample_s = time.perf_counter() - t_start
+    return {"value": 1.0 / total, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"oracle primitives at n={n} (complex128): one forward and one adjoint "
+                       f"application per gate kind {sorted(per)}, one derivative+clone+inner "
+                       f"product, {k_terms} of {len(w.terms)} Hamiltonian terms; Algorithm 1 "
+                       f"time extrapolated over {w.n_gates} gates / {n_slots} parameter slots "
+                       f"= {total:.1f} s per gradient; sample took {sample_s:.1f} s"),
+            "extrapolated_s_per_gradient": round(total, 2)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    import oracle
+    w = _workload(args)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline_sample(args, w, budget_s=args.cpu_budget)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_sample(args, w, budget_s=args.cpu_budget)
+        if last["value"]:
+            vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals) if vals else None
+    cpu = dict(last or {})
+    cpu["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / max(args.steps, 1), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic (seeded; no dataset)", "config": _config(args, w),
+            "cpu_baseline": cpu, "cores": oracle.threads(),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--cfg", type=int, default=3)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--layers", type=int, default=None)
+    ap.add_argument("--no-ps", action="store_true", help="skip the GPU parameter-shift baseline")
+    ap.add_argument("--ps-evals", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as tdist
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            tdist.init_process_group("nccl")
+            dist = tdist
+        line = run_ours(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * vqg.h -- C ABI of the GB300 (sm_103a) reverse-mode gradient library.
+ *
+ * The library evaluates, for a variational circuit U(theta) = U_G ... U_1 acting on
+ * |in> = |0...0> and a Pauli-sum Hamiltonian H,
+ *     E(theta) = <psi|H|psi>,  |psi> = U(theta)|in>            (Sec. 2.2, problem statement)
+ * and the full gradient dE/dtheta in O(G) gate passes by the "reverse mode" recurrence
+ *     phi_i = U_i^dag phi_{i+1},  lambda_i = U_{i+1}^dag lambda_{i+1},
+ *     dE/dtheta_i = 2 Re <lambda_i| dU_i/dtheta_i |phi_i>       (Sec. 2.2, Eq. recurrent_grad;
+ *                                                               Algorithm 1)
+ * with multi-parameter gates handled per App. B.1 (Algorithm 3) and repeated
+ * parameters by the chain-rule sum of App. B.2 (Algorithm 4): each gate names the
+ * parameter index of each of its slots, and gradient entries of all occurrences of
+ * one index are added.
+ *
+ * Conventions: qubit q is bit q of the amplitude index.  State vectors are 2^n
+ * complex amplitudes, interleaved (re, im), complex64 (8 B) or complex128 (16 B).
+ *   RX/RY/RZ(t) = exp(-i t sigma / 2)    (App. A's exp(alpha i t sigma) with alpha = -1/2)
+ *   U3(t, f, l) = [[cos t/2, -e^{il} sin t/2], [e^{if} sin t/2, e^{i(f+l)} cos t/2]],
+ *                 parameter slots (t, f, l) in that order
+ *   CNOT(q0 -> q1): flips q1 where q0 = 1.   CZ(q0, q1): -1 where both are 1.
+ *   Pauli term (x_mask, z_mask, coef): coef * i^{popcount(x & z)} X^x Z^z, i.e. the
+ *   tensor product with X where only the x bit is set, Z where only the z bit is set,
+ *   Y where both are set.
+ *
+ * Ownership: the library copies gates and Hamiltonian terms at create / set time and
+ * owns all device buffers of a circuit (state vectors, checkpoints, reduction
+ * scratch).  theta / energy / grad buffers are the caller's, read or written only
+ * during the call.  Calls on one circuit are not thread-safe; different circuits
+ * may be used from different threads.
+ *
+ * Errors: every entry point returns VQG_OK (0) or a negative vqg_status; nothing
+ * throws across the ABI.  vqg_last_error() gives a thread-local message for the
+ * last failing call on this thread.
+ */
+#ifndef VQG_H
+#define VQG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vqg_status {
+    VQG_OK = 0,
+    VQG_ERR_INVALID = -1,     /* bad argument: qubit >= n, q0 == q1, param index out of range,
+                                 mask bit >= n, n out of range, null pointer, ...          */
+    VQG_ERR_OOM = -2,         /* device memory allocation failed                           */
+    VQG_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed               */
+    VQG_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up (status word set)      */
+    VQG_ERR_UNSUPPORTED = -5, /* valid request this build does not implement               */
+    VQG_ERR_STATE = -6        /* call order problem, e.g. energy before set_hamiltonian    */
+} vqg_status;
+
+typedef enum vqg_gate_kind {
+    VQG_RX = 0, VQG_RY = 1, VQG_RZ = 2, VQG_U3 = 3, VQG_CNOT = 4, VQG_CZ = 5
+} vqg_gate_kind;
+
+typedef enum vqg_dtype {
+    VQG_C64 = 0,  /* complex64 amplitudes; FP64 reductions (energy, inner products) */
+    VQG_C128 = 1  /* complex128 amplitudes and arithmetic                            */
+} vqg_dtype;
+
+/* One gate.  q1 = -1 for one-qubit gates.  param[j] is the parameter index of slot j
+ * (RX/RY/RZ use slot 0, U3 slots 0..2); unused slots are ignored (use -1). */
+typedef struct vqg_gate {
+    int32_t kind;
+    int32_t q0;
+    int32_t q1;
+    int32_t param[3];
+} vqg_gate;
+
+/* Execution options (vqg_default_options fills the defaults). */
+typedef struct vqg_options {
+    int32_t fusion;              /* 1: apply runs of gates per tile pass (default);
+                                    0: one kernel per gate                                  */
+    int32_t checkpoint_interval; /* forward states stored every this many gates and used to
+                                    restart phi in the reverse sweep; 0 = automatic (64 for
+                                    complex64, none for complex128), -1 = none              */
+    int32_t tile_qubits;         /* qubits per fused tile; 0 = autotuned                     */
+    int32_t use_graph;           /* 1: replay the launch sequence from a CUDA graph          */
+    int32_t max_checkpoint_mib;  /* cap on checkpoint memory; 0 = fit in free memory         */
+    int32_t reserved[11];
+} vqg_options;
+
+typedef struct vqg_circuit vqg_circuit;
+
+void vqg_default_options(vqg_options *opt);
+
+/* Create a circuit of n_qubits (1..34) over gates[0..n_gates) with n_params parameters.
+ * dtype is a vqg_dtype.  opt may be NULL (defaults).  Device buffers for two state
+ * vectors (and checkpoints) are allocated here on the current CUDA device.
+ * Errors: VQG_ERR_INVALID for malformed gates, VQG_ERR_OOM when buffers do not fit. */
+int vqg_circuit_create(int n_qubits, const vqg_gate *gates, int n_gates, int n_params,
+                       int dtype, const vqg_options *opt, vqg_circuit **out);
+
+int vqg_circuit_destroy(vqg_circuit *c);
+
+/* Set (replace) the Hamiltonian: sum_t coef[t] * i^{popcount(x&z)} X^{x_mask[t]} Z^{z_mask[t]}.
+ * Any representation is allowed by the method (Sec. 2.1, Algorithm 1 input); this one
+ * groups terms by x_mask so that one pass over amplitude pairs (j, j^x) applies every
+ * term of a group.  coef real (Hermitian H).  May be called between evaluations. */
+int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *x_mask,
+                        const uint64_t *z_mask, const double *coef);
+
+/* All work of this circuit is issued on `stream` (a cudaStream_t; NULL = the library's
+ * own stream).  The caller keeps the stream alive while the circuit uses it. */
+int vqg_set_stream(vqg_circuit *c, void *stream);
+
+/* E(theta): forward sweep (Algorithm 1, line 2) then <psi|H|psi> with FP64 reduction.
+ * theta: host array of n_params doubles.  energy: host double.  Blocks until done. */
+int vqg_energy(vqg_circuit *c, const double *theta, double *energy);
+
+/* E(theta) and dE/dtheta (Algorithm 1 with App. B.1/B.2): forward sweep, lambda = H psi
+ * with E fused, then the fused reverse sweep.  theta: host, n_params doubles; energy:
+ * host double; grad: host, n_params doubles (overwritten).  Blocks until done. */
+int vqg_energy_and_gradient(vqg_circuit *c, const double *theta, double *energy, double *grad);
+
+/* Same as above with device pointers (theta_dev: n_params doubles; energy_dev: 1 double;
+ * grad_dev: n_params doubles).  Issued on the circuit's stream; does not synchronise. */
+int vqg_energy_device(vqg_circuit *c, const double *theta_dev, double *energy_dev);
+int vqg_energy_and_gradient_device(vqg_circuit *c, const double *theta_dev, double *energy_dev,
+                                   double *grad_dev);
+
+/* Faithful O(G^2) baseline on the GPU: per-occurrence parameter shift,
+ * g_p += [E(theta_o + pi/2) - E(theta_o - pi/2)] / 2 over every parameter slot o of
+ * gate occurrences [first_gate, last_gate) (last_gate < 0: all), each evaluation a
+ * full forward sweep plus expectation (Sec. 1, Sec. 3).  grad: host, n_params doubles,
+ * overwritten (entries of parameters outside the range are 0).  Blocks until done. */
+int vqg_gradient_parameter_shift(vqg_circuit *c, const double *theta, int first_gate,
+                                 int last_gate, double *grad);
+
+/* Copy |psi> of the last forward sweep (complex64 or complex128 per dtype) into host
+ * memory `out` of `bytes` >= 2^n * amplitude size.  Blocks until done. */
+int vqg_get_state(vqg_circuit *c, void *out, size_t bytes);
+
+/* Timing of the kernels of the last call, for measurement: fills up to max_entries
+ * (name_id, launches, total_ms) rows per kernel family; returns the row count.  Only
+ * populated when the circuit was created with profiling enabled via
+ * vqg_set_profiling(c, 1).  Names are returned by vqg_kernel_family_name(). */
+int vqg_set_profiling(vqg_circuit *c, int enable);
+int vqg_kernel_stats(vqg_circuit *c, int max_entries, int *name_id, int *launches,
+                     double *total_ms);
+const char *vqg_kernel_family_name(int name_id);
+
+/* Per-call details of the schedule: number of forward passes, reverse passes,
+ * Hamiltonian passes, kernel launches per energy_and_gradient, checkpoints. */
+typedef struct vqg_plan_info {
+    int32_t forward_passes;
+    int32_t hamiltonian_passes;
+    int32_t reverse_passes;
+    int32_t launches_per_gradient;
+    int32_t checkpoints;
+    int32_t tile_qubits;
+    int32_t hamiltonian_groups;
+    int32_t reserved[9];
+} vqg_plan_info;
+int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
+
+const char *vqg_last_error(void);
+const char *vqg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VQG_H */

@@ -1,0 +1,256 @@
+"""Thin ctypes binding over the C ABI in include/vqg.h (argument marshalling only;
+every step of the computation runs in libvqg.so's CUDA kernels).
+
+There is no CPU fallback: if libvqg.so cannot be built or loaded, or no CUDA device
+is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+VQG_OK = 0
+STATUS = {0: "VQG_OK", -1: "VQG_ERR_INVALID", -2: "VQG_ERR_OOM", -3: "VQG_ERR_CUDA",
+          -4: "VQG_ERR_TIMEOUT", -5: "VQG_ERR_UNSUPPORTED", -6: "VQG_ERR_STATE"}
+KIND = {"RX": 0, "RY": 1, "RZ": 2, "U3": 3, "CNOT": 4, "CZ": 5}
+DTYPE = {"c64": 0, "complex64": 0, "c128": 1, "complex128": 1}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "vqg.h")
+
+
+class VqgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vqg_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("param", ctypes.c_int32 * 3)]
+
+
+class vqg_options(ctypes.Structure):
+    _fields_ = [("fusion", ctypes.c_int32), ("checkpoint_interval", ctypes.c_int32),
+                ("tile_qubits", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("max_checkpoint_mib", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+
+
+class vqg_plan_info(ctypes.Structure):
+    _fields_ = [("forward_passes", ctypes.c_int32), ("hamiltonian_passes", ctypes.c_int32),
+                ("reverse_passes", ctypes.c_int32), ("launches_per_gradient", ctypes.c_int32),
+                ("checkpoints", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
+                ("hamiltonian_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/vqg.h declares (for export checks)."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vqg_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libvqg.so (building it in-tree with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        p, i, d, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sigs = {
+            "vqg_default_options": (None, [p]),
+            "vqg_circuit_create": (i, [i, p, i, i, i, p, pp]),
+            "vqg_circuit_destroy": (i, [p]),
+            "vqg_set_hamiltonian": (i, [p, i, p, p, p]),
+            "vqg_set_stream": (i, [p, p]),
+            "vqg_energy": (i, [p, p, p]),
+            "vqg_energy_and_gradient": (i, [p, p, p, p]),
+            "vqg_energy_device": (i, [p, p, p]),
+            "vqg_energy_and_gradient_device": (i, [p, p, p, p]),
+            "vqg_gradient_parameter_shift": (i, [p, p, i, i, p]),
+            "vqg_get_state": (i, [p, p, ctypes.c_size_t]),
+            "vqg_set_profiling": (i, [p, i]),
+            "vqg_kernel_stats": (i, [p, i, p, p, p]),
+            "vqg_kernel_family_name": (ctypes.c_char_p, [i]),
+            "vqg_plan": (i, [p, p]),
+            "vqg_last_error": (ctypes.c_char_p, []),
+            "vqg_status_string": (ctypes.c_char_p, [i]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _ = (d, u64)
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != VQG_OK:
+        raise VqgError(status, lib().vqg_last_error().decode())
+
+
+def gate_array(gates) -> ctypes.Array:
+    arr = (vqg_gate * max(len(gates), 1))()
+    for k, (kind, q0, q1, ps) in enumerate(gates):
+        arr[k].kind = KIND[kind] if isinstance(kind, str) else int(kind)
+        arr[k].q0 = q0
+        arr[k].q1 = q1
+        for j in range(3):
+            arr[k].param[j] = ps[j]
+    return arr
+
+
+def pauli_masks(terms, n: int):
+    """Neutral Pauli terms -> (x_mask, z_mask, coef): X sets x, Z sets z, Y sets both."""
+    x = np.zeros(len(terms), dtype=np.uint64)
+    z = np.zeros(len(terms), dtype=np.uint64)
+    c = np.zeros(len(terms), dtype=np.float64)
+    for t, (coef, ops) in enumerate(terms):
+        xm = zm = 0
+        for q, l in ops:
+            if not 0 <= q < 64:
+                raise ValueError(f"qubit {q}")
+            b = 1 << q
+            if l in ("X", "Y"):
+                xm |= b
+            if l in ("Z", "Y"):
+                zm |= b
+        x[t], z[t], c[t] = xm, zm, coef
+    return x, z, c
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Circuit:
+    """One variational circuit on the current CUDA device (wraps vqg_circuit)."""
+
+    def __init__(self, n: int, gates, n_params: int, dtype: str = "c64", *, fusion: bool = True,
+                 checkpoint_interval: int = 0, tile_qubits: int = 0, use_graph: bool = False,
+                 max_checkpoint_mib: int = 0, stream=None):
+        L = lib()
+        self.n, self.n_params, self.n_gates = n, n_params, len(gates)
+        self.dtype = dtype
+        opt = vqg_options()
+        L.vqg_default_options(ctypes.byref(opt))
+        opt.fusion = int(fusion)
+        opt.checkpoint_interval = checkpoint_interval
+        opt.tile_qubits = tile_qubits
+        opt.use_graph = int(use_graph)
+        opt.max_checkpoint_mib = max_checkpoint_mib
+        self._gates = gate_array(gates)
+        h = ctypes.c_void_p()
+        _check(L.vqg_circuit_create(n, self._gates, len(gates), n_params, DTYPE[dtype],
+                                    ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vqg_circuit_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(lib().vqg_set_stream(self._h, ctypes.c_void_p(raw or None)))
+
+    def set_hamiltonian(self, terms):
+        x, z, c = pauli_masks(terms, self.n)
+        self.set_hamiltonian_masks(x, z, c)
+
+    def set_hamiltonian_masks(self, x, z, coef):
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        z = np.ascontiguousarray(z, dtype=np.uint64)
+        c = np.ascontiguousarray(coef, dtype=np.float64)
+        _check(lib().vqg_set_hamiltonian(self._h, len(c), _ptr(x), _ptr(z), _ptr(c)))
+
+    # -- evaluation (host buffers)
+    def _theta(self, theta) -> np.ndarray:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        if th.shape != (self.n_params,):
+            raise ValueError(f"theta must have shape ({self.n_params},)")
+        return th
+
+    def energy(self, theta) -> float:
+        th = self._theta(theta)
+        e = np.zeros(1)
+        _check(lib().vqg_energy(self._h, _ptr(th), _ptr(e)))
+        return float(e[0])
+
+    def energy_and_gradient(self, theta, out: np.ndarray | None = None):
+        th = self._theta(theta)
+        e = np.zeros(1)
+        g = out if out is not None else np.zeros(max(self.n_params, 1))
+        _check(lib().vqg_energy_and_gradient(self._h, _ptr(th), _ptr(e), _ptr(g)))
+        return float(e[0]), g[: self.n_params]
+
+    def gradient_parameter_shift(self, theta, first_gate: int = 0, last_gate: int = -1):
+        th = self._theta(theta)
+        g = np.zeros(max(self.n_params, 1))
+        _check(lib().vqg_gradient_parameter_shift(self._h, _ptr(th), first_gate, last_gate, _ptr(g)))
+        return g[: self.n_params]
+
+    # -- evaluation (device pointers, e.g. torch CUDA tensors); no synchronisation
+    def energy_device(self, theta_ptr: int, energy_ptr: int):
+        _check(lib().vqg_energy_device(self._h, ctypes.c_void_p(theta_ptr), ctypes.c_void_p(energy_ptr)))
+
+    def energy_and_gradient_device(self, theta_ptr: int, energy_ptr: int, grad_ptr: int):
+        _check(lib().vqg_energy_and_gradient_device(self._h, ctypes.c_void_p(theta_ptr),
+                                                    ctypes.c_void_p(energy_ptr),
+                                                    ctypes.c_void_p(grad_ptr)))
+
+    # -- inspection
+    def get_state(self) -> np.ndarray:
+        dt = np.complex64 if DTYPE[self.dtype] == 0 else np.complex128
+        out = np.zeros(1 << self.n, dtype=dt)
+        _check(lib().vqg_get_state(self._h, _ptr(out), out.nbytes))
+        return out
+
+    def plan(self) -> dict:
+        info = vqg_plan_info()
+        _check(lib().vqg_plan(self._h, ctypes.byref(info)))
+        return {k: getattr(info, k) for k, _t in vqg_plan_info._fields_ if k != "reserved"}
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().vqg_set_profiling(self._h, int(enable)))
+
+    def kernel_stats(self) -> dict:
+        n = 32
+        ids = (ctypes.c_int * n)()
+        launches = (ctypes.c_int * n)()
+        ms = (ctypes.c_double * n)()
+        k = lib().vqg_kernel_stats(self._h, n, ids, launches, ms)
+        if k < 0:
+            _check(k)
+        return {lib().vqg_kernel_family_name(ids[i]).decode(): (launches[i], ms[i]) for i in range(k)}

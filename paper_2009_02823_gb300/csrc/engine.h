@@ -1,0 +1,118 @@
+// Circuit object and execution plan (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "../../include/vqg.h"
+#include "kernels.h"
+
+namespace vqg {
+
+int set_error(int status, const char *fmt, ...);
+
+enum Family {
+    FAM_INIT = 0, FAM_TABLE, FAM_FWD_GATE, FAM_FWD_FUSED, FAM_HAM_DIAG, FAM_HAM_GROUP,
+    FAM_HAM_FUSED, FAM_ADJ_GATE, FAM_ADJ_FUSED, FAM_REDUCE, FAM_CKPT, FAM_FINALIZE, FAM_BATCH,
+    FAM_COUNT
+};
+
+struct HamGroup {
+    uint64_t x;
+    int first, count;
+};
+
+struct PendingEvent {
+    int fam;
+    cudaEvent_t start, stop;
+};
+
+struct Circuit {
+    // problem
+    int n = 0, G = 0, P = 0, dtype = 0;
+    bool dbl = false;
+    int amp_bytes = 8;
+    size_t state_bytes = 0;
+    vqg_options opt{};
+    std::vector<vqg_gate> gates;
+    std::vector<int> slot_base;
+    int n_gslots = 0, n_eslots = 1;
+
+    // device / stream
+    int device = 0, num_sms = 1, nb = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // device buffers
+    std::vector<void *> dev_allocs;
+    void *psi = nullptr, *lam = nullptr;
+    std::vector<int> ckpt_pos;
+    std::vector<void *> ckpt_buf;
+    DevGate *d_gates = nullptr;
+    double *d_mats = nullptr, *d_theta = nullptr, *d_out = nullptr;
+    double *d_partials = nullptr, *d_red = nullptr;
+    int partial_cap = 0;
+    int *d_slot_base = nullptr, *d_occ_ptr = nullptr;
+    Occurrence *d_occ = nullptr;
+    double *h_pinned = nullptr;
+
+    // Hamiltonian
+    bool has_ham = false;
+    std::vector<HamGroup> ham;
+    PauliTerm *d_terms = nullptr;
+    int n_terms = 0;
+
+    // fused plan (engine.cu)
+    bool plan_ok = false, ham_plan_ok = false;
+    void *plan_dev = nullptr;  // opaque device-side schedule
+    struct Plan *plan = nullptr;
+
+    // graphs
+    cudaGraphExec_t graph_exec_grad = nullptr, graph_exec_energy = nullptr;
+
+    // profiling
+    bool profiling = false;
+    std::vector<PendingEvent> pending;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+    long fam_launches[FAM_COUNT] = {};
+    double fam_ms[FAM_COUNT] = {};
+
+    ~Circuit();
+    int init(int n, const vqg_gate *gates, int G, int P, int dtype, const vqg_options *opt);
+    int dalloc(void **p, size_t bytes);
+    void dfree(void *p);
+    int ensure_partials();
+    int plan_checkpoints();
+    int set_groups(const std::map<uint64_t, std::vector<PauliTerm>> &groups);
+
+    int issue_table(const double *theta_dev, int shift_gate, int shift_slot, double shift);
+    int issue_forward(bool with_ckpt);
+    int issue_hamiltonian(bool write_lam);
+    int issue_reverse();
+    int issue_finalize(double *energy_dev, double *grad_dev, const double *theta_dev);
+    int run_gradient(const double *theta_dev, double *energy_dev, double *grad_dev);
+    int run_energy(const double *theta_dev, double *energy_dev, int sg, int ss, double sh);
+
+    // fused path (engine.cu)
+    int build_plan();
+    void free_plan();
+    int issue_forward_fused(bool with_ckpt);
+    int issue_hamiltonian_fused();
+    int issue_reverse_fused();
+    void fill_plan_info(vqg_plan_info *info) const;
+    const void *psi_forward() const { return psi; }
+    void invalidate_graphs() {
+        if (graph_exec_grad) cudaGraphExecDestroy(graph_exec_grad);
+        if (graph_exec_energy) cudaGraphExecDestroy(graph_exec_energy);
+        graph_exec_grad = graph_exec_energy = nullptr;
+    }
+
+    void prof_begin(int fam);
+    void prof_end();
+    void prof_harvest();
+};
+
+}  // namespace vqg

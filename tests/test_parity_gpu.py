@@ -1,0 +1,183 @@
+"""Element-wise parity of the CUDA path (through the C ABI) with the CPU oracle on
+seeded inputs: every gate kind at every qubit position (q = 0, 1, n-1 included),
+repeated and multi-parameter gates, Pauli groups with Y factors, identity and
+diagonal-only Hamiltonians, both precisions, the unfused and fused schedules, and
+checkpointing."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_02823_gb300 import workloads as W
+from tests.tolerances import TOL, assert_parity, energy_err, grad_err
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = ["c128", "c64"]
+MODES = [dict(fusion=False), dict(fusion=True)]
+
+
+def _circ(w_n, gates, P, dtype, terms, **kw):
+    from paper_2009_02823_gb300 import Circuit
+    c = Circuit(w_n, gates, P, dtype, **kw)
+    c.set_hamiltonian(terms)
+    return c
+
+
+def _oracle(n, gates, theta, P, terms):
+    return oracle.gradient_alg1(n, gates, theta, P, terms)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["per_gate", "fused"])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("seed", range(10))
+def test_random_circuits(seed, dtype, mode):
+    rng = np.random.default_rng(1000 + seed)
+    n = [1, 2, 3, 4, 5, 7, 9, 11, 12, 13][seed]
+    kinds = ("RX", "RY", "RZ", "U3") if n == 1 else ("RX", "RY", "RZ", "U3", "CNOT", "CZ")
+    gates, P = W.random_circuit(rng, n, 40 + 4 * n, share_params=(seed % 3 == 0), kinds=kinds)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    terms = W.random_paulis(rng, n, 9, min(4, n))
+    if seed == 4:
+        terms.append((0.75, ()))  # identity term (x = z = 0)
+    if seed == 5:
+        terms = [(c, tuple((q, "Z") for q, _l in ops)) for c, ops in terms]  # diagonal only
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, dtype, terms, **mode) as c:
+        e, g = c.energy_and_gradient(theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, f"n={n}")
+        assert energy_err(c.energy(theta), e_ref) <= TOL[dtype]
+        psi = c.get_state()
+        ref = oracle.state(n, gates, theta)
+        assert np.max(np.abs(psi - ref)) <= (1e-12 if dtype == "c128" else 2e-5)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("kind", ["RX", "RY", "RZ", "U3", "CNOT", "CZ"])
+def test_every_qubit_position(kind, dtype):
+    """One gate kind on every qubit (and every ordered pair for entanglers), each with a
+    preparing layer so no amplitude is trivially zero."""
+    n = 6
+    rng = np.random.default_rng(7)
+    gates, P = [], 0
+    for q in range(n):
+        gates.append(("U3", q, -1, (P, P + 1, P + 2)))
+        P += 3
+    if kind in ("CNOT", "CZ"):
+        for a in range(n):
+            for b in range(n):
+                if a != b:
+                    gates.append((kind, a, b, (-1, -1, -1)))
+                    gates.append(("RY", b, -1, (P, -1, -1)))
+                    P += 1
+    else:
+        for q in range(n):
+            k = 3 if kind == "U3" else 1
+            gates.append((kind, q, -1, tuple(range(P, P + k)) + (-1,) * (3 - k)))
+            P += k
+            gates.append(("CNOT", q, (q + 1) % n, (-1, -1, -1)))
+    theta = rng.uniform(0, 2 * np.pi, P)
+    terms = W.random_paulis(rng, n, 12, 4)
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    for mode in MODES:
+        with _circ(n, gates, P, dtype, terms, **mode) as c:
+            e, g = c.energy_and_gradient(theta)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"{kind} {mode}")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES, ids=["per_gate", "fused"])
+def test_cfg1_vs_faithful_parameter_shift(dtype, mode):
+    """n=10 hardware-efficient ansatz with TFIM: against the faithful O(P^2) oracle."""
+    w = W.config(1)
+    g_ref = oracle.gradient_parameter_shift(w.n, w.gates, w.theta, w.n_params, w.terms)
+    e_ref = oracle.energy(w.n, w.gates, w.theta, w.terms)
+    with _circ(w.n, w.gates, w.n_params, dtype, w.terms, **mode) as c:
+        e, g = c.energy_and_gradient(w.theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, "cfg1")
+        # repeated calls give bit-identical results (deterministic reductions)
+        e2, g2 = c.energy_and_gradient(w.theta)
+        assert e2 == e and np.array_equal(g2, g)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("cfg,n,layers", [(2, 12, 4), (3, 14, 3), (5, 10, 3), (1, 16, 2)])
+def test_configs_reduced_size(cfg, n, layers, dtype):
+    """Each workload recipe at a size the oracle finishes in seconds (several tiles and a
+    ragged tail for the fused kernels)."""
+    w = W.config(cfg, n=n, layers=layers)
+    e_ref, g_ref = _oracle(w.n, w.gates, w.theta, w.n_params, w.terms)
+    for mode in MODES:
+        with _circ(w.n, w.gates, w.n_params, dtype, w.terms, **mode) as c:
+            e, g = c.energy_and_gradient(w.theta)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"cfg{cfg} {mode}")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_gpu_parameter_shift_baseline(dtype):
+    w = W.config(1, n=8, layers=2)
+    g_ref = oracle.gradient_parameter_shift(w.n, w.gates, w.theta, w.n_params, w.terms)
+    with _circ(w.n, w.gates, w.n_params, dtype, w.terms) as c:
+        g = c.gradient_parameter_shift(w.theta)
+        assert grad_err(g, g_ref) <= TOL[dtype]
+        # a sub-range of occurrences
+        g_part = c.gradient_parameter_shift(w.theta, 3, 9)
+        ref_part = oracle.gradient_parameter_shift(w.n, w.gates, w.theta, w.n_params, w.terms, 3, 9)
+        assert np.max(np.abs(g_part - ref_part)) <= TOL[dtype] * max(1.0, np.max(np.abs(ref_part)))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("interval", [1, 3, 7, 64])
+def test_checkpoint_restarts(dtype, interval):
+    """Forward-state checkpoints every `interval` gates restart phi in the reverse sweep;
+    the result is the same gradient."""
+    w = W.config(3, n=12, layers=4)
+    e_ref, g_ref = _oracle(w.n, w.gates, w.theta, w.n_params, w.terms)
+    for mode in MODES:
+        with _circ(w.n, w.gates, w.n_params, dtype, w.terms, checkpoint_interval=interval, **mode) as c:
+            assert c.plan()["checkpoints"] == (w.n_gates - 1) // interval
+            e, g = c.energy_and_gradient(w.theta)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"ckpt={interval} {mode}")
+
+
+def test_hamiltonian_can_change_between_calls():
+    w = W.config(1, n=9, layers=2)
+    rng = np.random.default_rng(3)
+    with _circ(w.n, w.gates, w.n_params, "c128", w.terms) as c:
+        for _ in range(3):
+            terms = W.random_paulis(rng, w.n, 7, 3)
+            c.set_hamiltonian(terms)
+            e_ref, g_ref = _oracle(w.n, w.gates, w.theta, w.n_params, terms)
+            e, g = c.energy_and_gradient(w.theta)
+            assert_parity("c128", e, g, e_ref, g_ref, "H swap")
+
+
+def test_empty_and_degenerate():
+    """No gates; no parameters; empty Hamiltonian; one qubit."""
+    from paper_2009_02823_gb300 import Circuit
+    with Circuit(3, [], 0, "c128") as c:
+        c.set_hamiltonian([(1.0, ((0, "Z"),)), (0.5, ((1, "X"),))])
+        e, g = c.energy_and_gradient(np.zeros(0))
+        assert e == pytest.approx(1.0, abs=1e-15) and g.size == 0
+    with Circuit(2, [("CNOT", 0, 1, (-1, -1, -1))], 0, "c64") as c:
+        c.set_hamiltonian([])
+        e, g = c.energy_and_gradient(np.zeros(0))
+        assert e == 0.0
+    with Circuit(1, [("RX", 0, -1, (0, -1, -1))], 1, "c128") as c:
+        c.set_hamiltonian([(1.0, ((0, "Z"),))])
+        for t in (0.0, 0.4, np.pi, 5.0):
+            e, g = c.energy_and_gradient(np.array([t]))
+            assert e == pytest.approx(np.cos(t), abs=1e-14)
+            assert g[0] == pytest.approx(-np.sin(t), abs=1e-14)
+
+
+def test_unused_parameter_has_zero_gradient():
+    from paper_2009_02823_gb300 import Circuit
+    gates = [("RY", 0, -1, (2, -1, -1)), ("CNOT", 0, 1, (-1, -1, -1)), ("RX", 1, -1, (0, -1, -1))]
+    th = np.array([0.3, 1.7, 0.9])
+    terms = [(1.0, ((0, "Z"), (1, "Z"))), (0.3, ((1, "X"),))]
+    e_ref, g_ref = _oracle(2, gates, th, 3, terms)
+    with Circuit(2, gates, 3, "c128") as c:
+        c.set_hamiltonian(terms)
+        e, g = c.energy_and_gradient(th)
+        assert g[1] == 0.0
+        assert_parity("c128", e, g, e_ref, g_ref)
