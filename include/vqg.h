@@ -162,6 +162,38 @@ int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 const char *vqg_last_error(void);
 const char *vqg_status_string(int status);
 
+/* ---------------------------------------------------------------- allocation-free step
+ * The paper has no counterpart to this entry point; it exists for callers that must
+ * not allocate device memory while they run: a process whose device memory is owned
+ * by another allocator (for example a framework's caching pool that holds the whole
+ * GPU), a service whose memory footprint is fixed at start-up, or a latency-critical
+ * thread that may not enter cudaMalloc/cudaFree because those calls can synchronise
+ * the device.  Every vqg_circuit allocates its state vectors at create time, so those
+ * callers use this function on state vectors they already own.
+ *
+ * vqg_reverse_noalloc runs the reverse-sweep body (un-apply U^dagger to phi and lambda,
+ * accumulate the gate's gradient contributions) for gates[n_gates-1] down to gates[0]:
+ *   phi, lam : device state vectors of 2^n_qubits amplitudes (dtype), both updated in
+ *              place; on entry phi = U_{1:G}|in> restricted to the segment's end and lam
+ *              the matching lambda, exactly as in Algorithm 1's loop.
+ *   theta    : host array of n_params doubles; grad: device array of n_params doubles
+ *              to which the contributions are ADDED (the caller zeroes it first).
+ *   stream   : cudaStream_t (NULL = legacy default stream); work is asynchronous.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its reduction scratch
+ * is a file-scope static device array (1 MiB of per-block partial sums plus 8 KiB of
+ * gate matrices) that every GPU the process uses holds until the process exits.  At
+ * most VQG_NOALLOC_MAX_GATES gates per call; more returns VQG_ERR_INVALID (split a
+ * longer sweep into segments and call them last segment first).  The first call on
+ * each device resolves the scratch arrays' device addresses (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the scratch: calls
+ * whose work overlaps on the GPU (different streams or host threads) race and must be
+ * serialised by the caller.  Returns VQG_OK or a negative vqg_status. */
+#define VQG_NOALLOC_MAX_GATES 32
+#define VQG_NOALLOC_BLOCKS 512
+int vqg_reverse_noalloc(int n_qubits, int dtype, const vqg_gate *gates, int n_gates,
+                        const double *theta, int n_params, void *phi, void *lam, double *grad,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

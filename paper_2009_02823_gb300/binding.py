@@ -88,6 +88,7 @@ def lib():
             "vqg_plan": (i, [p, p]),
             "vqg_last_error": (ctypes.c_char_p, []),
             "vqg_status_string": (ctypes.c_char_p, [i]),
+            "vqg_reverse_noalloc": (i, [i, i, p, i, p, i, p, p, p, p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -254,3 +255,20 @@ class Circuit:
         if k < 0:
             _check(k)
         return {lib().vqg_kernel_family_name(ids[i]).decode(): (launches[i], ms[i]) for i in range(k)}
+
+
+NOALLOC_MAX_GATES = 32
+
+
+def reverse_noalloc(n: int, dtype: str, gates, theta, n_params: int, phi_ptr: int, lam_ptr: int,
+                    grad_ptr: int, stream=None):
+    """vqg_reverse_noalloc: reverse-sweep steps over caller-owned device vectors, no
+    device allocation (at most NOALLOC_MAX_GATES gates per call)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.size == 0:
+        th = np.zeros(1)
+    arr = gate_array(gates)
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().vqg_reverse_noalloc(n, DTYPE[dtype], arr, len(gates), _ptr(th), n_params,
+                                     ctypes.c_void_p(phi_ptr), ctypes.c_void_p(lam_ptr),
+                                     ctypes.c_void_p(grad_ptr), ctypes.c_void_p(raw or None)))
