@@ -159,6 +159,15 @@ typedef struct vqg_plan_info {
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 
+/* Plan a circuit and Hamiltonian on the host only (no GPU is touched): the same tile
+ * passes, register stages and Hamiltonian passes a vqg_circuit with these options
+ * would run, checked index by index.  info->reserved[0] / [1] receive the forward /
+ * reverse register-stage counts.  Returns VQG_ERR_INVALID for malformed input and
+ * VQG_ERR_UNSUPPORTED if the schedule fails its checks. */
+int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype,
+                     const vqg_options *opt, int n_terms, const uint64_t *x_mask,
+                     const uint64_t *z_mask, const double *coef, vqg_plan_info *info);
+
 const char *vqg_last_error(void);
 const char *vqg_status_string(int status);
 

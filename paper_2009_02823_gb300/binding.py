@@ -89,6 +89,7 @@ def lib():
             "vqg_last_error": (ctypes.c_char_p, []),
             "vqg_status_string": (ctypes.c_char_p, [i]),
             "vqg_reverse_noalloc": (i, [i, i, p, i, p, i, p, p, p, p]),
+            "vqg_plan_dry_run": (i, [i, p, i, i, i, p, i, p, p, p, p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -272,3 +273,22 @@ def reverse_noalloc(n: int, dtype: str, gates, theta, n_params: int, phi_ptr: in
     _check(lib().vqg_reverse_noalloc(n, DTYPE[dtype], arr, len(gates), _ptr(th), n_params,
                                      ctypes.c_void_p(phi_ptr), ctypes.c_void_p(lam_ptr),
                                      ctypes.c_void_p(grad_ptr), ctypes.c_void_p(raw or None)))
+
+
+def plan_dry_run(n: int, gates, n_params: int, terms, dtype: str = "c64", *, fusion: bool = True,
+                 tile_qubits: int = 0, checkpoint_interval: int = 0) -> dict:
+    """Host-only schedule of a circuit + Hamiltonian (vqg_plan_dry_run); no GPU needed."""
+    L = lib()
+    opt = vqg_options()
+    L.vqg_default_options(ctypes.byref(opt))
+    opt.fusion = int(fusion)
+    opt.tile_qubits = tile_qubits
+    opt.checkpoint_interval = checkpoint_interval
+    x, z, c = pauli_masks(terms, n)
+    info = vqg_plan_info()
+    arr = gate_array(gates)
+    _check(L.vqg_plan_dry_run(n, arr, len(gates), n_params, DTYPE[dtype], ctypes.byref(opt), len(c),
+                              _ptr(x), _ptr(z), _ptr(c), ctypes.byref(info)))
+    out = {k: getattr(info, k) for k, _t in vqg_plan_info._fields_ if k != "reserved"}
+    out["forward_stages"], out["reverse_stages"] = info.reserved[0], info.reserved[1]
+    return out

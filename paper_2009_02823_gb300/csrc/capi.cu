@@ -114,6 +114,7 @@ void Circuit::prof_harvest() {
 }
 
 Circuit::~Circuit() {
+    free_plan();
     if (graph_exec_grad) cudaGraphExecDestroy(graph_exec_grad);
     if (graph_exec_energy) cudaGraphExecDestroy(graph_exec_energy);
     for (void *p : dev_allocs) cudaFree(p);
@@ -163,10 +164,7 @@ int Circuit::ensure_partials() {
 static bool is_1q(int k) { return k >= VQG_RX && k <= VQG_U3; }
 static int nparams_of(int k) { return k == VQG_U3 ? 3 : (is_1q(k) ? 1 : 0); }
 
-extern "C" int vqg_circuit_create(int n_qubits, const vqg_gate *gates, int n_gates, int n_params,
-                                  int dtype, const vqg_options *opt, vqg_circuit **out) {
-    if (!out) return set_error(VQG_ERR_INVALID, "out is NULL");
-    *out = nullptr;
+int vqg::vqg_validate_circuit(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype) {
     if (n_qubits < 1 || n_qubits > 34) return set_error(VQG_ERR_INVALID, "n_qubits=%d outside 1..34", n_qubits);
     if (n_gates < 0 || (n_gates > 0 && !gates)) return set_error(VQG_ERR_INVALID, "bad gate list");
     if (n_params < 0) return set_error(VQG_ERR_INVALID, "n_params=%d < 0", n_params);
@@ -183,6 +181,15 @@ extern "C" int vqg_circuit_create(int n_qubits, const vqg_gate *gates, int n_gat
             if (g.param[j] < 0 || g.param[j] >= n_params)
                 return set_error(VQG_ERR_INVALID, "gate %d: parameter index %d out of range", i, g.param[j]);
     }
+    return VQG_OK;
+}
+
+extern "C" int vqg_circuit_create(int n_qubits, const vqg_gate *gates, int n_gates, int n_params,
+                                  int dtype, const vqg_options *opt, vqg_circuit **out) {
+    if (!out) return set_error(VQG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int vst = vqg_validate_circuit(n_qubits, gates, n_gates, n_params, dtype);
+    if (vst) return vst;
     Circuit *c = new (std::nothrow) Circuit();
     if (!c) return set_error(VQG_ERR_OOM, "host allocation failed");
     int st = c->init(n_qubits, gates, n_gates, n_params, dtype, opt);
@@ -256,17 +263,22 @@ int Circuit::init(int n_, const vqg_gate *gates_, int G_, int P_, int dtype_, co
     // state vectors
     if ((st = dalloc(&psi, state_bytes))) return st;
     if ((st = dalloc(&lam, state_bytes))) return st;
-    if ((st = plan_checkpoints())) return st;
-    return build_plan();
+    if ((st = build_plan())) return st;
+    return plan_checkpoints();
 }
 
+// Forward states are stored every `interval` gates (per-gate schedule) or at the first
+// pass boundary after every `interval` gates (fused schedule), as many as fit.
 int Circuit::plan_checkpoints() {
     int interval = opt.checkpoint_interval;
     if (interval == 0) interval = dbl ? -1 : 64;
     ckpt_pos.clear();
     if (interval < 0 || G < 2) return VQG_OK;
+    const bool fused = opt.fusion && plan_ok;
     std::vector<int> want;
-    for (int c = interval; c < G; c += interval) want.push_back(c);
+    if (fused) want = fused_checkpoint_passes(interval);
+    else
+        for (int c = interval; c < G; c += interval) want.push_back(c);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     const size_t headroom = (size_t)4 << 30;
@@ -281,7 +293,8 @@ int Circuit::plan_checkpoints() {
     for (int pos : want) {
         void *buf = nullptr;
         if (dalloc(&buf, state_bytes) != VQG_OK) break;  // fewer checkpoints, still correct
-        ckpt_pos.push_back(pos);
+        if (fused) set_fused_checkpoint(pos, (int)ckpt_buf.size());
+        else ckpt_pos.push_back(pos);
         ckpt_buf.push_back(buf);
     }
     cudaGetLastError();
@@ -322,37 +335,15 @@ extern "C" int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *
                                    const uint64_t *z_mask, const double *coef) {
     if (!c) return set_error(VQG_ERR_INVALID, "circuit is NULL");
     Circuit *cc = reinterpret_cast<Circuit *>(c);
-    if (n_terms < 0 || (n_terms > 0 && (!x_mask || !z_mask || !coef)))
-        return set_error(VQG_ERR_INVALID, "bad Hamiltonian arrays");
-    const uint64_t lim = cc->n >= 64 ? ~0ull : ((1ull << cc->n) - 1ull);
-    std::map<uint64_t, std::vector<PauliTerm>> groups;
-    groups[0];  // the diagonal group always exists (it writes lambda first)
-    for (int t = 0; t < n_terms; ++t) {
-        if ((x_mask[t] & ~lim) || (z_mask[t] & ~lim))
-            return set_error(VQG_ERR_INVALID, "term %d: mask has bits >= n", t);
-        if (!std::isfinite(coef[t])) return set_error(VQG_ERR_INVALID, "term %d: coefficient not finite", t);
-        const int ny = __builtin_popcountll(x_mask[t] & z_mask[t]) & 3;
-        PauliTerm p;
-        p.z = z_mask[t];
-        // i^{ny} * coef
-        p.wr = (ny == 0) ? coef[t] : (ny == 2 ? -coef[t] : 0.0);
-        p.wi = (ny == 1) ? coef[t] : (ny == 3 ? -coef[t] : 0.0);
-        groups[x_mask[t]].push_back(p);
-    }
-    return cc->set_groups(groups);
+    std::vector<HamGroup> ham;
+    std::vector<PauliTerm> flat;
+    int st = group_pauli_terms(cc->n, n_terms, x_mask, z_mask, coef, ham, flat);
+    if (st) return st;
+    return cc->set_groups(ham, flat);
 }
 
-int Circuit::set_groups(const std::map<uint64_t, std::vector<PauliTerm>> &groups) {
-    std::vector<PauliTerm> flat;
-    ham.clear();
-    for (auto &kv : groups) {
-        HamGroup g;
-        g.x = kv.first;
-        g.first = (int)flat.size();
-        g.count = (int)kv.second.size();
-        flat.insert(flat.end(), kv.second.begin(), kv.second.end());
-        ham.push_back(g);
-    }
+int Circuit::set_groups(const std::vector<HamGroup> &groups, const std::vector<PauliTerm> &flat) {
+    ham = groups;
     int st;
     dfree(d_terms);
     d_terms = nullptr;
@@ -360,7 +351,8 @@ int Circuit::set_groups(const std::map<uint64_t, std::vector<PauliTerm>> &groups
     if (!flat.empty())
         VQG_CUDA(cudaMemcpy(d_terms, flat.data(), sizeof(PauliTerm) * flat.size(), cudaMemcpyHostToDevice));
     n_terms = (int)flat.size();
-    n_eslots = (int)ham.size();
+    host_terms = flat;
+    n_eslots = std::max(n_eslots, (int)ham.size());
     has_ham = true;
     if ((st = ensure_partials())) return st;
     invalidate_graphs();
@@ -370,16 +362,16 @@ int Circuit::set_groups(const std::map<uint64_t, std::vector<PauliTerm>> &groups
 // ------------------------------------------------------------------ launch sequences
 int Circuit::issue_table(const double *theta_dev, int shift_gate, int shift_slot, double shift) {
     prof_begin(FAM_TABLE);
-    launch_build_mats(theta_dev, d_gates, G, d_mats, shift_gate, shift_slot, shift, stream);
+    launch_build_mats(theta_dev, d_gates, G, d_mats, mats_f(), shift_gate, shift_slot, shift, stream);
     prof_end();
     return check_launch("build_mats");
 }
 
 int Circuit::issue_forward(bool with_ckpt) {
+    if (opt.fusion && plan_ok) return issue_forward_fused(with_ckpt);  // pass 0 starts from |0...0>
     prof_begin(FAM_INIT);
     launch_init_zero(psi, n, dbl, nb, stream);
     prof_end();
-    if (opt.fusion && plan_ok) return issue_forward_fused(with_ckpt);
     size_t k = 0;
     for (int i = 0; i < G; ++i) {
         const vqg_gate &g = gates[i];
@@ -397,7 +389,8 @@ int Circuit::issue_forward(bool with_ckpt) {
 }
 
 int Circuit::issue_hamiltonian(bool write_lam) {
-    if (opt.fusion && plan_ok && write_lam && ham_plan_ok) return issue_hamiltonian_fused();
+    if (opt.fusion && plan_ok && ham_plan_ok) return issue_hamiltonian_fused();
+    e_used = (int)ham.size();
     for (size_t g = 0; g < ham.size(); ++g) {
         const HamGroup &h = ham[g];
         double *part = d_partials + (size_t)g * nb;
@@ -435,7 +428,7 @@ int Circuit::issue_finalize(double *energy_dev, double *grad_dev, const double *
     launch_reduce_slots(d_partials, n_eslots + (grad_dev ? n_gslots : 0), nb, d_red, stream);
     prof_end();
     prof_begin(FAM_FINALIZE);
-    launch_finalize(d_red, n_eslots, d_red + n_eslots, theta_dev, d_gates, d_slot_base, d_occ_ptr,
+    launch_finalize(d_red, e_used, d_red + n_eslots, theta_dev, d_gates, d_slot_base, d_occ_ptr,
                     d_occ, grad_dev ? P : 0, energy_dev, grad_dev, stream);
     prof_end();
     return check_launch("finalize");

@@ -1,31 +1,742 @@
-// Execution planner: turns the gate list into fused tile passes.
+// Execution planner: turns the gate list into tile passes and register stages, and
+// the Pauli groups into Hamiltonian tile passes; issues the fused launch sequence.
+//
+// Scheduling rule (shared by passes and stages).  Gates are taken in circuit order;
+// a gate is applied in the current pass/stage if every qubit it acts on
+// non-diagonally lies in the chosen set S and no earlier gate left for later blocks
+// it: an earlier deferred gate blocks a later one on a shared qubit unless both act
+// diagonally there (RZ, CZ, and the control of CNOT are diagonal in the
+// computational basis, so they commute).  The result is a reordering of the circuit
+// that only swaps commuting gates, so U(theta) -- and with it E(theta) and every
+// gradient entry -- is unchanged.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
 #include <cstring>
+#include <string>
+#include <vector>
 
 #include "engine.h"
+#include "fused.h"
 
 namespace vqg {
 
+void launch_fused_fwd(bool dbl, int K, const void *src, void *dst, const FPass *passes, int pi,
+                      const FStage *st, const FOp *ops, const void *mats, uint64_t n_tiles, int grid,
+                      cudaStream_t s);
+void launch_fused_rev(bool dbl, int K, const void *phi_src, void *phi_dst, void *lam,
+                      const FPass *passes, int pi, const FStage *st, const FOp *ops,
+                      const int *slot_map, const void *mats, uint64_t n_tiles, double *partials,
+                      int nb, cudaStream_t s);
+void launch_fused_ham(bool dbl, int K, const void *psi, void *lam, const HPass *hp, int pi,
+                      const HGroup *groups, const HTerm *terms, uint64_t n_tiles, double *partials,
+                      int nb, cudaStream_t s);
+
+struct QUse {
+    int q;
+    bool diag;
+};
+
+static int uses_of(const vqg_gate &g, QUse *u) {
+    switch (g.kind) {
+    case VQG_RX: case VQG_RY: case VQG_U3: u[0] = {g.q0, false}; return 1;
+    case VQG_RZ: u[0] = {g.q0, true}; return 1;
+    case VQG_CZ: u[0] = {g.q0, true}; u[1] = {g.q1, true}; return 2;
+    case VQG_CNOT: u[0] = {g.q0, true}; u[1] = {g.q1, false}; return 2;
+    default: return 0;
+    }
+}
+
+static int red_values(int kind) { return kind == VQG_U3 ? 8 : (kind <= VQG_RZ ? 1 : 0); }
+
+// One greedy sweep over `order` with non-diagonal set `inS` (indexed by qubit).
+// Applied gates go to `applied` (in order), the rest to `left`.  `cap_ops` /
+// `cap_slots` bound the run (gates past the cap are deferred like blocked ones).
+static void greedy(const std::vector<vqg_gate> &gates, const std::vector<int> &order,
+                   const std::vector<char> &inS, int n, int cap_ops, int cap_slots,
+                   std::vector<int> &applied, std::vector<int> &left) {
+    std::vector<char> nd(n, 0), dg(n, 0);
+    int slots = 0;
+    applied.clear();
+    left.clear();
+    for (int i : order) {
+        QUse u[2];
+        const int nu = uses_of(gates[i], u);
+        bool ok = (int)applied.size() < cap_ops && slots + red_values(gates[i].kind) <= cap_slots;
+        for (int k = 0; k < nu && ok; ++k) {
+            const int q = u[k].q;
+            if (u[k].diag) ok = !nd[q];
+            else ok = !nd[q] && !dg[q] && inS[q];
+        }
+        if (ok) {
+            applied.push_back(i);
+            slots += red_values(gates[i].kind);
+        } else {
+            left.push_back(i);
+            for (int k = 0; k < nu; ++k) (u[k].diag ? dg : nd)[u[k].q] = 1;
+        }
+    }
+}
+
+struct Plan {
+    int K = 0, L = 0, Rf = 0, Rr = 0;
+    uint64_t n_tiles = 0;
+    int grid_fwd = 0;
+    std::vector<FPass> passes;
+    std::vector<FStage> stages;
+    std::vector<FOp> ops;
+    std::vector<int> slot_map;
+    std::vector<int> ckpt_of_pass;  // checkpoint index storing the output of pass j, or -1
+    std::vector<HPass> hp;
+    std::vector<HGroup> hg;
+    std::vector<HTerm> ht;
+    FPass *d_passes = nullptr;
+    FStage *d_stages = nullptr;
+    FOp *d_ops = nullptr;
+    int *d_slot_map = nullptr;
+    HPass *d_hp = nullptr;
+    HGroup *d_hg = nullptr;
+    HTerm *d_ht = nullptr;
+    float *d_mats_f = nullptr;
+};
+
+// Tile layout of a pass: positions 0..L-1 are qubits 0..L-1, then `high` ascending.
+struct TileMap {
+    int K, L;
+    std::vector<int> pos_of;   // qubit -> tile position or -1
+    std::vector<int> qubit_of; // tile position -> qubit
+};
+
+static TileMap make_tilemap(int n, int K, int L, const std::vector<int> &high) {
+    TileMap t;
+    t.K = K;
+    t.L = L;
+    t.pos_of.assign(n, -1);
+    for (int q = 0; q < L; ++q) t.pos_of[q] = q, t.qubit_of.push_back(q);
+    for (size_t i = 0; i < high.size(); ++i) t.pos_of[high[i]] = L + (int)i, t.qubit_of.push_back(high[i]);
+    return t;
+}
+
+// Choose the K-L high qubits for the next pass: the first distinct qubits >= L used
+// non-diagonally by the remaining gates, padded with the lowest unused qubits.
+static std::vector<int> choose_high(const std::vector<vqg_gate> &gates, const std::vector<int> &rem,
+                                    int n, int K, int L) {
+    std::vector<int> high;
+    std::vector<char> taken(n, 0);
+    for (int i : rem) {
+        QUse u[2];
+        const int nu = uses_of(gates[i], u);
+        for (int k = 0; k < nu; ++k)
+            if (!u[k].diag && u[k].q >= L && !taken[u[k].q] && (int)high.size() < K - L)
+                taken[u[k].q] = 1, high.push_back(u[k].q);
+        if ((int)high.size() == K - L) break;
+    }
+    for (int q = L; q < n && (int)high.size() < K - L; ++q)
+        if (!taken[q]) taken[q] = 1, high.push_back(q);
+    std::sort(high.begin(), high.end());
+    return high;
+}
+
+// Register stages of one pass over `seq` (gates in application order).  Emits stages
+// and ops into the plan; reverse stages carry reduction slots.
+static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
+                         int n, const TileMap &tm, const std::vector<int> &seq, int R, bool dbl,
+                         bool reverse, int &n_lslots, int &stage0, int &n_stage) {
+    stage0 = (int)pl.stages.size();
+    n_stage = 0;
+    n_lslots = 0;
+    const int K = tm.K;
+    const int AB = dbl ? 16 : 8;
+    std::vector<int> uns = seq, applied, left;
+    while (!uns.empty()) {
+        // register positions: needed tile positions in order of first use
+        std::vector<int> regs;
+        std::vector<char> isreg(K, 0);
+        for (int i : uns) {
+            QUse u[2];
+            const int nu = uses_of(gates[i], u);
+            for (int k = 0; k < nu; ++k) {
+                if (u[k].diag) continue;
+                const int p = tm.pos_of[u[k].q];
+                if (!isreg[p] && (int)regs.size() < R) isreg[p] = 1, regs.push_back(p);
+            }
+            if ((int)regs.size() == R) break;
+        }
+        // pad with high tile positions, keeping low positions for the lanes
+        for (int p = K - 1; p >= 0 && (int)regs.size() < R; --p)
+            if (!isreg[p]) isreg[p] = 1, regs.push_back(p);
+        std::vector<char> inS(n, 0);
+        for (int p : regs) inS[tm.qubit_of[p]] = 1;
+        greedy(gates, uns, inS, n, kMaxPassOps, kMaxPassSlots, applied, left);
+        // thread positions: lane bits with distinct residues (bank-conflict-free), then the rest
+        const int NL = dbl ? 3 : 4, MOD = dbl ? 3 : 4;
+        std::vector<int> thr;
+        std::vector<char> used(K, 0);
+        for (int r = 0; r < NL; ++r)
+            for (int p = 0; p < K; ++p)
+                if (!isreg[p] && !used[p] && p % MOD == r) {
+                    used[p] = 1;
+                    thr.push_back(p);
+                    break;
+                }
+        for (int p = 0; p < K; ++p)
+            if (!isreg[p] && !used[p]) used[p] = 1, thr.push_back(p);
+        FStage st;
+        std::memset(&st, 0, sizeof st);
+        for (size_t b = 0; b < thr.size(); ++b) {
+            st.thr_sw[b] = (uint16_t)(AB == 8 ? swz<8>(1u << thr[b]) : swz<16>(1u << thr[b]));
+            st.thr_g[b] = 1ull << tm.qubit_of[thr[b]];
+        }
+        for (int k = 0; k < R; ++k)
+            st.reg_sw[k] = (uint16_t)(AB == 8 ? swz<8>(1u << regs[k]) : swz<16>(1u << regs[k]));
+        st.op0 = (int)pl.ops.size();
+        st.n_op = (int)applied.size();
+        auto regbit = [&](int q) -> int {
+            const int p = tm.pos_of[q];
+            if (p < 0) return -1;
+            for (int k = 0; k < R; ++k)
+                if (regs[k] == p) return k;
+            return -1;
+        };
+        for (int i : applied) {
+            const vqg_gate &g = gates[i];
+            FOp op;
+            std::memset(&op, 0, sizeof op);
+            op.gate = i;
+            op.lslot = -1;
+            op.gslot = -1;
+            switch (g.kind) {
+            case VQG_RY: op.type = OP_RY; op.k = (int16_t)regbit(g.q0); break;
+            case VQG_RX: op.type = OP_RX; op.k = (int16_t)regbit(g.q0); break;
+            case VQG_U3: op.type = OP_U3; op.k = (int16_t)regbit(g.q0); break;
+            case VQG_RZ: {
+                const int k = regbit(g.q0);
+                if (k >= 0) op.type = OP_RZ_REG, op.k = (int16_t)k;
+                else op.type = OP_RZ_THR, op.g0 = 1ull << g.q0;
+                break;
+            }
+            case VQG_CZ: {
+                const int k0 = regbit(g.q0), k1 = regbit(g.q1);
+                op.type = OP_CZ;
+                if (k0 >= 0) op.rm0 = 1u << k0; else op.g0 = 1ull << g.q0;
+                if (k1 >= 0) op.rm1 = 1u << k1; else op.g1 = 1ull << g.q1;
+                break;
+            }
+            case VQG_CNOT: {
+                const int kc = regbit(g.q0);
+                op.type = OP_CNOT;
+                op.k = (int16_t)regbit(g.q1);
+                if (kc >= 0) op.rm0 = 1u << kc; else op.g0 = 1ull << g.q0;
+                break;
+            }
+            default: break;
+            }
+            if (reverse) {
+                const int nv = red_values(g.kind);
+                if (nv) {
+                    op.lslot = n_lslots;
+                    op.gslot = slot_base[i];
+                    for (int v = 0; v < nv; ++v) pl.slot_map.push_back(slot_base[i] + v);
+                    n_lslots += nv;
+                }
+            }
+            pl.ops.push_back(op);
+        }
+        pl.stages.push_back(st);
+        ++n_stage;
+        uns.swap(left);
+    }
+}
+
+// Host-side check of every index a fused kernel derives from the plan: tile
+// geometry, register/thread bit assignment (a permutation of the K tile positions),
+// op fields, reduction slots and Hamiltonian masks.  Returns an empty string if valid.
+static std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
+    char buf[256];
+    const int K = pl.K, L = pl.L;
+    auto fail = [&](const char *what, int a, int b) {
+        snprintf(buf, sizeof buf, "plan check failed: %s (%d, %d)", what, a, b);
+        return std::string(buf);
+    };
+    auto check_geom = [&](const int32_t *high, int n_high, const int32_t *nontile, int n_nt) -> std::string {
+        if (n_high != K - L || n_nt != n - K) return fail("tile geometry", n_high, n_nt);
+        std::vector<int> seen(n, 0);
+        for (int q = 0; q < L; ++q) seen[q]++;
+        for (int i = 0; i < n_high; ++i) {
+            if (high[i] < L || high[i] >= n) return fail("high qubit", i, high[i]);
+            seen[high[i]]++;
+        }
+        for (int i = 0; i < n_nt; ++i) {
+            if (nontile[i] < 0 || nontile[i] >= n) return fail("non-tile qubit", i, nontile[i]);
+            seen[nontile[i]]++;
+        }
+        for (int q = 0; q < n; ++q)
+            if (seen[q] != 1) return fail("qubit coverage", q, seen[q]);
+        return "";
+    };
+    for (size_t j = 0; j < pl.passes.size(); ++j) {
+        const FPass &p = pl.passes[j];
+        std::string e = check_geom(p.high, p.n_high, p.nontile, p.n_nontile);
+        if (!e.empty()) return e;
+        if (p.n_stage < 1 || p.n_stage > kMaxPassStages || p.n_rstage < 1 || p.n_rstage > kMaxPassStages)
+            return fail("stage count", p.n_stage, p.n_rstage);
+        if (p.n_lslots < 0 || p.n_lslots > kMaxPassSlots) return fail("slot count", (int)j, p.n_lslots);
+        if (p.slotmap0 < 0 || p.slotmap0 + p.n_lslots > (int)pl.slot_map.size()) return fail("slot map", (int)j, p.slotmap0);
+        for (int i = 0; i < p.n_lslots; ++i)
+            if (pl.slot_map[p.slotmap0 + i] < 0 || pl.slot_map[p.slotmap0 + i] >= n_gslots)
+                return fail("global slot", i, pl.slot_map[p.slotmap0 + i]);
+        for (int dir = 0; dir < 2; ++dir) {
+            const int s0 = dir ? p.rstage0 : p.stage0, ns = dir ? p.n_rstage : p.n_stage;
+            const int R = dir ? pl.Rr : pl.Rf;
+            if (s0 < 0 || s0 + ns > (int)pl.stages.size()) return fail("stage range", s0, ns);
+            const int op_first = pl.stages[s0].op0;
+            int op_total = 0;
+            for (int s = s0; s < s0 + ns; ++s) {
+                const FStage &st = pl.stages[s];
+                if (st.op0 != op_first + op_total) return fail("op contiguity", s, st.op0);
+                op_total += st.n_op;
+                // swizzled masks of thread and register bits must span all 2^K slots
+                uint32_t span = 0;
+                std::vector<uint32_t> basis;
+                for (int b = 0; b < K - R; ++b) basis.push_back(st.thr_sw[b]);
+                for (int k = 0; k < R; ++k) basis.push_back(st.reg_sw[k]);
+                // Gaussian elimination over GF(2)
+                std::vector<uint32_t> rows;
+                for (uint32_t v : basis) {
+                    for (uint32_t r : rows) v = std::min(v, v ^ r);
+                    if (!v) return fail("dependent tile bits", s, 0);
+                    rows.push_back(v);
+                    std::sort(rows.rbegin(), rows.rend());
+                    span |= v;
+                }
+                for (uint32_t v : basis)
+                    if (v >> K) return fail("swizzled mask range", s, (int)v);
+                for (int o = st.op0; o < st.op0 + st.n_op; ++o) {
+                    const FOp &op = pl.ops[o];
+                    const bool needs_k = op.type == OP_RY || op.type == OP_RX || op.type == OP_U3 ||
+                                         op.type == OP_RZ_REG || op.type == OP_CNOT;
+                    if (needs_k && (op.k < 0 || op.k >= R)) return fail("register bit", o, op.k);
+                    if ((op.rm0 >> R) || (op.rm1 >> R)) return fail("register mask", o, (int)op.rm0);
+                    if (op.type == OP_CNOT && op.rm0 == (1u << op.k)) return fail("control = target", o, op.k);
+                    if (op.gate < 0) return fail("gate index", o, op.gate);
+                    if (dir && op.lslot >= 0) {
+                        const int nv = op.type == OP_U3 ? 8 : 1;
+                        if (op.lslot + nv > p.n_lslots) return fail("local slot", o, op.lslot);
+                    }
+                }
+            }
+            if (op_total > kMaxPassOps) return fail("ops per pass", (int)j, op_total);
+        }
+    }
+    for (size_t h = 0; h < pl.hp.size(); ++h) {
+        const HPass &p = pl.hp[h];
+        std::string e = check_geom(p.high, p.n_high, p.nontile, p.n_nontile);
+        if (!e.empty()) return e;
+        if (p.group0 < 0 || p.group0 + p.n_group > (int)pl.hg.size()) return fail("group range", (int)h, p.group0);
+        for (int g = p.group0; g < p.group0 + p.n_group; ++g) {
+            const HGroup &G0 = pl.hg[g];
+            if (G0.xl >> K) return fail("tile flip mask", g, (int)G0.xl);
+            if (G0.term0 < 0 || G0.term0 + G0.n_term > (int)pl.ht.size()) return fail("term range", g, G0.term0);
+        }
+    }
+    (void)dbl;
+    return "";
+}
+
+static int occupancy_grid(int num_sms, int per_sm, uint64_t n_tiles) {
+    const uint64_t g = (uint64_t)num_sms * (uint64_t)std::max(per_sm, 1);
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(g, n_tiles));
+}
+
+// Pure host planning of the gate passes (no device work).  Returns nullptr with an
+// empty `err` when no fused schedule applies (n or the tile below 10 qubits, fusion
+// off), nullptr with `err` set when the plan fails validation.
+static Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
+                        int n_gslots, bool dbl, const vqg_options &opt, std::string &err) {
+    err.clear();
+    const int G = (int)gates.size();
+    const int Kmax = dbl ? 12 : 13;
+    int K = std::min(n, Kmax);
+    if (opt.tile_qubits > 0) K = std::min(opt.tile_qubits, n);
+    if (!opt.fusion || K < 10 || K > Kmax || G == 0) return nullptr;
+    Plan *pl = new Plan();
+    pl->K = K;
+    pl->L = dbl ? 3 : 4;
+    pl->Rf = dbl ? 4 : 5;
+    pl->Rr = dbl ? 3 : 4;
+    pl->n_tiles = 1ull << (n - K);
+    const int L = pl->L;
+    std::vector<int> rem(G), applied, left;
+    for (int i = 0; i < G; ++i) rem[i] = i;
+    while (!rem.empty()) {
+        std::vector<int> high = choose_high(gates, rem, n, K, L);
+        TileMap tm = make_tilemap(n, K, L, high);
+        std::vector<char> inS(n, 0);
+        for (int q = 0; q < n; ++q) inS[q] = tm.pos_of[q] >= 0;
+        greedy(gates, rem, inS, n, kMaxPassOps, kMaxPassSlots, applied, left);
+        FPass p;
+        std::memset(&p, 0, sizeof p);
+        p.n_high = (int)high.size();
+        for (size_t i = 0; i < high.size(); ++i) p.high[i] = high[i];
+        for (int q = 0; q < n; ++q)
+            if (tm.pos_of[q] < 0) p.nontile[p.n_nontile++] = q;
+        p.from_zero = pl->passes.empty() ? 1 : 0;
+        p.n_gates = (int)applied.size();
+        int nls;
+        build_stages(*pl, gates, slot_base, n, tm, applied, pl->Rf, dbl, false, nls, p.stage0, p.n_stage);
+        std::vector<int> rseq(applied.rbegin(), applied.rend());
+        p.slotmap0 = (int)pl->slot_map.size();
+        build_stages(*pl, gates, slot_base, n, tm, rseq, pl->Rr, dbl, true, p.n_lslots, p.rstage0, p.n_rstage);
+        pl->passes.push_back(p);
+        rem.swap(left);
+    }
+    err = validate_plan(*pl, n, n_gslots, dbl);
+    if (!err.empty()) {
+        delete pl;
+        return nullptr;
+    }
+    pl->ckpt_of_pass.assign(pl->passes.size(), -1);
+    return pl;
+}
+
 int Circuit::build_plan() {
-    plan_ok = false;
-    ham_plan_ok = false;
+    // gate plan once; Hamiltonian plan whenever the Hamiltonian changes
+    if (!plan) {
+        plan_ok = false;
+        std::string err;
+        Plan *pl = plan_gates(n, gates, slot_base, n_gslots, dbl, opt, err);
+        if (!pl) {
+            if (!err.empty()) return set_error(VQG_ERR_UNSUPPORTED, "%s", err.c_str());
+            return VQG_OK;  // no fused schedule for this size: one kernel per gate
+        }
+        pl->grid_fwd = occupancy_grid(num_sms, 2, pl->n_tiles);
+        int st;
+        auto up = [&](void **d, const void *h, size_t bytes) -> int {
+            int s2 = dalloc(d, bytes);
+            if (s2) return s2;
+            if (bytes && cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+                return set_error(VQG_ERR_CUDA, "plan upload failed");
+            return VQG_OK;
+        };
+        plan = pl;
+        if ((st = up((void **)&pl->d_passes, pl->passes.data(), sizeof(FPass) * pl->passes.size()))) return st;
+        if ((st = up((void **)&pl->d_stages, pl->stages.data(), sizeof(FStage) * pl->stages.size()))) return st;
+        if ((st = up((void **)&pl->d_ops, pl->ops.data(), sizeof(FOp) * std::max<size_t>(pl->ops.size(), 1)))) return st;
+        if ((st = up((void **)&pl->d_slot_map, pl->slot_map.data(), sizeof(int) * std::max<size_t>(pl->slot_map.size(), 1)))) return st;
+        if (!dbl && (st = dalloc((void **)&pl->d_mats_f, sizeof(float) * 8 * std::max(G, 1)))) return st;
+        plan_ok = true;
+    }
+    if (plan && has_ham) return build_ham_plan();
     return VQG_OK;
 }
 
-void Circuit::free_plan() {}
+// Hamiltonian passes: greedy set cover of the groups' flip masks by tiles (the low L
+// qubits are always inside; each pass adds the groups whose high flip bits fit).
+static void plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
+                             const std::vector<PauliTerm> &host_terms) {
+    pl->hp.clear();
+    pl->hg.clear();
+    pl->ht.clear();
+    const int K = pl->K, L = pl->L;
+    const uint64_t lowmask = (1ull << L) - 1ull;
+    std::vector<int> rem;
+    for (size_t g = 0; g < ham.size(); ++g) rem.push_back((int)g);
+    // the diagonal group (x = 0) is group 0 (ordered map) and goes in the first pass
+    bool first = true;
+    while (!rem.empty()) {
+        uint64_t S = 0;
+        std::vector<char> chosen(ham.size(), 0);
+        auto high_of = [&](int g) { return ham[g].x & ~lowmask; };
+        while (true) {
+            int best = -1, best_new = 1 << 30, best_cov = -1;
+            for (int g : rem) {
+                if (chosen[g]) continue;
+                const uint64_t h = high_of(g);
+                if (__builtin_popcountll(S | h) > K - L) continue;
+                const int nw = __builtin_popcountll(h & ~S);
+                const uint64_t cand = S | h;
+                int cov = 0;
+                for (int g2 : rem) cov += ((high_of(g2) & ~cand) == 0);
+                if (nw < best_new || (nw == best_new && cov > best_cov)) best = g, best_new = nw, best_cov = cov;
+            }
+            if (best < 0) break;
+            S |= high_of(best);
+            for (int g2 : rem)
+                if ((high_of(g2) & ~S) == 0) chosen[g2] = 1;
+        }
+        // fill the tile's high set: S's qubits, then the lowest others
+        std::vector<int> high;
+        for (int q = L; q < n; ++q)
+            if ((S >> q) & 1) high.push_back(q);
+        for (int q = L; q < n && (int)high.size() < K - L; ++q)
+            if (!((S >> q) & 1)) high.push_back(q), S |= 1ull << q;
+        std::sort(high.begin(), high.end());
+        TileMap tm = make_tilemap(n, K, L, high);
+        HPass hp;
+        std::memset(&hp, 0, sizeof hp);
+        hp.n_high = (int)high.size();
+        for (size_t i = 0; i < high.size(); ++i) hp.high[i] = high[i];
+        for (int q = 0; q < n; ++q)
+            if (tm.pos_of[q] < 0) hp.nontile[hp.n_nontile++] = q;
+        hp.group0 = (int)pl->hg.size();
+        hp.first = first ? 1 : 0;
+        hp.eslot = (int)pl->hp.size();
+        std::vector<int> next;
+        for (int g : rem) {
+            if (!chosen[g]) {
+                next.push_back(g);
+                continue;
+            }
+            const HamGroup &G0 = ham[g];
+            HGroup hg;
+            std::memset(&hg, 0, sizeof hg);
+            hg.xg = G0.x;
+            uint32_t xl = 0;
+            for (int q = 0; q < n; ++q)
+                if ((G0.x >> q) & 1) xl |= 1u << tm.pos_of[q];
+            hg.xl = xl;
+            hg.term0 = (int)pl->ht.size();
+            hg.n_term = G0.count;
+            for (int k = 0; k < G0.count; ++k) {
+                const PauliTerm &t = host_terms[G0.first + k];
+                HTerm h;
+                h.z = t.z;
+                const double sg = (__builtin_popcountll(G0.x & t.z) & 1) ? -1.0 : 1.0;
+                h.wr = sg * t.wr;
+                h.wi = sg * t.wi;
+                h.fr = (float)h.wr;
+                h.fi = (float)h.wi;
+                pl->ht.push_back(h);
+            }
+            pl->hg.push_back(hg);
+        }
+        hp.n_group = (int)pl->hg.size() - hp.group0;
+        pl->hp.push_back(hp);
+        rem.swap(next);
+        first = false;
+    }
+    if (pl->hp.empty()) {  // no terms at all: one pass that writes lambda = 0
+        HPass hp;
+        std::memset(&hp, 0, sizeof hp);
+        std::vector<int> high;
+        for (int q = L; q < n && (int)high.size() < K - L; ++q) high.push_back(q);
+        TileMap tm = make_tilemap(n, K, L, high);
+        hp.n_high = (int)high.size();
+        for (size_t i = 0; i < high.size(); ++i) hp.high[i] = high[i];
+        for (int q = 0; q < n; ++q)
+            if (tm.pos_of[q] < 0) hp.nontile[hp.n_nontile++] = q;
+        hp.first = 1;
+        pl->hp.push_back(hp);
+    }
+}
 
-int Circuit::issue_forward_fused(bool) { return set_error(VQG_ERR_UNSUPPORTED, "fused forward not built"); }
-int Circuit::issue_hamiltonian_fused() { return set_error(VQG_ERR_UNSUPPORTED, "fused H not built"); }
-int Circuit::issue_reverse_fused() { return set_error(VQG_ERR_UNSUPPORTED, "fused reverse not built"); }
+int Circuit::build_ham_plan() {
+    Plan *pl = plan;
+    ham_plan_ok = false;
+    plan_hamiltonian(pl, n, ham, host_terms);
+    {
+        const std::string err = validate_plan(*pl, n, n_gslots, dbl);
+        if (!err.empty()) return set_error(VQG_ERR_UNSUPPORTED, "%s", err.c_str());
+    }
+    if ((int)pl->hp.size() > n_eslots) {
+        n_eslots = (int)pl->hp.size();
+        int st = ensure_partials();
+        if (st) return st;
+    }
+    dfree(pl->d_hp);
+    dfree(pl->d_hg);
+    dfree(pl->d_ht);
+    pl->d_hp = nullptr;
+    pl->d_hg = nullptr;
+    pl->d_ht = nullptr;
+    int st;
+    if ((st = dalloc((void **)&pl->d_hp, sizeof(HPass) * pl->hp.size()))) return st;
+    if ((st = dalloc((void **)&pl->d_hg, sizeof(HGroup) * std::max<size_t>(pl->hg.size(), 1)))) return st;
+    if ((st = dalloc((void **)&pl->d_ht, sizeof(HTerm) * std::max<size_t>(pl->ht.size(), 1)))) return st;
+    cudaMemcpy(pl->d_hp, pl->hp.data(), sizeof(HPass) * pl->hp.size(), cudaMemcpyHostToDevice);
+    if (!pl->hg.empty()) cudaMemcpy(pl->d_hg, pl->hg.data(), sizeof(HGroup) * pl->hg.size(), cudaMemcpyHostToDevice);
+    if (!pl->ht.empty()) cudaMemcpy(pl->d_ht, pl->ht.data(), sizeof(HTerm) * pl->ht.size(), cudaMemcpyHostToDevice);
+    if (cudaGetLastError() != cudaSuccess) return set_error(VQG_ERR_CUDA, "Hamiltonian plan upload failed");
+    ham_plan_ok = true;
+    return VQG_OK;
+}
+
+void Circuit::free_plan() {
+    delete plan;
+    plan = nullptr;
+}
+
+// Checkpoints of the fused schedule sit at pass boundaries: the output of pass j is
+// stored when at least `interval` gates have passed since the previous one (never the
+// last pass: its output is psi itself).
+std::vector<int> Circuit::fused_checkpoint_passes(int interval) const {
+    std::vector<int> want;
+    int since = 0;
+    for (size_t j = 0; j + 1 < plan->passes.size(); ++j) {
+        since += plan->passes[j].n_gates;
+        if (since >= interval) want.push_back((int)j), since = 0;
+    }
+    return want;
+}
+
+void Circuit::set_fused_checkpoint(int pass, int k) { plan->ckpt_of_pass[pass] = k; }
+
+int Circuit::issue_forward_fused(bool with_ckpt) {
+    Plan *pl = plan;
+    const void *mats = dbl ? (const void *)d_mats : (const void *)pl->d_mats_f;
+    const void *in = psi;
+    for (size_t j = 0; j < pl->passes.size(); ++j) {
+        const int k = with_ckpt ? pl->ckpt_of_pass[j] : -1;
+        void *out = k >= 0 ? ckpt_buf[k] : psi;
+        prof_begin(FAM_FWD_FUSED);
+        launch_fused_fwd(dbl, pl->K, in, out, pl->d_passes, (int)j, pl->d_stages, pl->d_ops, mats,
+                         pl->n_tiles, pl->grid_fwd, stream);
+        prof_end();
+        in = out;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "fused forward launch: %s", cudaGetErrorString(e));
+    return VQG_OK;
+}
+
+int Circuit::issue_hamiltonian_fused() {
+    Plan *pl = plan;
+    for (size_t h = 0; h < pl->hp.size(); ++h) {
+        prof_begin(FAM_HAM_FUSED);
+        launch_fused_ham(dbl, pl->K, psi, lam, pl->d_hp, (int)h, pl->d_hg, pl->d_ht, pl->n_tiles,
+                         d_partials, nb, stream);
+        prof_end();
+    }
+    e_used = (int)pl->hp.size();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "fused Hamiltonian launch: %s", cudaGetErrorString(e));
+    return VQG_OK;
+}
+
+int Circuit::issue_reverse_fused() {
+    Plan *pl = plan;
+    const void *mats = dbl ? (const void *)d_mats : (const void *)pl->d_mats_f;
+    double *gpart = d_partials + (size_t)n_eslots * nb;
+    for (int j = (int)pl->passes.size() - 1; j >= 0; --j) {
+        const int k = pl->ckpt_of_pass[j];
+        const void *src = k >= 0 ? ckpt_buf[k] : psi;  // restart phi from the stored state
+        prof_begin(FAM_ADJ_FUSED);
+        launch_fused_rev(dbl, pl->K, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops,
+                         pl->d_slot_map, mats, pl->n_tiles, gpart, nb, stream);
+        prof_end();
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "fused reverse launch: %s", cudaGetErrorString(e));
+    return VQG_OK;
+}
+
+float *Circuit::mats_f() const { return plan ? plan->d_mats_f : nullptr; }
 
 void Circuit::fill_plan_info(vqg_plan_info *info) const {
     const bool fused = opt.fusion && plan_ok;
-    info->forward_passes = fused ? 0 : G;
-    info->hamiltonian_passes = (int)ham.size();
-    info->reverse_passes = fused ? 0 : G;
-    info->checkpoints = (int)ckpt_pos.size();
-    info->tile_qubits = 0;
+    info->forward_passes = fused ? (int)plan->passes.size() : G;
+    info->hamiltonian_passes = (fused && ham_plan_ok) ? (int)plan->hp.size() : (int)ham.size();
+    info->reverse_passes = fused ? (int)plan->passes.size() : G;
+    int nck = 0;
+    if (fused) {
+        for (int k : plan->ckpt_of_pass) nck += k >= 0;
+    } else {
+        nck = (int)ckpt_pos.size();
+    }
+    info->checkpoints = nck;
+    info->tile_qubits = fused ? plan->K : 0;
     info->hamiltonian_groups = (int)ham.size();
-    info->launches_per_gradient = 1 + 1 + G + (int)ckpt_pos.size() + (int)ham.size() + G + 2;
+    info->launches_per_gradient = 1 + info->forward_passes + info->hamiltonian_passes + info->reverse_passes + 2 +
+                                  (fused ? 0 : 1 + nck);
+}
+
+// Group Pauli terms by flip mask x (one pass over pairs (j, j^x) serves a group);
+// each term keeps its z mask and w = coef * i^{popcount(x & z)}.  The diagonal group
+// (x = 0) always exists and comes first.
+int group_pauli_terms(int n, int n_terms, const uint64_t *x_mask, const uint64_t *z_mask,
+                      const double *coef, std::vector<HamGroup> &ham, std::vector<PauliTerm> &flat) {
+    if (n_terms < 0 || (n_terms > 0 && (!x_mask || !z_mask || !coef)))
+        return set_error(VQG_ERR_INVALID, "bad Hamiltonian arrays");
+    const uint64_t lim = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+    std::map<uint64_t, std::vector<PauliTerm>> groups;
+    groups[0];
+    for (int t = 0; t < n_terms; ++t) {
+        if ((x_mask[t] & ~lim) || (z_mask[t] & ~lim))
+            return set_error(VQG_ERR_INVALID, "term %d: mask has bits >= n", t);
+        if (!std::isfinite(coef[t])) return set_error(VQG_ERR_INVALID, "term %d: coefficient not finite", t);
+        const int ny = __builtin_popcountll(x_mask[t] & z_mask[t]) & 3;
+        PauliTerm p;
+        p.z = z_mask[t];
+        p.wr = (ny == 0) ? coef[t] : (ny == 2 ? -coef[t] : 0.0);
+        p.wi = (ny == 1) ? coef[t] : (ny == 3 ? -coef[t] : 0.0);
+        groups[x_mask[t]].push_back(p);
+    }
+    ham.clear();
+    flat.clear();
+    for (auto &kv : groups) {
+        HamGroup g;
+        g.x = kv.first;
+        g.first = (int)flat.size();
+        g.count = (int)kv.second.size();
+        flat.insert(flat.end(), kv.second.begin(), kv.second.end());
+        ham.push_back(g);
+    }
+    return VQG_OK;
 }
 
 }  // namespace vqg
+
+// Host-only planning of a circuit and Hamiltonian: the same schedule a vqg_circuit
+// would use, validated, without touching a GPU.
+extern "C" int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype,
+                                const vqg_options *opt_in, int n_terms, const uint64_t *x_mask,
+                                const uint64_t *z_mask, const double *coef, vqg_plan_info *info) {
+    using namespace vqg;
+    if (!info) return set_error(VQG_ERR_INVALID, "info is NULL");
+    std::memset(info, 0, sizeof *info);
+    int st = vqg_validate_circuit(n_qubits, gates, n_gates, n_params, dtype);
+    if (st) return st;
+    vqg_options opt;
+    vqg_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    const bool dbl = dtype == VQG_C128;
+    std::vector<vqg_gate> gv(gates, gates + n_gates);
+    std::vector<int> slot_base(std::max(n_gates, 1), 0);
+    int n_gslots = 0;
+    for (int i = 0; i < n_gates; ++i) {
+        slot_base[i] = n_gslots;
+        n_gslots += red_values(gv[i].kind);
+    }
+    std::vector<HamGroup> ham;
+    std::vector<PauliTerm> flat;
+    if ((st = group_pauli_terms(n_qubits, n_terms, x_mask, z_mask, coef, ham, flat))) return st;
+    std::string err;
+    Plan *pl = plan_gates(n_qubits, gv, slot_base, n_gslots, dbl, opt, err);
+    if (!pl) {
+        if (!err.empty()) return set_error(VQG_ERR_UNSUPPORTED, "%s", err.c_str());
+        info->forward_passes = n_gates;
+        info->reverse_passes = n_gates;
+        info->hamiltonian_passes = (int)ham.size();
+        info->hamiltonian_groups = (int)ham.size();
+        return VQG_OK;
+    }
+    plan_hamiltonian(pl, n_qubits, ham, flat);
+    err = validate_plan(*pl, n_qubits, n_gslots, dbl);
+    if (!err.empty()) {
+        delete pl;
+        return set_error(VQG_ERR_UNSUPPORTED, "%s", err.c_str());
+    }
+    info->forward_passes = (int)pl->passes.size();
+    info->reverse_passes = (int)pl->passes.size();
+    info->hamiltonian_passes = (int)pl->hp.size();
+    info->hamiltonian_groups = (int)ham.size();
+    info->tile_qubits = pl->K;
+    int fs = 0, rs = 0;
+    for (const FPass &p : pl->passes) fs += p.n_stage, rs += p.n_rstage;
+    info->reserved[0] = fs;  // forward register stages
+    info->reserved[1] = rs;  // reverse register stages
+    info->launches_per_gradient = 1 + 2 * info->forward_passes + info->hamiltonian_passes + 2;
+    delete pl;
+    return VQG_OK;
+}

@@ -12,7 +12,9 @@
 
 namespace vqg {
 
+struct Plan;
 int set_error(int status, const char *fmt, ...);
+int vqg_validate_circuit(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype);
 
 enum Family {
     FAM_INIT = 0, FAM_TABLE, FAM_FWD_GATE, FAM_FWD_FUSED, FAM_HAM_DIAG, FAM_HAM_GROUP,
@@ -24,6 +26,9 @@ struct HamGroup {
     uint64_t x;
     int first, count;
 };
+
+int group_pauli_terms(int n, int n_terms, const uint64_t *x_mask, const uint64_t *z_mask,
+                      const double *coef, std::vector<HamGroup> &ham, std::vector<PauliTerm> &flat);
 
 struct PendingEvent {
     int fam;
@@ -62,12 +67,13 @@ struct Circuit {
     // Hamiltonian
     bool has_ham = false;
     std::vector<HamGroup> ham;
+    std::vector<PauliTerm> host_terms;
     PauliTerm *d_terms = nullptr;
     int n_terms = 0;
+    int e_used = 1;  // energy partial slots written by the last Hamiltonian application
 
     // fused plan (engine.cu)
     bool plan_ok = false, ham_plan_ok = false;
-    void *plan_dev = nullptr;  // opaque device-side schedule
     struct Plan *plan = nullptr;
 
     // graphs
@@ -86,7 +92,7 @@ struct Circuit {
     void dfree(void *p);
     int ensure_partials();
     int plan_checkpoints();
-    int set_groups(const std::map<uint64_t, std::vector<PauliTerm>> &groups);
+    int set_groups(const std::vector<HamGroup> &groups, const std::vector<PauliTerm> &flat);
 
     int issue_table(const double *theta_dev, int shift_gate, int shift_slot, double shift);
     int issue_forward(bool with_ckpt);
@@ -98,7 +104,11 @@ struct Circuit {
 
     // fused path (engine.cu)
     int build_plan();
+    int build_ham_plan();
     void free_plan();
+    std::vector<int> fused_checkpoint_passes(int interval) const;
+    void set_fused_checkpoint(int pass, int k);
+    float *mats_f() const;
     int issue_forward_fused(bool with_ckpt);
     int issue_hamiltonian_fused();
     int issue_reverse_fused();

@@ -1,0 +1,98 @@
+// Plan records of the tile-fused sweeps, shared by the host planner (engine.cu) and
+// the kernels (k_fused.cu).
+//
+// A tile is 2^K amplitudes: the L lowest qubits (contiguous 128-byte rows of the
+// state) plus K-L chosen "high" qubits; the other n-K qubits are fixed per tile.  One
+// pass streams every tile through shared memory once and applies a run of gates
+// whose non-diagonal qubits lie in the tile (diagonal gates and CNOT controls can
+// sit anywhere: their index bits are known).  Inside a pass, stages gather 2^R
+// amplitudes per thread into registers (R "register qubits"), apply every gate of
+// the stage there, and scatter back.
+#pragma once
+
+#include <stdint.h>
+
+namespace vqg {
+
+constexpr int kMaxHigh = 24;
+constexpr int kMaxNontile = 40;
+constexpr int kMaxThreadBits = 12;
+constexpr int kMaxRegBits = 5;
+constexpr int kMaxPassOps = 256;
+constexpr int kMaxPassStages = 64;
+constexpr int kMaxPassSlots = 256;
+
+enum FOpType : int16_t {
+    OP_RY = 0,      // real rotation on register bit k
+    OP_RX = 1,      // RX on register bit k (complex matrix)
+    OP_U3 = 2,      // general 2x2 on register bit k (three parameters)
+    OP_RZ_REG = 3,  // diagonal phase on register bit k
+    OP_RZ_THR = 4,  // diagonal phase on a thread- or tile-level bit (mask g0)
+    OP_CZ = 5,      // sign where both bits are set (each register mask or global mask)
+    OP_CNOT = 6     // swap on target register bit k where the control is set
+};
+
+struct FPass {
+    int32_t high[kMaxHigh];        // global qubit at tile position L + i
+    int32_t nontile[kMaxNontile];  // global qubits outside the tile, ascending
+    int32_t n_high, n_nontile;
+    int32_t stage0, n_stage;       // forward stages
+    int32_t rstage0, n_rstage;     // reverse stages
+    int32_t n_lslots;              // reverse: reduction values accumulated by this pass
+    int32_t slotmap0;              // reverse: first entry of this pass in the slot map
+    int32_t from_zero;             // forward: the input is |0...0> (nothing to load)
+    int32_t n_gates;               // gates applied by this pass
+};
+
+struct FStage {
+    uint64_t thr_g[kMaxThreadBits];  // global mask of thread bit b
+    uint16_t thr_sw[kMaxThreadBits]; // swizzled tile-local mask of thread bit b
+    uint16_t reg_sw[kMaxRegBits + 3];// swizzled tile-local mask of register bit k
+    int32_t op0, n_op;
+};
+
+struct FOp {
+    int16_t type, k;
+    int32_t gate;
+    uint32_t rm0, rm1;  // register-index masks (0: that qubit is not a register bit)
+    int32_t lslot;      // reverse: first local reduction value (-1: none)
+    uint64_t g0, g1;    // global masks of the diagonal / control qubits
+    int32_t gslot;      // reverse: first global gate slot
+    int32_t pad;
+};
+
+// Hamiltonian tile pass: groups whose flip mask lies inside the tile.
+struct HPass {
+    int32_t high[kMaxHigh];
+    int32_t nontile[kMaxNontile];
+    int32_t n_high, n_nontile;
+    int32_t group0, n_group;
+    int32_t first;  // writes lambda (no accumulate)
+    int32_t eslot;  // energy partial slot
+};
+
+struct HGroup {
+    uint64_t xg;     // global flip mask
+    uint32_t xl;     // tile-local flip mask
+    int32_t term0, n_term;
+    int32_t pad;
+};
+
+// Term of a group, evaluated at the source index j^x: w' = w * (-1)^{popcount(x & z)}.
+struct HTerm {
+    uint64_t z;
+    double wr, wi;
+    float fr, fi;  // the same weight rounded to FP32 (complex64 kernels)
+};
+
+// Swizzle of a tile-local amplitude index into its shared-memory slot: XOR-folds the
+// bits above the 128-byte row into the position within the row, so that 16 (8) lanes
+// touching indices whose varying bits have distinct residues mod 4 (mod 3) hit
+// distinct banks.  Linear over GF(2); keeps rows intact.
+template <int AMP_BYTES>
+__host__ __device__ inline uint32_t swz(uint32_t t) {
+    if (AMP_BYTES == 8) return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12) ^ (t >> 16)) & 15u);
+    return t ^ (((t >> 3) ^ (t >> 6) ^ (t >> 9) ^ (t >> 12) ^ (t >> 15)) & 7u);
+}
+
+}  // namespace vqg

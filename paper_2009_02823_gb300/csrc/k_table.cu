@@ -9,8 +9,8 @@ namespace vqg {
 // shift_gate/shift_slot add `shift` to one parameter slot of one occurrence (the
 // per-occurrence parameter-shift baseline).
 __global__ void k_build_mats(const double *__restrict__ theta, const DevGate *__restrict__ gates,
-                             int G, double *__restrict__ mats, int shift_gate, int shift_slot,
-                             double shift) {
+                             int G, double *__restrict__ mats, float *__restrict__ mats_f,
+                             int shift_gate, int shift_slot, double shift) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G) return;
     DevGate g = gates[i];
@@ -53,13 +53,17 @@ __global__ void k_build_mats(const double *__restrict__ theta, const DevGate *__
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) m[k] = r[k];
+    if (mats_f) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mats_f[8 * (size_t)i + k] = (float)r[k];
+    }
 }
 
 void launch_build_mats(const double *theta, const DevGate *gates, int G, double *mats,
-                       int shift_gate, int shift_slot, double shift, cudaStream_t s) {
+                       float *mats_f, int shift_gate, int shift_slot, double shift, cudaStream_t s) {
     if (G <= 0) return;
-    k_build_mats<<<(G + 127) / 128, 128, 0, s>>>(theta, gates, G, mats, shift_gate, shift_slot,
-                                                 shift);
+    k_build_mats<<<(G + 127) / 128, 128, 0, s>>>(theta, gates, G, mats, mats_f, shift_gate,
+                                                 shift_slot, shift);
 }
 
 template <typename T>

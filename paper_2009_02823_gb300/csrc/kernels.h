@@ -19,8 +19,9 @@ struct Occurrence {
 };
 
 // --- gate table and result assembly (k_table.cu)
+// mats: FP64 table (8 doubles per gate); mats_f (nullable): the same rounded to FP32.
 void launch_build_mats(const double *theta, const DevGate *gates, int G, double *mats,
-                       int shift_gate, int shift_slot, double shift, cudaStream_t s);
+                       float *mats_f, int shift_gate, int shift_slot, double shift, cudaStream_t s);
 void launch_init_zero(void *psi, int n, bool dbl, int nb, cudaStream_t s);
 void launch_reduce_slots(const double *partials, int n_slots, int nb, double *red, cudaStream_t s);
 // E = sum red_e[0 .. e_count); grad[p] from the reduced reverse-sweep values

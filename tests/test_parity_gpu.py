@@ -128,15 +128,46 @@ def test_gpu_parameter_shift_baseline(dtype):
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("interval", [1, 3, 7, 64])
 def test_checkpoint_restarts(dtype, interval):
-    """Forward-state checkpoints every `interval` gates restart phi in the reverse sweep;
-    the result is the same gradient."""
-    w = W.config(3, n=12, layers=4)
+    """Forward-state checkpoints every `interval` gates (per-gate schedule) or at pass
+    boundaries (fused schedule) restart phi in the reverse sweep; same gradient."""
+    w = W.config(3, n=13, layers=4)
     e_ref, g_ref = _oracle(w.n, w.gates, w.theta, w.n_params, w.terms)
     for mode in MODES:
-        with _circ(w.n, w.gates, w.n_params, dtype, w.terms, checkpoint_interval=interval, **mode) as c:
-            assert c.plan()["checkpoints"] == (w.n_gates - 1) // interval
+        with _circ(w.n, w.gates, w.n_params, dtype, w.terms, checkpoint_interval=interval,
+                   tile_qubits=10, **mode) as c:
+            info = c.plan()
+            if mode["fusion"]:
+                assert info["forward_passes"] > 1
+                assert 1 <= info["checkpoints"] <= info["forward_passes"] - 1
+            else:
+                assert info["checkpoints"] == (w.n_gates - 1) // interval
             e, g = c.energy_and_gradient(w.theta)
             assert_parity(dtype, e, g, e_ref, g_ref, f"ckpt={interval} {mode}")
+
+
+@pytest.mark.parametrize("dtype,K", [("c64", 10), ("c64", 11), ("c64", 12), ("c64", 13),
+                                     ("c128", 10), ("c128", 11), ("c128", 12)])
+@pytest.mark.parametrize("case", ["cfg2", "cfg3", "cfg5", "random"])
+def test_fused_tile_sizes(case, dtype, K):
+    """Every compiled tile size, with several tiles and several passes (n = 14)."""
+    n = 14
+    if case == "random":
+        rng = np.random.default_rng(77 + K)
+        gates, P = W.random_circuit(rng, n, 120, share_params=True)
+        theta = rng.uniform(0, 2 * np.pi, P)
+        terms = W.random_paulis(rng, n, 25, 4)
+    else:
+        w = W.config(int(case[3]), n=n, layers=3)
+        gates, P, theta, terms = w.gates, w.n_params, w.theta, w.terms
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, dtype, terms, tile_qubits=K) as c:
+        info = c.plan()
+        assert info["tile_qubits"] == K and info["forward_passes"] >= 1
+        e, g = c.energy_and_gradient(theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, f"{case} K={K}")
+        assert energy_err(c.energy(theta), e_ref) <= TOL[dtype]
+        psi = c.get_state()
+        assert np.max(np.abs(psi - oracle.state(n, gates, theta))) <= (1e-12 if dtype == "c128" else 2e-5)
 
 
 def test_hamiltonian_can_change_between_calls():

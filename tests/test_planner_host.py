@@ -1,0 +1,57 @@
+"""The fused-schedule planner, run on the host through vqg_plan_dry_run (no GPU):
+every workload at full size and random circuits plan into passes whose every index
+(tile geometry, register/thread bits, op fields, reduction slots, Hamiltonian masks)
+passes the library's own bounds checks."""
+import numpy as np
+import pytest
+
+from paper_2009_02823_gb300 import binding as B
+from paper_2009_02823_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 5])
+def test_workloads_plan(cfg, dtype):
+    w = W.config(cfg)
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype)
+    assert info["tile_qubits"] == min(w.n, 13 if dtype == "c64" else 12)
+    assert 1 <= info["forward_passes"] <= w.n_gates
+    assert info["hamiltonian_passes"] >= 1
+    assert info["forward_stages"] >= info["forward_passes"]
+
+
+def test_n30_workload_pass_counts():
+    """The n=30 hardware-efficient ansatz (745 gates) runs in a handful of tile passes:
+    CZ brickwork is diagonal, so later layers slide into earlier passes."""
+    w = W.config(3)
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c64")
+    assert info["forward_passes"] <= 12
+    assert info["hamiltonian_passes"] <= 16
+    assert info["hamiltonian_groups"] > 100
+
+
+@pytest.mark.parametrize("K", [10, 11, 12, 13])
+@pytest.mark.parametrize("seed", range(6))
+def test_random_circuits_plan(seed, K):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(K, 22))
+    gates, P = W.random_circuit(rng, n, 300, share_params=True)
+    terms = W.random_paulis(rng, n, 60, 4)
+    for dtype in ("c64", "c128"):
+        if dtype == "c128" and K > 12:
+            continue
+        info = B.plan_dry_run(n, gates, P, terms, dtype, tile_qubits=K)
+        assert info["tile_qubits"] == K
+
+
+def test_small_n_uses_one_kernel_per_gate():
+    w = W.config(1, n=8, layers=2)
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c64")
+    assert info["tile_qubits"] == 0 and info["forward_passes"] == w.n_gates
+
+
+def test_dry_run_rejects_bad_input():
+    with pytest.raises(B.VqgError):
+        B.plan_dry_run(4, [("RX", 9, -1, (0, -1, -1))], 1, [], "c64")
+    with pytest.raises(B.VqgError):
+        B.plan_dry_run(4, [("RX", 0, -1, (0, -1, -1))], 1, [(1.0, ((5, "Z"),))], "c64")
