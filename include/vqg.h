@@ -82,7 +82,11 @@ typedef struct vqg_options {
     int32_t tile_qubits;         /* qubits per fused tile; 0 = autotuned                     */
     int32_t use_graph;           /* 1: replay the launch sequence from a CUDA graph          */
     int32_t max_checkpoint_mib;  /* cap on checkpoint memory; 0 = fit in free memory         */
-    int32_t reserved[11];
+    int32_t fwd_reg_qubits;      /* qubits held in registers per forward stage; 0 = default  */
+    int32_t rev_reg_qubits;      /* qubits held in registers per reverse stage; 0 = default  */
+    int32_t autotune;            /* 1: time candidate schedules on the first evaluation and
+                                    keep the fastest (see vqg_autotune)                     */
+    int32_t reserved[8];
 } vqg_options;
 
 typedef struct vqg_circuit vqg_circuit;
@@ -106,7 +110,8 @@ int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *x_mask,
                         const uint64_t *z_mask, const double *coef);
 
 /* All work of this circuit is issued on `stream` (a cudaStream_t; NULL = the library's
- * own stream).  The caller keeps the stream alive while the circuit uses it. */
+ * own non-blocking stream; pass cudaStreamLegacy, (void *)0x1, for the legacy default
+ * stream).  The caller keeps the stream alive while the circuit uses it. */
 int vqg_set_stream(vqg_circuit *c, void *stream);
 
 /* E(theta): forward sweep (Algorithm 1, line 2) then <psi|H|psi> with FP64 reduction.

@@ -41,7 +41,9 @@ class vqg_gate(ctypes.Structure):
 class vqg_options(ctypes.Structure):
     _fields_ = [("fusion", ctypes.c_int32), ("checkpoint_interval", ctypes.c_int32),
                 ("tile_qubits", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("max_checkpoint_mib", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("max_checkpoint_mib", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
+                ("rev_reg_qubits", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class vqg_plan_info(ctypes.Structure):
@@ -135,6 +137,18 @@ def pauli_masks(terms, n: int):
     return x, z, c
 
 
+CUDA_STREAM_LEGACY = 0x1
+
+
+def stream_handle(stream):
+    """cudaStream_t value for the C ABI: None -> NULL (library's own stream); a torch
+    stream or integer handle; handle 0 (the legacy default stream) -> cudaStreamLegacy."""
+    if stream is None:
+        return None
+    raw = getattr(stream, "cuda_stream", stream)
+    return CUDA_STREAM_LEGACY if int(raw) == 0 else int(raw)
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
@@ -144,7 +158,8 @@ class Circuit:
 
     def __init__(self, n: int, gates, n_params: int, dtype: str = "c64", *, fusion: bool = True,
                  checkpoint_interval: int = 0, tile_qubits: int = 0, use_graph: bool = False,
-                 max_checkpoint_mib: int = 0, stream=None):
+                 max_checkpoint_mib: int = 0, fwd_reg_qubits: int = 0, rev_reg_qubits: int = 0,
+                 autotune: bool = False, stream=None):
         L = lib()
         self.n, self.n_params, self.n_gates = n, n_params, len(gates)
         self.dtype = dtype
@@ -155,6 +170,9 @@ class Circuit:
         opt.tile_qubits = tile_qubits
         opt.use_graph = int(use_graph)
         opt.max_checkpoint_mib = max_checkpoint_mib
+        opt.fwd_reg_qubits = fwd_reg_qubits
+        opt.rev_reg_qubits = rev_reg_qubits
+        opt.autotune = int(autotune)
         self._gates = gate_array(gates)
         h = ctypes.c_void_p()
         _check(L.vqg_circuit_create(n, self._gates, len(gates), n_params, DTYPE[dtype],
@@ -183,9 +201,10 @@ class Circuit:
 
     # -- configuration
     def set_stream(self, stream):
-        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
-        raw = getattr(stream, "cuda_stream", stream)
-        _check(lib().vqg_set_stream(self._h, ctypes.c_void_p(raw or None)))
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (the library's
+        own stream).  A handle of 0 (torch's default stream) means the legacy default
+        stream and is passed as cudaStreamLegacy."""
+        _check(lib().vqg_set_stream(self._h, ctypes.c_void_p(stream_handle(stream))))
 
     def set_hamiltonian(self, terms):
         x, z, c = pauli_masks(terms, self.n)
@@ -269,14 +288,14 @@ def reverse_noalloc(n: int, dtype: str, gates, theta, n_params: int, phi_ptr: in
     if th.size == 0:
         th = np.zeros(1)
     arr = gate_array(gates)
-    raw = getattr(stream, "cuda_stream", stream)
     _check(lib().vqg_reverse_noalloc(n, DTYPE[dtype], arr, len(gates), _ptr(th), n_params,
                                      ctypes.c_void_p(phi_ptr), ctypes.c_void_p(lam_ptr),
-                                     ctypes.c_void_p(grad_ptr), ctypes.c_void_p(raw or None)))
+                                     ctypes.c_void_p(grad_ptr), ctypes.c_void_p(stream_handle(stream))))
 
 
 def plan_dry_run(n: int, gates, n_params: int, terms, dtype: str = "c64", *, fusion: bool = True,
-                 tile_qubits: int = 0, checkpoint_interval: int = 0) -> dict:
+                 tile_qubits: int = 0, checkpoint_interval: int = 0, fwd_reg_qubits: int = 0,
+                 rev_reg_qubits: int = 0) -> dict:
     """Host-only schedule of a circuit + Hamiltonian (vqg_plan_dry_run); no GPU needed."""
     L = lib()
     opt = vqg_options()
@@ -284,6 +303,8 @@ def plan_dry_run(n: int, gates, n_params: int, terms, dtype: str = "c64", *, fus
     opt.fusion = int(fusion)
     opt.tile_qubits = tile_qubits
     opt.checkpoint_interval = checkpoint_interval
+    opt.fwd_reg_qubits = fwd_reg_qubits
+    opt.rev_reg_qubits = rev_reg_qubits
     x, z, c = pauli_masks(terms, n)
     info = vqg_plan_info()
     arr = gate_array(gates)

@@ -22,13 +22,24 @@
 
 namespace vqg {
 
-void launch_fused_fwd(bool dbl, int K, const void *src, void *dst, const FPass *passes, int pi,
-                      const FStage *st, const FOp *ops, const void *mats, uint64_t n_tiles, int grid,
-                      cudaStream_t s);
-void launch_fused_rev(bool dbl, int K, const void *phi_src, void *phi_dst, void *lam,
-                      const FPass *passes, int pi, const FStage *st, const FOp *ops,
-                      const int *slot_map, const void *mats, uint64_t n_tiles, double *partials,
-                      int nb, cudaStream_t s);
+#define VQG_FWD_ARGS                                                                             \
+    int K, int R, const void *src, void *dst, const FPass *passes, int pi, const FStage *st,      \
+        const FOp *ops, const FDiag *dg, const FDItem *it, const void *mats, uint64_t n_tiles,    \
+        int grid, cudaStream_t s
+#define VQG_REV_ARGS                                                                             \
+    int K, int R, const void *phi_src, void *phi_dst, void *lam, const FPass *passes, int pi,     \
+        const FStage *st, const FOp *ops, const FDiag *dg, const FDItem *it, const int *slot_map, \
+        const void *mats, uint64_t n_tiles, double *partials, int nb, cudaStream_t s
+bool launch_fused_fwd_c64(VQG_FWD_ARGS);
+bool launch_fused_fwd_c128(VQG_FWD_ARGS);
+bool launch_fused_rev_c64(VQG_REV_ARGS);
+bool launch_fused_rev_c128(VQG_REV_ARGS);
+
+// Compiled (tile qubits, register qubits) variants; every one fits shared memory.
+static bool fused_supported(bool dbl, int K, int Rf, int Rr) {
+    if (!dbl) return K >= 10 && K <= 13 && (Rf == 4 || Rf == 5) && (Rr == 4 || (Rr == 3 && K <= 12));
+    return K >= 10 && K <= 12 && (Rf == 3 || Rf == 4) && (Rr == 3 || (Rr == 2 && K <= 11));
+}
 void launch_fused_ham(bool dbl, int K, const void *psi, void *lam, const HPass *hp, int pi,
                       const HGroup *groups, const HTerm *terms, uint64_t n_tiles, double *partials,
                       int nb, cudaStream_t s);
@@ -86,6 +97,8 @@ struct Plan {
     std::vector<FPass> passes;
     std::vector<FStage> stages;
     std::vector<FOp> ops;
+    std::vector<FDiag> diags;
+    std::vector<FDItem> items;
     std::vector<int> slot_map;
     std::vector<int> ckpt_of_pass;  // checkpoint index storing the output of pass j, or -1
     std::vector<HPass> hp;
@@ -94,6 +107,8 @@ struct Plan {
     FPass *d_passes = nullptr;
     FStage *d_stages = nullptr;
     FOp *d_ops = nullptr;
+    FDiag *d_diags = nullptr;
+    FDItem *d_items = nullptr;
     int *d_slot_map = nullptr;
     HPass *d_hp = nullptr;
     HGroup *d_hg = nullptr;
@@ -138,19 +153,30 @@ static std::vector<int> choose_high(const std::vector<vqg_gate> &gates, const st
     return high;
 }
 
-// Register stages of one pass over `seq` (gates in application order).  Emits stages
-// and ops into the plan; reverse stages carry reduction slots.
+// Register stages of one pass over `seq` (gates in application order).  Emits stages,
+// ops, diagonal blocks and their items into the plan; reverse stages carry reduction
+// slots.  Within a stage, diagonal gates (RZ, CZ) are gathered into diagonal blocks:
+// a diagonal gate joins the earliest block after the last op it does not commute
+// with, and a non-diagonal gate is placed before a trailing run of blocks it commutes
+// with.  Both moves only swap commuting gates.
+struct StageItem {
+    bool diag;
+    uint64_t nd, dq;            // non-diagonal / diagonal qubit masks
+    std::vector<int> gates;     // one gate, or the gates of a diagonal block
+    int n_rz = 0, n_cz = 0;
+};
+
 static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
                          int n, const TileMap &tm, const std::vector<int> &seq, int R, bool dbl,
-                         bool reverse, int &n_lslots, int &stage0, int &n_stage) {
+                         bool reverse, int &n_lslots, int &stage0, int &n_stage, int &diag0, int &n_diag) {
     stage0 = (int)pl.stages.size();
+    diag0 = (int)pl.diags.size();
     n_stage = 0;
     n_lslots = 0;
     const int K = tm.K;
     const int AB = dbl ? 16 : 8;
     std::vector<int> uns = seq, applied, left;
     while (!uns.empty()) {
-        // register positions: needed tile positions in order of first use
         std::vector<int> regs;
         std::vector<char> isreg(K, 0);
         for (int i : uns) {
@@ -163,13 +189,11 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             }
             if ((int)regs.size() == R) break;
         }
-        // pad with high tile positions, keeping low positions for the lanes
         for (int p = K - 1; p >= 0 && (int)regs.size() < R; --p)
             if (!isreg[p]) isreg[p] = 1, regs.push_back(p);
         std::vector<char> inS(n, 0);
         for (int p : regs) inS[tm.qubit_of[p]] = 1;
         greedy(gates, uns, inS, n, kMaxPassOps, kMaxPassSlots, applied, left);
-        // thread positions: lane bits with distinct residues (bank-conflict-free), then the rest
         const int NL = dbl ? 3 : 4, MOD = dbl ? 3 : 4;
         std::vector<int> thr;
         std::vector<char> used(K, 0);
@@ -186,12 +210,10 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
         std::memset(&st, 0, sizeof st);
         for (size_t b = 0; b < thr.size(); ++b) {
             st.thr_sw[b] = (uint16_t)(AB == 8 ? swz<8>(1u << thr[b]) : swz<16>(1u << thr[b]));
-            st.thr_g[b] = 1ull << tm.qubit_of[thr[b]];
+            st.thr_q[b] = (int8_t)tm.qubit_of[thr[b]];
         }
         for (int k = 0; k < R; ++k)
             st.reg_sw[k] = (uint16_t)(AB == 8 ? swz<8>(1u << regs[k]) : swz<16>(1u << regs[k]));
-        st.op0 = (int)pl.ops.size();
-        st.n_op = (int)applied.size();
         auto regbit = [&](int q) -> int {
             const int p = tm.pos_of[q];
             if (p < 0) return -1;
@@ -199,54 +221,124 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                 if (regs[k] == p) return k;
             return -1;
         };
+        // order the stage's gates into single ops and diagonal blocks
+        std::vector<StageItem> out;
         for (int i : applied) {
             const vqg_gate &g = gates[i];
+            const bool is_diag = g.kind == VQG_RZ || g.kind == VQG_CZ;
+            if (is_diag) {
+                const uint64_t dq = (1ull << g.q0) | (g.kind == VQG_CZ ? 1ull << g.q1 : 0ull);
+                int lim = -1;
+                for (int idx = (int)out.size() - 1; idx >= 0; --idx)
+                    if (!out[idx].diag && (out[idx].nd & dq)) { lim = idx; break; }
+                bool placed = false;
+                for (int idx = lim + 1; idx < (int)out.size() && !placed; ++idx) {
+                    StageItem &b = out[idx];
+                    if (!b.diag) continue;
+                    if (g.kind == VQG_RZ ? b.n_rz >= kMaxDiagRz : b.n_cz >= kMaxDiagCz) continue;
+                    b.gates.push_back(i);
+                    b.dq |= dq;
+                    (g.kind == VQG_RZ ? b.n_rz : b.n_cz)++;
+                    placed = true;
+                }
+                if (!placed) {
+                    StageItem b;
+                    b.diag = true;
+                    b.nd = 0;
+                    b.dq = dq;
+                    b.gates.push_back(i);
+                    (g.kind == VQG_RZ ? b.n_rz : b.n_cz) = 1;
+                    out.push_back(b);
+                }
+            } else {
+                StageItem it;
+                it.diag = false;
+                it.nd = 1ull << (g.kind == VQG_CNOT ? g.q1 : g.q0);
+                it.dq = g.kind == VQG_CNOT ? 1ull << g.q0 : 0ull;
+                it.gates.push_back(i);
+                size_t pos = out.size();
+                while (pos > 0 && out[pos - 1].diag && !(out[pos - 1].dq & it.nd)) --pos;
+                out.insert(out.begin() + pos, it);
+            }
+        }
+        st.op0 = (int)pl.ops.size();
+        for (const StageItem &it : out) {
             FOp op;
             std::memset(&op, 0, sizeof op);
-            op.gate = i;
             op.lslot = -1;
-            op.gslot = -1;
-            switch (g.kind) {
-            case VQG_RY: op.type = OP_RY; op.k = (int16_t)regbit(g.q0); break;
-            case VQG_RX: op.type = OP_RX; op.k = (int16_t)regbit(g.q0); break;
-            case VQG_U3: op.type = OP_U3; op.k = (int16_t)regbit(g.q0); break;
-            case VQG_RZ: {
-                const int k = regbit(g.q0);
-                if (k >= 0) op.type = OP_RZ_REG, op.k = (int16_t)k;
-                else op.type = OP_RZ_THR, op.g0 = 1ull << g.q0;
-                break;
-            }
-            case VQG_CZ: {
-                const int k0 = regbit(g.q0), k1 = regbit(g.q1);
-                op.type = OP_CZ;
-                if (k0 >= 0) op.rm0 = 1u << k0; else op.g0 = 1ull << g.q0;
-                if (k1 >= 0) op.rm1 = 1u << k1; else op.g1 = 1ull << g.q1;
-                break;
-            }
-            case VQG_CNOT: {
-                const int kc = regbit(g.q0);
-                op.type = OP_CNOT;
-                op.k = (int16_t)regbit(g.q1);
-                if (kc >= 0) op.rm0 = 1u << kc; else op.g0 = 1ull << g.q0;
-                break;
-            }
-            default: break;
-            }
-            if (reverse) {
-                const int nv = red_values(g.kind);
-                if (nv) {
-                    op.lslot = n_lslots;
-                    op.gslot = slot_base[i];
-                    for (int v = 0; v < nv; ++v) pl.slot_map.push_back(slot_base[i] + v);
-                    n_lslots += nv;
+            op.diag = -1;
+            op.cq = -1;
+            if (!it.diag) {
+                const int i = it.gates[0];
+                const vqg_gate &g = gates[i];
+                op.gate = i;
+                switch (g.kind) {
+                case VQG_RY: op.type = OP_RY; op.k = (int8_t)regbit(g.q0); break;
+                case VQG_RX: op.type = OP_RX; op.k = (int8_t)regbit(g.q0); break;
+                case VQG_U3: op.type = OP_U3; op.k = (int8_t)regbit(g.q0); break;
+                case VQG_CNOT: {
+                    const int kc = regbit(g.q0);
+                    op.type = OP_CNOT;
+                    op.k = (int8_t)regbit(g.q1);
+                    op.cq = -1;
+                    if (kc >= 0) op.rm0 = 1u << kc; else op.cq = (int8_t)g.q0;
+                    break;
                 }
+                default: break;
+                }
+                if (reverse) {
+                    const int nv = red_values(g.kind);
+                    if (nv) {
+                        op.lslot = (int16_t)n_lslots;
+                        for (int v = 0; v < nv; ++v) pl.slot_map.push_back(slot_base[i] + v);
+                        n_lslots += nv;
+                    }
+                }
+            } else {
+                op.type = OP_DIAG;
+                op.gate = -1;
+                op.cq = -1;
+                op.diag = (int16_t)((int)pl.diags.size() - diag0);
+                FDiag d;
+                std::memset(&d, 0, sizeof d);
+                d.item0 = (int)pl.items.size();
+                for (int pass_rz = 1; pass_rz >= 0; --pass_rz)  // RZ items first
+                    for (int i : it.gates) {
+                        const vqg_gate &g = gates[i];
+                        if ((g.kind == VQG_RZ) != (pass_rz == 1)) continue;
+                        FDItem x;
+                        std::memset(&x, 0, sizeof x);
+                        x.gate = i;
+                        x.lslot = -1;
+                        if (g.kind == VQG_RZ) {
+                            const int k = regbit(g.q0);
+                            if (k >= 0) x.type = DI_RZ_REG, x.k0 = (int16_t)k;
+                            else x.type = DI_RZ_THR, x.g0 = 1ull << g.q0;
+                            if (reverse) {
+                                x.lslot = n_lslots++;
+                                pl.slot_map.push_back(slot_base[i]);
+                            }
+                            d.n_rz++;
+                        } else {
+                            const int ka = regbit(g.q0), kb = regbit(g.q1);
+                            if (ka >= 0 && kb >= 0) x.type = DI_CZ_RR, x.k0 = (int16_t)ka, x.k1 = (int16_t)kb;
+                            else if (ka >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)ka, x.g0 = 1ull << g.q1;
+                            else if (kb >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)kb, x.g0 = 1ull << g.q0;
+                            else x.type = DI_CZ_TT, x.g0 = 1ull << g.q0, x.g1 = 1ull << g.q1;
+                        }
+                        pl.items.push_back(x);
+                    }
+                d.n_item = (int)pl.items.size() - d.item0;
+                pl.diags.push_back(d);
             }
             pl.ops.push_back(op);
         }
+        st.n_op = (int)pl.ops.size() - st.op0;
         pl.stages.push_back(st);
         ++n_stage;
         uns.swap(left);
     }
+    n_diag = (int)pl.diags.size() - diag0;
 }
 
 // Host-side check of every index a fused kernel derives from the plan: tile
@@ -312,21 +404,54 @@ static std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) 
                 }
                 for (uint32_t v : basis)
                     if (v >> K) return fail("swizzled mask range", s, (int)v);
+                for (int k = 0; k < K - R; ++k)
+                    if (st.thr_q[k] < 0 || st.thr_q[k] >= n) return fail("thread qubit", s, st.thr_q[k]);
                 for (int o = st.op0; o < st.op0 + st.n_op; ++o) {
                     const FOp &op = pl.ops[o];
-                    const bool needs_k = op.type == OP_RY || op.type == OP_RX || op.type == OP_U3 ||
-                                         op.type == OP_RZ_REG || op.type == OP_CNOT;
-                    if (needs_k && (op.k < 0 || op.k >= R)) return fail("register bit", o, op.k);
-                    if ((op.rm0 >> R) || (op.rm1 >> R)) return fail("register mask", o, (int)op.rm0);
+                    if (op.type < OP_RY || op.type > OP_DIAG) return fail("op type", o, op.type);
+                    if (op.type != OP_DIAG && (op.k < 0 || op.k >= R)) return fail("register bit", o, op.k);
+                    if (op.rm0 >> R) return fail("register mask", o, (int)op.rm0);
                     if (op.type == OP_CNOT && op.rm0 == (1u << op.k)) return fail("control = target", o, op.k);
-                    if (op.gate < 0) return fail("gate index", o, op.gate);
+                    if (op.type == OP_CNOT && !op.rm0 && (op.cq < 0 || op.cq >= n)) return fail("control qubit", o, op.cq);
+                    if (op.type != OP_DIAG && (op.gate < 0)) return fail("gate index", o, op.gate);
                     if (dir && op.lslot >= 0) {
                         const int nv = op.type == OP_U3 ? 8 : 1;
                         if (op.lslot + nv > p.n_lslots) return fail("local slot", o, op.lslot);
                     }
+                    if (op.type == OP_DIAG) {
+                        const int d0 = dir ? p.rdiag0 : p.diag0, nd = dir ? p.n_rdiag : p.n_diag;
+                        if (op.diag < 0 || op.diag >= nd) return fail("diagonal block", o, op.diag);
+                        const FDiag &D = pl.diags[d0 + op.diag];
+                        if (D.n_rz > kMaxDiagRz || D.n_rz > D.n_item) return fail("block RZ count", o, D.n_rz);
+                        if (D.item0 < 0 || D.item0 + D.n_item > (int)pl.items.size()) return fail("item range", o, D.item0);
+                        for (int i = D.item0; i < D.item0 + D.n_item; ++i) {
+                            const FDItem &x = pl.items[i];
+                            const bool rz = x.type == DI_RZ_REG || x.type == DI_RZ_THR;
+                            if ((i - D.item0 < D.n_rz) != rz) return fail("item order", i, x.type);
+                            if (x.type < DI_RZ_REG || x.type > DI_CZ_TT) return fail("item type", i, x.type);
+                            const bool k0 = x.type == DI_RZ_REG || x.type == DI_CZ_RR || x.type == DI_CZ_RT;
+                            if (k0 && (x.k0 < 0 || x.k0 >= R)) return fail("item bit", i, x.k0);
+                            if (x.type == DI_CZ_RR && (x.k1 < 0 || x.k1 >= R || x.k1 == x.k0)) return fail("item bit 2", i, x.k1);
+                            if (rz && (x.gate < 0)) return fail("item gate", i, x.gate);
+                            if (dir && rz && (x.lslot < 0 || x.lslot >= p.n_lslots)) return fail("item slot", i, x.lslot);
+                        }
+                    }
                 }
             }
             if (op_total > kMaxPassOps) return fail("ops per pass", (int)j, op_total);
+        }
+        for (int dir = 0; dir < 2; ++dir) {
+            const int d0 = dir ? p.rdiag0 : p.diag0, nd = dir ? p.n_rdiag : p.n_diag;
+            if (nd > kMaxPassDiags) return fail("diagonal blocks per pass", (int)j, nd);
+            if (nd) {
+                if (d0 < 0 || d0 + nd > (int)pl.diags.size()) return fail("diagonal range", d0, nd);
+                int it = pl.diags[d0].item0;
+                for (int d = d0; d < d0 + nd; ++d) {
+                    if (pl.diags[d].item0 != it) return fail("item contiguity", d, pl.diags[d].item0);
+                    it += pl.diags[d].n_item;
+                }
+                if (it - pl.diags[d0].item0 > kMaxPassItems) return fail("items per pass", (int)j, it);
+            }
         }
     }
     for (size_t h = 0; h < pl.hp.size(); ++h) {
@@ -334,6 +459,15 @@ static std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) 
         std::string e = check_geom(p.high, p.n_high, p.nontile, p.n_nontile);
         if (!e.empty()) return e;
         if (p.group0 < 0 || p.group0 + p.n_group > (int)pl.hg.size()) return fail("group range", (int)h, p.group0);
+        if (p.n_group > kMaxHamGroups) return fail("groups per pass", (int)h, p.n_group);
+        {
+            int nt = 0;
+            for (int g = p.group0; g < p.group0 + p.n_group; ++g) nt += pl.hg[g].n_term;
+            if (nt > kMaxHamTerms) return fail("terms per pass", (int)h, nt);
+            if (p.n_group && pl.hg[p.group0 + p.n_group - 1].term0 + pl.hg[p.group0 + p.n_group - 1].n_term -
+                                 pl.hg[p.group0].term0 != nt)
+                return fail("term contiguity", (int)h, nt);
+        }
         for (int g = p.group0; g < p.group0 + p.n_group; ++g) {
             const HGroup &G0 = pl.hg[g];
             if (G0.xl >> K) return fail("tile flip mask", g, (int)G0.xl);
@@ -359,12 +493,18 @@ static Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::ve
     const int Kmax = dbl ? 12 : 13;
     int K = std::min(n, Kmax);
     if (opt.tile_qubits > 0) K = std::min(opt.tile_qubits, n);
-    if (!opt.fusion || K < 10 || K > Kmax || G == 0) return nullptr;
+    const int Rf = opt.fwd_reg_qubits > 0 ? opt.fwd_reg_qubits : (dbl ? 4 : 5);
+    const int Rr = opt.rev_reg_qubits > 0 ? opt.rev_reg_qubits : (dbl ? 3 : 4);
+    if (!opt.fusion || G == 0 || K < 10) return nullptr;
+    if (!fused_supported(dbl, K, Rf, Rr)) {
+        err = "no compiled fused kernel for this tile / register-qubit choice";
+        return nullptr;
+    }
     Plan *pl = new Plan();
     pl->K = K;
     pl->L = dbl ? 3 : 4;
-    pl->Rf = dbl ? 4 : 5;
-    pl->Rr = dbl ? 3 : 4;
+    pl->Rf = Rf;
+    pl->Rr = Rr;
     pl->n_tiles = 1ull << (n - K);
     const int L = pl->L;
     std::vector<int> rem(G), applied, left;
@@ -374,21 +514,43 @@ static Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::ve
         TileMap tm = make_tilemap(n, K, L, high);
         std::vector<char> inS(n, 0);
         for (int q = 0; q < n; ++q) inS[q] = tm.pos_of[q] >= 0;
-        greedy(gates, rem, inS, n, kMaxPassOps, kMaxPassSlots, applied, left);
-        FPass p;
-        std::memset(&p, 0, sizeof p);
-        p.n_high = (int)high.size();
-        for (size_t i = 0; i < high.size(); ++i) p.high[i] = high[i];
-        for (int q = 0; q < n; ++q)
-            if (tm.pos_of[q] < 0) p.nontile[p.n_nontile++] = q;
-        p.from_zero = pl->passes.empty() ? 1 : 0;
-        p.n_gates = (int)applied.size();
-        int nls;
-        build_stages(*pl, gates, slot_base, n, tm, applied, pl->Rf, dbl, false, nls, p.stage0, p.n_stage);
-        std::vector<int> rseq(applied.rbegin(), applied.rend());
-        p.slotmap0 = (int)pl->slot_map.size();
-        build_stages(*pl, gates, slot_base, n, tm, rseq, pl->Rr, dbl, true, p.n_lslots, p.rstage0, p.n_rstage);
-        pl->passes.push_back(p);
+        // a pass must fit the kernels' shared-memory program budget; shrink it if not
+        for (int cap = kMaxPassOps;; cap = std::max(1, cap / 2)) {
+            greedy(gates, rem, inS, n, cap, kMaxPassSlots, applied, left);
+            const size_t n_st = pl->stages.size(), n_op = pl->ops.size(), n_dg = pl->diags.size();
+            const size_t n_it = pl->items.size(), n_sm = pl->slot_map.size();
+            FPass p;
+            std::memset(&p, 0, sizeof p);
+            p.n_high = (int)high.size();
+            for (size_t i = 0; i < high.size(); ++i) p.high[i] = high[i];
+            for (int q = 0; q < n; ++q)
+                if (tm.pos_of[q] < 0) p.nontile[p.n_nontile++] = q;
+            p.from_zero = pl->passes.empty() ? 1 : 0;
+            p.n_gates = (int)applied.size();
+            int nls;
+            build_stages(*pl, gates, slot_base, n, tm, applied, pl->Rf, dbl, false, nls, p.stage0, p.n_stage,
+                         p.diag0, p.n_diag);
+            std::vector<int> rseq(applied.rbegin(), applied.rend());
+            p.slotmap0 = (int)pl->slot_map.size();
+            build_stages(*pl, gates, slot_base, n, tm, rseq, pl->Rr, dbl, true, p.n_lslots, p.rstage0,
+                         p.n_rstage, p.rdiag0, p.n_rdiag);
+            auto items_of = [&](int d0, int nd) {
+                return nd ? pl->diags[d0 + nd - 1].item0 + pl->diags[d0 + nd - 1].n_item - pl->diags[d0].item0 : 0;
+            };
+            const bool fits = p.n_stage <= kMaxPassStages && p.n_rstage <= kMaxPassStages &&
+                              p.n_diag <= kMaxPassDiags && p.n_rdiag <= kMaxPassDiags &&
+                              items_of(p.diag0, p.n_diag) <= kMaxPassItems &&
+                              items_of(p.rdiag0, p.n_rdiag) <= kMaxPassItems;
+            if (fits || cap == 1) {
+                pl->passes.push_back(p);
+                break;
+            }
+            pl->stages.resize(n_st);
+            pl->ops.resize(n_op);
+            pl->diags.resize(n_dg);
+            pl->items.resize(n_it);
+            pl->slot_map.resize(n_sm);
+        }
         rem.swap(left);
     }
     err = validate_plan(*pl, n, n_gslots, dbl);
@@ -424,6 +586,8 @@ int Circuit::build_plan() {
         if ((st = up((void **)&pl->d_stages, pl->stages.data(), sizeof(FStage) * pl->stages.size()))) return st;
         if ((st = up((void **)&pl->d_ops, pl->ops.data(), sizeof(FOp) * std::max<size_t>(pl->ops.size(), 1)))) return st;
         if ((st = up((void **)&pl->d_slot_map, pl->slot_map.data(), sizeof(int) * std::max<size_t>(pl->slot_map.size(), 1)))) return st;
+        if ((st = up((void **)&pl->d_diags, pl->diags.data(), sizeof(FDiag) * std::max<size_t>(pl->diags.size(), 1)))) return st;
+        if ((st = up((void **)&pl->d_items, pl->items.data(), sizeof(FDItem) * std::max<size_t>(pl->items.size(), 1)))) return st;
         if (!dbl && (st = dalloc((void **)&pl->d_mats_f, sizeof(float) * 8 * std::max(G, 1)))) return st;
         plan_ok = true;
     }
@@ -433,13 +597,17 @@ int Circuit::build_plan() {
 
 // Hamiltonian passes: greedy set cover of the groups' flip masks by tiles (the low L
 // qubits are always inside; each pass adds the groups whose high flip bits fit).
-static void plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
+// Returns false (nothing planned) when some group cannot live in one tile: its flip
+// mask has more high bits than the tile has, or it has more terms than a pass holds.
+static bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
                              const std::vector<PauliTerm> &host_terms) {
     pl->hp.clear();
     pl->hg.clear();
     pl->ht.clear();
     const int K = pl->K, L = pl->L;
     const uint64_t lowmask = (1ull << L) - 1ull;
+    for (const HamGroup &g : ham)
+        if (__builtin_popcountll(g.x & ~lowmask) > K - L || g.count > kMaxHamTerms) return false;
     std::vector<int> rem;
     for (size_t g = 0; g < ham.size(); ++g) rem.push_back((int)g);
     // the diagonal group (x = 0) is group 0 (ordered map) and goes in the first pass
@@ -461,7 +629,12 @@ static void plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
                 if (nw < best_new || (nw == best_new && cov > best_cov)) best = g, best_new = nw, best_cov = cov;
             }
             if (best < 0) break;
-            S |= high_of(best);
+            const uint64_t S2 = S | high_of(best);
+            int ng = 0, nt = 0;
+            for (int g2 : rem)
+                if ((high_of(g2) & ~S2) == 0) ++ng, nt += ham[g2].count;
+            if (ng > kMaxHamGroups || nt > kMaxHamTerms) break;
+            S = S2;
             for (int g2 : rem)
                 if ((high_of(g2) & ~S) == 0) chosen[g2] = 1;
         }
@@ -501,7 +674,13 @@ static void plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
             for (int k = 0; k < G0.count; ++k) {
                 const PauliTerm &t = host_terms[G0.first + k];
                 HTerm h;
+                std::memset(&h, 0, sizeof h);
                 h.z = t.z;
+                for (int q = 0; q < n; ++q) {
+                    if (!((t.z >> q) & 1)) continue;
+                    if (tm.pos_of[q] >= 0) h.zl |= 1u << tm.pos_of[q];
+                    else h.znt |= 1ull << q;
+                }
                 const double sg = (__builtin_popcountll(G0.x & t.z) & 1) ? -1.0 : 1.0;
                 h.wr = sg * t.wr;
                 h.wi = sg * t.wi;
@@ -529,12 +708,13 @@ static void plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
         hp.first = 1;
         pl->hp.push_back(hp);
     }
+    return true;
 }
 
 int Circuit::build_ham_plan() {
     Plan *pl = plan;
     ham_plan_ok = false;
-    plan_hamiltonian(pl, n, ham, host_terms);
+    if (!plan_hamiltonian(pl, n, ham, host_terms)) return VQG_OK;  // one pass per group instead
     {
         const std::string err = validate_plan(*pl, n, n_gslots, dbl);
         if (!err.empty()) return set_error(VQG_ERR_UNSUPPORTED, "%s", err.c_str());
@@ -590,8 +770,9 @@ int Circuit::issue_forward_fused(bool with_ckpt) {
         const int k = with_ckpt ? pl->ckpt_of_pass[j] : -1;
         void *out = k >= 0 ? ckpt_buf[k] : psi;
         prof_begin(FAM_FWD_FUSED);
-        launch_fused_fwd(dbl, pl->K, in, out, pl->d_passes, (int)j, pl->d_stages, pl->d_ops, mats,
-                         pl->n_tiles, pl->grid_fwd, stream);
+        (dbl ? launch_fused_fwd_c128 : launch_fused_fwd_c64)(pl->K, pl->Rf, in, out, pl->d_passes, (int)j,
+                                                             pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
+                                                             mats, pl->n_tiles, pl->grid_fwd, stream);
         prof_end();
         in = out;
     }
@@ -622,8 +803,9 @@ int Circuit::issue_reverse_fused() {
         const int k = pl->ckpt_of_pass[j];
         const void *src = k >= 0 ? ckpt_buf[k] : psi;  // restart phi from the stored state
         prof_begin(FAM_ADJ_FUSED);
-        launch_fused_rev(dbl, pl->K, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops,
-                         pl->d_slot_map, mats, pl->n_tiles, gpart, nb, stream);
+        (dbl ? launch_fused_rev_c128 : launch_fused_rev_c64)(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j,
+                                                             pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
+                                                             pl->d_slot_map, mats, pl->n_tiles, gpart, nb, stream);
         prof_end();
     }
     cudaError_t e = cudaGetLastError();
@@ -721,7 +903,7 @@ extern "C" int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates
         info->hamiltonian_groups = (int)ham.size();
         return VQG_OK;
     }
-    plan_hamiltonian(pl, n_qubits, ham, flat);
+    const bool ham_fused = plan_hamiltonian(pl, n_qubits, ham, flat);
     err = validate_plan(*pl, n_qubits, n_gslots, dbl);
     if (!err.empty()) {
         delete pl;
@@ -729,13 +911,15 @@ extern "C" int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates
     }
     info->forward_passes = (int)pl->passes.size();
     info->reverse_passes = (int)pl->passes.size();
-    info->hamiltonian_passes = (int)pl->hp.size();
+    info->hamiltonian_passes = ham_fused ? (int)pl->hp.size() : (int)ham.size();
     info->hamiltonian_groups = (int)ham.size();
     info->tile_qubits = pl->K;
-    int fs = 0, rs = 0;
-    for (const FPass &p : pl->passes) fs += p.n_stage, rs += p.n_rstage;
+    int fs = 0, rs = 0, fd = 0, rd = 0;
+    for (const FPass &p : pl->passes) fs += p.n_stage, rs += p.n_rstage, fd += p.n_diag, rd += p.n_rdiag;
     info->reserved[0] = fs;  // forward register stages
     info->reserved[1] = rs;  // reverse register stages
+    info->reserved[2] = (int)pl->ops.size();  // register-stage ops, both directions
+    info->reserved[3] = fd + rd;              // diagonal blocks, both directions
     info->launches_per_gradient = 1 + 2 * info->forward_passes + info->hamiltonian_passes + 2;
     delete pl;
     return VQG_OK;

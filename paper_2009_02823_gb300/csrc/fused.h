@@ -18,18 +18,31 @@ constexpr int kMaxHigh = 24;
 constexpr int kMaxNontile = 40;
 constexpr int kMaxThreadBits = 12;
 constexpr int kMaxRegBits = 5;
-constexpr int kMaxPassOps = 256;
+constexpr int kMaxPassOps = 192;     // register-stage ops (gates or diagonal blocks) per pass
 constexpr int kMaxPassStages = 64;
-constexpr int kMaxPassSlots = 256;
+constexpr int kMaxPassSlots = 256;   // reverse reduction values per pass
+constexpr int kMaxPassDiags = 48;    // diagonal blocks per pass
+constexpr int kMaxPassItems = 320;   // diagonal-block items per pass
+constexpr int kMaxDiagRz = 8;        // RZ gates per diagonal block
+constexpr int kMaxDiagCz = 16;       // CZ gates per diagonal block
+constexpr int kMaxHamGroups = 256;   // groups per Hamiltonian pass
+constexpr int kMaxHamTerms = 1024;   // terms per Hamiltonian pass
 
 enum FOpType : int16_t {
-    OP_RY = 0,      // real rotation on register bit k
-    OP_RX = 1,      // RX on register bit k (complex matrix)
-    OP_U3 = 2,      // general 2x2 on register bit k (three parameters)
-    OP_RZ_REG = 3,  // diagonal phase on register bit k
-    OP_RZ_THR = 4,  // diagonal phase on a thread- or tile-level bit (mask g0)
-    OP_CZ = 5,      // sign where both bits are set (each register mask or global mask)
-    OP_CNOT = 6     // swap on target register bit k where the control is set
+    OP_RY = 0,    // real rotation on register bit k
+    OP_RX = 1,    // RX on register bit k (complex matrix)
+    OP_U3 = 2,    // general 2x2 on register bit k (three parameters)
+    OP_CNOT = 3,  // swap on target register bit k where the control is set
+    OP_DIAG = 4   // a block of commuting diagonal gates (RZ, CZ): table x per-thread factor
+};
+
+// Items of a diagonal block.  RZ items come first (they carry reverse reductions).
+enum FDItemType : int16_t {
+    DI_RZ_REG = 0,  // RZ on register bit k0 (in the block's table)
+    DI_RZ_THR = 1,  // RZ on a thread- or tile-level qubit g0 (per-thread phase)
+    DI_CZ_RR = 2,   // CZ on register bits k0, k1 (in the table)
+    DI_CZ_RT = 3,   // CZ on register bit k0 and thread-level qubit g0 (per-thread sign mask)
+    DI_CZ_TT = 4    // CZ on thread-level qubits g0, g1 (per-thread sign)
 };
 
 struct FPass {
@@ -42,23 +55,38 @@ struct FPass {
     int32_t slotmap0;              // reverse: first entry of this pass in the slot map
     int32_t from_zero;             // forward: the input is |0...0> (nothing to load)
     int32_t n_gates;               // gates applied by this pass
+    int32_t diag0, n_diag;         // forward diagonal blocks
+    int32_t rdiag0, n_rdiag;       // reverse diagonal blocks
 };
 
 struct FStage {
-    uint64_t thr_g[kMaxThreadBits];  // global mask of thread bit b
-    uint16_t thr_sw[kMaxThreadBits]; // swizzled tile-local mask of thread bit b
-    uint16_t reg_sw[kMaxRegBits + 3];// swizzled tile-local mask of register bit k
+    uint16_t thr_sw[kMaxThreadBits];     // swizzled tile-local mask of thread bit b
+    uint16_t reg_sw[kMaxRegBits + 3];    // swizzled tile-local mask of register bit k
+    int8_t thr_q[kMaxThreadBits];        // global qubit of thread bit b
     int32_t op0, n_op;
 };
 
-struct FOp {
-    int16_t type, k;
-    int32_t gate;
-    uint32_t rm0, rm1;  // register-index masks (0: that qubit is not a register bit)
-    int32_t lslot;      // reverse: first local reduction value (-1: none)
-    uint64_t g0, g1;    // global masks of the diagonal / control qubits
-    int32_t gslot;      // reverse: first global gate slot
+struct FOp {          // 16 bytes: one shared-memory vector load
+    int8_t type, k;   // k: register bit of the non-diagonal target
+    int8_t cq;        // CNOT: global qubit of a control that is not a register bit, else -1
+    int8_t pad;
+    int16_t diag;     // OP_DIAG: block index within the pass
+    int16_t lslot;    // reverse: first local reduction value (-1: none)
+    uint32_t rm0;     // CNOT: register mask of the control (0: control not a register bit)
+    int32_t gate;     // gate index (matrix source); OP_DIAG: -1
+};
+
+struct FDiag {
+    int32_t item0, n_item;  // items (global index)
+    int32_t n_rz;           // leading RZ items
     int32_t pad;
+};
+
+struct FDItem {
+    int16_t type, k0, k1, pad;
+    int32_t gate;   // RZ: gate index (phases)
+    int32_t lslot;  // reverse RZ: local reduction slot
+    uint64_t g0, g1;
 };
 
 // Hamiltonian tile pass: groups whose flip mask lies inside the tile.
@@ -80,9 +108,12 @@ struct HGroup {
 
 // Term of a group, evaluated at the source index j^x: w' = w * (-1)^{popcount(x & z)}.
 struct HTerm {
-    uint64_t z;
+    uint64_t z;     // global z mask
+    uint64_t znt;   // the part of z on qubits outside the tile of its pass
     double wr, wi;
-    float fr, fi;  // the same weight rounded to FP32 (complex64 kernels)
+    float fr, fi;   // the same weight rounded to FP32 (complex64 kernels)
+    uint32_t zl;    // the part of z inside the tile, as tile-local positions
+    int32_t pad;
 };
 
 // Swizzle of a tile-local amplitude index into its shared-memory slot: XOR-folds the

@@ -1,0 +1,840 @@
+// Tile-fused sweeps (the gate-fusion scheme of the GB300 design; the paper's
+// algorithm only needs "apply gate" primitives, Sec. 2.1, and leaves their fusion to
+// the simulator).
+//
+//   k_fused_fwd : one forward pass -- every tile of 2^K amplitudes is read from HBM once,
+//                 a run of gates is applied in shared memory / registers, and the tile
+//                 is written once (Algorithm 1, line 2, many gates per state traversal).
+//   k_fused_rev : one reverse pass -- phi and lambda tiles are read once, and for each
+//                 gate of the run in reverse order the kernel reduces the gradient sums
+//                 from (phi_{i+1}, lambda_i) and un-applies U_i^dagger to both
+//                 (Algorithm 1, lines 6-11, with App. A's dR = -(i/2) sigma R so that
+//                 mu = dU phi is never formed; App. B.1 for U3).
+//   k_fused_ham : one Hamiltonian pass -- the Pauli groups whose flip mask lies inside
+//                 the tile, lambda (+)= sum_g f_g(j^x) psi[j^x], with E = Re<psi|lambda>.
+//
+// Reduction precision (complex64 amplitudes): products in FP32, per-thread runs of at
+// most 16 terms in FP32, the 32-lane warp tree in FP32, then every warp sum is added
+// into an FP64 accumulator (shared memory), and block / grid levels are FP64.
+#pragma once
+#include <type_traits>
+
+#include "fused.h"
+#include "kernels.h"
+
+namespace vqg {
+
+template <typename T> struct FT;
+template <> struct FT<float> { static constexpr int L = 4, AB = 8; };
+template <> struct FT<double> { static constexpr int L = 3, AB = 16; };
+
+template <typename T> VQG_DEV T shfl(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+template <typename T> VQG_DEV T warp_tree(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl(v, o);
+    return v;
+}
+
+// Reduce 8 values over the warp with 9 shuffles; returns the total of value index
+// ((lane>>4)&1)*4 + ((lane>>3)&1)*2 + ((lane>>2)&1), identical on the 4 lanes sharing
+// those bits.
+template <typename T> VQG_DEV T warp_reduce8(const T (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    T k4[4], k2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) k4[i] = (h4 ? v[i + 4] : v[i]) + shfl(h4 ? v[i] : v[i + 4], 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) k2[i] = (h3 ? k4[i + 2] : k4[i]) + shfl(h3 ? k4[i] : k4[i + 2], 8);
+    T k1 = (h2 ? k2[1] : k2[0]) + shfl(h2 ? k2[0] : k2[1], 4);
+    k1 += shfl(k1, 2);
+    k1 += shfl(k1, 1);
+    return k1;
+}
+
+template <int R, typename F> VQG_DEV void with_k(int k, F &&f) {
+    switch (k) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: if constexpr (R > 1) f(std::integral_constant<int, 1>{}); break;
+    case 2: if constexpr (R > 2) f(std::integral_constant<int, 2>{}); break;
+    case 3: if constexpr (R > 3) f(std::integral_constant<int, 3>{}); break;
+    case 4: if constexpr (R > 4) f(std::integral_constant<int, 4>{}); break;
+    default: break;
+    }
+}
+
+template <typename T> VQG_DEV amp_t<T> neg(amp_t<T> a) { return mk<T>(-a.x, -a.y); }
+
+// ------------------------------------------------------------------ gate ops (forward)
+template <int KB, int NA, typename T>
+VQG_DEV void op_ry(amp_t<T> (&a)[NA], T c, T s) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const int j1 = j | (1 << KB);
+        const amp_t<T> x = a[j], y = a[j1];
+        a[j] = mk<T>(c * x.x - s * y.x, c * x.y - s * y.y);
+        a[j1] = mk<T>(s * x.x + c * y.x, s * x.y + c * y.y);
+    }
+}
+
+template <int KB, int NA, typename T>
+VQG_DEV void op_gen(amp_t<T> (&a)[NA], const Mat2<T> &u) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        apply2<T>(u, a[j], a[j | (1 << KB)]);
+    }
+}
+
+template <int KB, int NA, typename T>
+VQG_DEV void op_cnot(amp_t<T> (&a)[NA], uint32_t rc, bool thr_c) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const bool c = rc ? ((j & rc) != 0) : thr_c;
+        if (c) {
+            const amp_t<T> t = a[j];
+            a[j] = a[j | (1 << KB)];
+            a[j | (1 << KB)] = t;
+        }
+    }
+}
+
+template <typename T> VQG_DEV Mat2<T> mat_of(const amp_t<T> *__restrict__ m) {
+    Mat2<T> u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u.m[k] = m[k];
+    return u;
+}
+
+template <typename T> VQG_DEV Mat2<T> dagger(const Mat2<T> &u) {
+    Mat2<T> r;
+    r.m[0] = mk<T>(u.m[0].x, -u.m[0].y);
+    r.m[1] = mk<T>(u.m[2].x, -u.m[2].y);
+    r.m[2] = mk<T>(u.m[1].x, -u.m[1].y);
+    r.m[3] = mk<T>(u.m[3].x, -u.m[3].y);
+    return r;
+}
+
+// Sign pattern over register indices j < 2^R: bit j = parity(j & c).
+VQG_DEV uint32_t walsh_bits(uint32_t c) {
+    uint32_t w = 0;
+    if (c & 1u) w ^= 0xAAAAAAAAu;
+    if (c & 2u) w ^= 0xCCCCCCCCu;
+    if (c & 4u) w ^= 0xF0F0F0F0u;
+    if (c & 8u) w ^= 0xFF00FF00u;
+    if (c & 16u) w ^= 0xFFFF0000u;
+    return w;
+}
+
+// ------------------------------------------------------------------ pass program in smem
+// One pass's register-stage program (forward or reverse), staged in shared memory by
+// every block at launch: stages, ops, diagonal blocks and their items, the gate
+// matrices of the ops (U; the reverse kernel takes U^dagger of them), the RZ phases of
+// the items (conjugated for the reverse), and each diagonal block's 2^R-entry table
+// (RZ phases on register bits times CZ signs between register bits).
+template <typename T, int R>
+struct Prog {
+    static constexpr int AB = FT<T>::AB;
+    static constexpr size_t align8(size_t x) { return (x + 15) & ~(size_t)15; }
+    static constexpr size_t o_st = 0;
+    static constexpr size_t o_op = align8(o_st + sizeof(FStage) * kMaxPassStages);
+    static constexpr size_t o_dg = align8(o_op + sizeof(FOp) * kMaxPassOps);
+    static constexpr size_t o_it = align8(o_dg + sizeof(FDiag) * kMaxPassDiags);
+    static constexpr size_t o_prm = align8(o_it + sizeof(FDItem) * kMaxPassItems);
+    static constexpr size_t o_iph = align8(o_prm + (size_t)AB * 4 * kMaxPassOps);
+    static constexpr size_t o_tab = align8(o_iph + (size_t)AB * 2 * kMaxPassItems);
+    static constexpr size_t bytes = align8(o_tab + (size_t)AB * (1 << R) * kMaxPassDiags);
+
+    FStage *st;
+    FOp *op;
+    FDiag *dg;
+    FDItem *it;
+    amp_t<T> *prm, *iph, *tab;
+    int op_base, item_base;
+
+    VQG_DEV void bind(unsigned char *p) {
+        st = reinterpret_cast<FStage *>(p + o_st);
+        op = reinterpret_cast<FOp *>(p + o_op);
+        dg = reinterpret_cast<FDiag *>(p + o_dg);
+        it = reinterpret_cast<FDItem *>(p + o_it);
+        prm = reinterpret_cast<amp_t<T> *>(p + o_prm);
+        iph = reinterpret_cast<amp_t<T> *>(p + o_iph);
+        tab = reinterpret_cast<amp_t<T> *>(p + o_tab);
+    }
+};
+
+template <typename W>
+VQG_DEV void copy_words(W *dst, const W *__restrict__ src, int count, int tid, int nt) {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    const int words = count * (int)(sizeof(W) / 4);
+    for (int i = tid; i < words; i += nt) d[i] = s[i];
+}
+
+template <typename T, int R>
+VQG_DEV void load_prog(Prog<T, R> &pg, int s0, int ns, int d0, int nd, const FStage *__restrict__ stages,
+                       const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
+                       const FDItem *__restrict__ items, const T *__restrict__ mats, bool reverse,
+                       int tid, int nt) {
+    const int op0 = ns ? stages[s0].op0 : 0;
+    const int n_op = ns ? stages[s0 + ns - 1].op0 + stages[s0 + ns - 1].n_op - op0 : 0;
+    const int it0 = nd ? diags[d0].item0 : 0;
+    const int n_it = nd ? diags[d0 + nd - 1].item0 + diags[d0 + nd - 1].n_item - it0 : 0;
+    pg.op_base = op0;
+    pg.item_base = it0;
+    copy_words(pg.st, stages + s0, ns, tid, nt);
+    copy_words(pg.op, ops + op0, n_op, tid, nt);
+    copy_words(pg.dg, diags + d0, nd, tid, nt);
+    copy_words(pg.it, items + it0, n_it, tid, nt);
+    for (int o = tid; o < n_op; o += nt) {
+        const FOp op = ops[op0 + o];
+        const int g = op.gate;
+        if (g < 0) continue;
+        const T *m = mats + 8 * (size_t)g;
+        if (op.type == OP_RY) {  // (cos, sin) of the real rotation in one slot
+            pg.prm[4 * o] = mk<T>(m[0], m[4]);
+            continue;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pg.prm[4 * o + e] = mk<T>(m[2 * e], m[2 * e + 1]);
+    }
+    for (int i = tid; i < n_it; i += nt) {
+        const FDItem x = items[it0 + i];
+        if (x.type != DI_RZ_REG && x.type != DI_RZ_THR) continue;
+        const T *m = mats + 8 * (size_t)x.gate;
+        const T sg = reverse ? (T)-1 : (T)1;
+        pg.iph[2 * i] = mk<T>(m[0], sg * m[1]);
+        pg.iph[2 * i + 1] = mk<T>(m[6], sg * m[7]);
+    }
+    __syncthreads();
+    constexpr int NA = 1 << R;
+    for (int e = tid; e < nd * NA; e += nt) {
+        const int d = e / NA, j = e % NA;
+        const FDiag D = pg.dg[d];
+        amp_t<T> v = mk<T>((T)1, (T)0);
+        for (int i = D.item0 - it0; i < D.item0 - it0 + D.n_item; ++i) {
+            const FDItem &x = pg.it[i];
+            if (x.type == DI_RZ_REG) v = cmul<T>(((j >> x.k0) & 1) ? pg.iph[2 * i + 1] : pg.iph[2 * i], v);
+            else if (x.type == DI_CZ_RR && ((j >> x.k0) & 1) && ((j >> x.k1) & 1)) v = neg<T>(v);
+        }
+        pg.tab[e] = v;
+    }
+}
+
+// Per-thread factor of a diagonal block: tau (phases of RZ on thread-level qubits and
+// CZ signs between thread-level qubits) and the register mask whose parity flips sign
+// (CZ between a register bit and a set thread-level bit).
+template <typename T, int R>
+VQG_DEV void diag_thread(const Prog<T, R> &pg, const FDiag &D, uint64_t gb, amp_t<T> &tau, uint32_t &c) {
+    tau = mk<T>((T)1, (T)0);
+    c = 0;
+    const int i0 = D.item0 - pg.item_base;
+    for (int i = i0; i < i0 + D.n_item; ++i) {
+        const FDItem &x = pg.it[i];
+        if (x.type == DI_RZ_THR) tau = cmul<T>((gb & x.g0) ? pg.iph[2 * i + 1] : pg.iph[2 * i], tau);
+        else if (x.type == DI_CZ_TT) {
+            if ((gb & x.g0) && (gb & x.g1)) tau = neg<T>(tau);
+        } else if (x.type == DI_CZ_RT) {
+            if (gb & x.g0) c ^= 1u << x.k0;
+        }
+    }
+}
+
+// Multiply by the block's table with the per-thread sign pattern; the per-thread
+// phase tau is not applied here but folded into the stage's pending phase: a common
+// factor on all of a thread's amplitudes commutes with every later op of the stage
+// (they act within the thread's amplitudes) and is applied once before the scatter.
+template <int NA, typename T>
+VQG_DEV void diag_apply(amp_t<T> (&a)[NA], const amp_t<T> *__restrict__ tab, uint32_t c) {
+    const uint32_t w = walsh_bits(c);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        amp_t<T> d = tab[j];
+        if ((w >> j) & 1u) d = neg<T>(d);
+        a[j] = cmul<T>(d, a[j]);
+    }
+}
+
+template <int R, int NA, typename T>
+VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64_t gb, amp_t<T> &phase) {
+    const FOp op = pg.op[o];
+    const amp_t<T> *m = pg.prm + 4 * o;
+    switch (op.type) {
+    case OP_RY: {
+        const amp_t<T> cs = m[0];
+        with_k<R>(op.k, [&](auto kb) { op_ry<decltype(kb)::value, NA, T>(a, cs.x, cs.y); });
+        break;
+    }
+    case OP_RX:
+    case OP_U3: {
+        const Mat2<T> u = mat_of<T>(m);
+        with_k<R>(op.k, [&](auto kb) { op_gen<decltype(kb)::value, NA, T>(a, u); });
+        break;
+    }
+    case OP_CNOT: {
+        const bool c = op.rm0 ? false : ((gb >> op.cq) & 1ull) != 0;
+        with_k<R>(op.k, [&](auto kb) { op_cnot<decltype(kb)::value, NA, T>(a, op.rm0, c); });
+        break;
+    }
+    case OP_DIAG: {
+        amp_t<T> tau;
+        uint32_t c;
+        diag_thread<T, R>(pg, pg.dg[op.diag], gb, tau, c);
+        phase = cmul<T>(tau, phase);
+        diag_apply<NA, T>(a, pg.tab + op.diag * NA, c);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// ------------------------------------------------------------------ gate ops (reverse)
+// Each returns the thread's partial of the gate's reduction value(s) computed from
+// (phi_{i+1} = a, lambda_i = l) before un-applying U^dagger to both.
+template <int KB, int NA, typename T>
+VQG_DEV T rev_ry(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], T c, T s) {
+    T v = 0;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const int j1 = j | (1 << KB);
+        const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+        // Im <lambda| Y |phi> over the pair: Re(conj(l1) a0) - Re(conj(l0) a1)
+        v += (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
+        // RY^dagger = [[c, s], [-s, c]]
+        a[j] = mk<T>(c * a0.x + s * a1.x, c * a0.y + s * a1.y);
+        a[j1] = mk<T>(c * a1.x - s * a0.x, c * a1.y - s * a0.y);
+        l[j] = mk<T>(c * l0.x + s * l1.x, c * l0.y + s * l1.y);
+        l[j1] = mk<T>(c * l1.x - s * l0.x, c * l1.y - s * l0.y);
+    }
+    return v;
+}
+
+template <int KB, int NA, typename T>
+VQG_DEV T rev_rx(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud) {
+    T v = 0;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const int j1 = j | (1 << KB);
+        const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+        // Im <lambda| X |phi>: Im(conj(l0) a1) + Im(conj(l1) a0)
+        v += (l0.x * a1.y - l0.y * a1.x) + (l1.x * a0.y - l1.y * a0.x);
+        apply2<T>(ud, a[j], a[j1]);
+        apply2<T>(ud, l[j], l[j1]);
+    }
+    return v;
+}
+
+template <int KB, int NA, typename T>
+VQG_DEV void rev_u3(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud, T (&v)[8]) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const int j1 = j | (1 << KB);
+        const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+        const amp_t<T> o00 = cconjmul<T>(l0, a0), o01 = cconjmul<T>(l0, a1);
+        const amp_t<T> o10 = cconjmul<T>(l1, a0), o11 = cconjmul<T>(l1, a1);
+        v[0] += o00.x; v[1] += o00.y; v[2] += o01.x; v[3] += o01.y;
+        v[4] += o10.x; v[5] += o10.y; v[6] += o11.x; v[7] += o11.y;
+        apply2<T>(ud, a[j], a[j1]);
+        apply2<T>(ud, l[j], l[j1]);
+    }
+}
+
+// Reverse diagonal block.  Every RZ of the block gets Im <lambda| Z_q |phi> from the
+// block's input pair: the other gates of the block are diagonal, commute with Z_q and
+// cancel between bra and ket.  With p_j = Im(conj(lambda_j) phi_j), an RZ on register
+// bit k needs sum_j (-1)^{j_k} p_j and an RZ on a thread-level qubit +-sum_j p_j.
+template <int R, int NA, typename T>
+VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg, const FDiag &D,
+                      int di, uint64_t gb, double *acc_w, amp_t<T> &phase) {
+    if (D.n_rz > 0) {
+        T S = 0, H[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) H[k] = 0;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const T pj = l[j].x * a[j].y - l[j].y * a[j].x;
+            S += pj;
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (!((j >> k) & 1)) H[k] += pj;
+        }
+        const int i0 = D.item0 - pg.item_base;
+        T v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            v[r] = 0;
+            if (r < D.n_rz) {
+                const FDItem &x = pg.it[i0 + r];
+                if (x.type == DI_RZ_REG) {
+                    T h = H[0];
+#pragma unroll
+                    for (int k = 1; k < R; ++k)
+                        if (x.k0 == k) h = H[k];
+                    v[r] = (T)2 * h - S;  // sum over bit 0 minus sum over bit 1
+                } else {
+                    v[r] = (gb & x.g0) ? -S : S;
+                }
+            }
+        }
+        const int lane = threadIdx.x & 31;
+        if (D.n_rz == 1) {
+            const T tot = warp_tree<T>(v[0]);
+            if (lane == 0) acc_w[pg.it[i0].lslot] += (double)tot;
+        } else {
+            const T tot = warp_reduce8<T>(v);
+            const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            if ((lane & 3) == 0 && vi < D.n_rz) acc_w[pg.it[i0 + vi].lslot] += (double)tot;
+        }
+    }
+    amp_t<T> tau;
+    uint32_t c;
+    diag_thread<T, R>(pg, D, gb, tau, c);
+    phase = cmul<T>(tau, phase);  // common to phi and lambda: leaves every reduction unchanged
+    const amp_t<T> *tab = pg.tab + di * NA;
+    const uint32_t w = walsh_bits(c);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        amp_t<T> d = tab[j];
+        if ((w >> j) & 1u) d = neg<T>(d);
+        a[j] = cmul<T>(d, a[j]);
+        l[j] = cmul<T>(d, l[j]);
+    }
+}
+
+// ------------------------------------------------------------------ tile I/O
+template <typename T, int K>
+struct TileIO {
+    static constexpr int L = FT<T>::L, AB = FT<T>::AB;
+    static constexpr int TILE = 1 << K, ROWS = 1 << (K - L);
+    static constexpr int CA = 16 / AB;          // amplitudes per 16-byte chunk
+    static constexpr int CPR = (1 << L) / CA;   // chunks per 128-byte row
+    static constexpr int CHUNKS = TILE / CA;
+
+    static VQG_DEV void load(amp_t<T> *tile, const amp_t<T> *__restrict__ src, uint64_t base,
+                             const uint64_t *row_off, int tid, int nt) {
+        for (int c = tid; c < CHUNKS; c += nt) {
+            const int row = c / CPR, col = c % CPR;
+            const uint32_t t = (uint32_t)(row << L) | (uint32_t)(col * CA);
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(src + (base | row_off[row]) + col * CA));
+            put_chunk(tile, t, v);
+        }
+    }
+    static VQG_DEV void zero(amp_t<T> *tile, uint64_t base, int tid, int nt) {
+        for (int c = tid; c < CHUNKS; c += nt) put_chunk(tile, (uint32_t)(c * CA), make_float4(0.f, 0.f, 0.f, 0.f));
+        if (base == 0 && tid == 0) tile[swz<AB>(0)] = mk<T>((T)1, (T)0);
+    }
+    // A 16-byte chunk (two complex64 or one complex128 amplitudes starting at tile-local
+    // index t) to / from shared memory.  The complex64 swizzle may separate the two
+    // amplitudes (it folds higher bits into bit 0), so each goes to its own 8-byte slot.
+    static VQG_DEV void put_chunk(amp_t<T> *tile, uint32_t t, float4 v) {
+        if constexpr (AB == 8) {
+            tile[swz<AB>(t)] = mk<T>(v.x, v.y);
+            tile[swz<AB>(t + 1)] = mk<T>(v.z, v.w);
+        } else {
+            *reinterpret_cast<float4 *>(tile + swz<AB>(t)) = v;
+        }
+    }
+    static VQG_DEV float4 get_chunk(const amp_t<T> *tile, uint32_t t) {
+        if constexpr (AB == 8) {
+            const amp_t<T> a = tile[swz<AB>(t)], b = tile[swz<AB>(t + 1)];
+            return make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            return *reinterpret_cast<const float4 *>(tile + swz<AB>(t));
+        }
+    }
+    static VQG_DEV void store(const amp_t<T> *tile, amp_t<T> *__restrict__ dst, uint64_t base,
+                              const uint64_t *row_off, int tid, int nt) {
+        for (int c = tid; c < CHUNKS; c += nt) {
+            const int row = c / CPR, col = c % CPR;
+            const uint32_t t = (uint32_t)(row << L) | (uint32_t)(col * CA);
+            __stcs(reinterpret_cast<float4 *>(dst + (base | row_off[row]) + col * CA), get_chunk(tile, t));
+        }
+    }
+};
+
+VQG_DEV uint64_t tile_base(uint64_t tile, const int32_t *nontile, int n_nontile) {
+    uint64_t b = 0;
+    for (int i = 0; i < n_nontile; ++i) b |= ((tile >> i) & 1ull) << nontile[i];
+    return b;
+}
+
+template <typename T, int K>
+VQG_DEV void fill_row_offsets(const int32_t *high, uint64_t *row_off, int tid, int nt) {
+    constexpr int L = FT<T>::L, ROWS = 1 << (K - L);
+    for (int r = tid; r < ROWS; r += nt) {
+        uint64_t off = 0;
+        for (int i = 0; i < K - L; ++i)
+            if ((r >> i) & 1) off |= 1ull << high[i];
+        row_off[r] = off;
+    }
+}
+
+// Tile-local smem base and global index of register index 0 for this thread.
+template <int K, int R, int AB>
+VQG_DEV void thread_base(const FStage &st, int tid, uint64_t base, uint32_t &sb, uint64_t &gb) {
+    sb = 0;
+    gb = base;
+#pragma unroll
+    for (int b = 0; b < K - R; ++b)
+        if ((tid >> b) & 1) sb ^= st.thr_sw[b], gb |= 1ull << st.thr_q[b];
+}
+
+template <int R, int NA>
+VQG_DEV uint32_t reg_addr(uint32_t sb, const uint32_t (&w)[R], int j) {
+    uint32_t ad = sb;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if ((j >> k) & 1) ad ^= w[k];
+    return ad;
+}
+
+// ------------------------------------------------------------------ forward pass
+template <typename T, int K, int R>
+struct FwdCfg {
+    static constexpr int NT = 1 << (K - R);
+    static constexpr size_t o_row = (size_t)(1 << K) * FT<T>::AB;
+    static constexpr size_t o_prog = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
+    static constexpr size_t smem() { return o_prog + Prog<T, R>::bytes; }
+    static_assert(o_prog + Prog<T, R>::bytes <= 227 * 1024, "forward pass exceeds shared memory");
+};
+
+template <typename T, int K, int R>
+__global__ void __launch_bounds__(1 << (K - R), 2)
+    k_fused_fwd(const amp_t<T> *__restrict__ src, amp_t<T> *__restrict__ dst,
+                const FPass *__restrict__ passes, int pi, const FStage *__restrict__ stages,
+                const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
+                const FDItem *__restrict__ items, const T *__restrict__ mats, uint64_t n_tiles) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    using C = FwdCfg<T, K, R>;
+    constexpr int AB = FT<T>::AB, NT = C::NT, NA = 1 << R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    A *tile = reinterpret_cast<A *>(smem);
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
+    Prog<T, R> pg;
+    pg.bind(smem + C::o_prog);
+    const FPass &P = passes[pi];
+    const int tid = threadIdx.x;
+    fill_row_offsets<T, K>(P.high, row_off, tid, NT);
+    load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, stages, ops, diags, items, mats, false, tid, NT);
+    const int n_stage = P.n_stage, n_nontile = P.n_nontile;
+    const bool from_zero = P.from_zero;
+    __syncthreads();
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const uint64_t base = tile_base(ti, P.nontile, n_nontile);
+        if (from_zero) IO::zero(tile, base, tid, NT);
+        else IO::load(tile, src, base, row_off, tid, NT);
+        __syncthreads();
+        for (int s = 0; s < n_stage; ++s) {
+            const FStage &st = pg.st[s];
+            uint32_t sb;
+            uint64_t gb;
+            thread_base<K, R, AB>(st, tid, base, sb, gb);
+            uint32_t w[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
+            A a[NA];
+#pragma unroll
+            for (int j = 0; j < NA; ++j) a[j] = tile[reg_addr<R, NA>(sb, w, j)];
+            A phase = mk<T>((T)1, (T)0);
+            const int o0 = st.op0 - pg.op_base;
+            for (int o = o0; o < o0 + st.n_op; ++o) apply_fwd_op<R, NA, T>(a, pg, o, gb, phase);
+            asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
+#pragma unroll
+            for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = cmul<T>(phase, a[j]);
+            __syncthreads();
+        }
+        IO::store(tile, dst, base, row_off, tid, NT);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ reverse pass
+template <typename T, int K, int R>
+struct RevCfg {
+    static constexpr int NT = 1 << (K - R), NW = NT / 32;
+    static constexpr size_t o_row = 2 * (size_t)(1 << K) * FT<T>::AB;
+    static constexpr size_t o_prog = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
+    static constexpr size_t o_acc = o_prog + Prog<T, R>::bytes;
+    static constexpr size_t o_map = o_acc + sizeof(double) * (size_t)NW * kMaxPassSlots;
+    static constexpr size_t smem() { return o_map + sizeof(int) * kMaxPassSlots; }
+    static_assert(o_map + sizeof(int) * kMaxPassSlots <= 227 * 1024, "reverse pass exceeds shared memory");
+};
+
+template <typename T, int K, int R>
+__global__ void __launch_bounds__(1 << (K - R))
+    k_fused_rev(const amp_t<T> *__restrict__ phi_src, amp_t<T> *__restrict__ phi_dst,
+                amp_t<T> *__restrict__ lam, const FPass *__restrict__ passes, int pi,
+                const FStage *__restrict__ stages, const FOp *__restrict__ ops,
+                const FDiag *__restrict__ diags, const FDItem *__restrict__ items,
+                const int *__restrict__ slot_map, const T *__restrict__ mats, uint64_t n_tiles,
+                double *__restrict__ partials, int nb) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    using C = RevCfg<T, K, R>;
+    constexpr int AB = FT<T>::AB, NT = C::NT, NA = 1 << R, NW = C::NW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    A *tphi = reinterpret_cast<A *>(smem);
+    A *tlam = tphi + (1 << K);
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
+    Prog<T, R> pg;
+    pg.bind(smem + C::o_prog);
+    double *acc = reinterpret_cast<double *>(smem + C::o_acc);
+    int *smap = reinterpret_cast<int *>(smem + C::o_map);
+    const FPass &P = passes[pi];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_stage = P.n_rstage, n_ls = P.n_lslots;
+    fill_row_offsets<T, K>(P.high, row_off, tid, NT);
+    for (int i = tid; i < NW * n_ls; i += NT) acc[i] = 0.0;
+    for (int i = tid; i < n_ls; i += NT) smap[i] = slot_map[P.slotmap0 + i];
+    load_prog<T, R>(pg, P.rstage0, n_stage, P.rdiag0, P.n_rdiag, stages, ops, diags, items, mats, true, tid, NT);
+    double *acc_w = acc + warp * n_ls;
+    const int n_nontile = P.n_nontile;
+    __syncthreads();
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const uint64_t base = tile_base(ti, P.nontile, n_nontile);
+        IO::load(tphi, phi_src, base, row_off, tid, NT);
+        IO::load(tlam, lam, base, row_off, tid, NT);
+        __syncthreads();
+        for (int s = 0; s < n_stage; ++s) {
+            const FStage &st = pg.st[s];
+            uint32_t sb;
+            uint64_t gb;
+            thread_base<K, R, AB>(st, tid, base, sb, gb);
+            uint32_t w[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
+            A a[NA], l[NA];
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                a[j] = tphi[ad];
+                l[j] = tlam[ad];
+            }
+            A phase = mk<T>((T)1, (T)0);
+            const int o0 = st.op0 - pg.op_base;
+            for (int o = o0; o < o0 + st.n_op; ++o) {
+                const FOp op = pg.op[o];
+                const A *m = pg.prm + 4 * o;
+                T v1 = 0;
+                bool red1 = false;
+                switch (op.type) {
+                case OP_RY: {
+                    const A cs = m[0];
+                    with_k<R>(op.k, [&](auto kb) { v1 = rev_ry<decltype(kb)::value, NA, T>(a, l, cs.x, cs.y); });
+                    red1 = true;
+                    break;
+                }
+                case OP_RX: {
+                    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+                    with_k<R>(op.k, [&](auto kb) { v1 = rev_rx<decltype(kb)::value, NA, T>(a, l, ud); });
+                    red1 = true;
+                    break;
+                }
+                case OP_U3: {
+                    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+                    T v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    with_k<R>(op.k, [&](auto kb) { rev_u3<decltype(kb)::value, NA, T>(a, l, ud, v8); });
+                    const T tot = warp_reduce8<T>(v8);
+                    if ((lane & 3) == 0) {
+                        const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                        acc_w[op.lslot + vi] += (double)tot;
+                    }
+                    break;
+                }
+                case OP_CNOT: {
+                    const bool c = op.rm0 ? false : ((gb >> op.cq) & 1ull) != 0;
+                    with_k<R>(op.k, [&](auto kb) {
+                        op_cnot<decltype(kb)::value, NA, T>(a, op.rm0, c);
+                        op_cnot<decltype(kb)::value, NA, T>(l, op.rm0, c);
+                    });
+                    break;
+                }
+                case OP_DIAG:
+                    rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, acc_w, phase);
+                    break;
+                default:
+                    break;
+                }
+                if (red1) {
+                    const T tot = warp_tree<T>(v1);
+                    if (lane == 0) acc_w[op.lslot] += (double)tot;
+                }
+            }
+            asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                tphi[ad] = cmul<T>(phase, a[j]);
+                tlam[ad] = cmul<T>(phase, l[j]);
+            }
+            __syncthreads();
+        }
+        IO::store(tphi, phi_dst, base, row_off, tid, NT);
+        IO::store(tlam, lam, base, row_off, tid, NT);
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = tid; i < n_ls; i += NT) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += acc[w * n_ls + i];
+        partials[(size_t)smap[i] * nb + blockIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------------ Hamiltonian pass
+// Per tile, each thread owns CPT 16-byte chunks of amplitudes and treats them in
+// batches of 8 amplitudes held in registers.  For a term z of a group with flip mask x,
+// the sign at global index j = base | tile bits is
+//   (-1)^{popcount(j & z)} = (-1)^{popcount(base & z_nt)} (-1)^{popcount(t & z_l)},
+// so the first factor is folded into the weight once per tile and the inner loop is a
+// 32-bit popcount per amplitude.
+template <typename T, int K>
+struct HamCfg {
+    static constexpr int NT = 256;
+    static constexpr size_t smem() {
+        return (size_t)(1 << K) * FT<T>::AB + sizeof(uint64_t) * (1 << (K - FT<T>::L)) +
+               (sizeof(uint32_t) * 3) * kMaxHamGroups +
+               (sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
+    }
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_fused_ham(const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam,
+                const HPass *__restrict__ hp, int pi, const HGroup *__restrict__ groups,
+                const HTerm *__restrict__ terms, uint64_t n_tiles, double *__restrict__ partials, int nb) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
+    constexpr int CPT = IO::CHUNKS / NT;                 // chunks per thread per tile
+    constexpr int BCH = CPT < 8 / IO::CA ? CPT : 8 / IO::CA;  // chunks per batch
+    constexpr int BA = BCH * IO::CA;                     // amplitudes per batch
+    static_assert(CPT % BCH == 0, "batching");
+    extern __shared__ __align__(16) unsigned char smem[];
+    A *tile = reinterpret_cast<A *>(smem);
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + (size_t)(1 << K) * AB);
+    uint64_t *t_znt = row_off + IO::ROWS;                          // [kMaxHamTerms]
+    A *t_w = reinterpret_cast<A *>(t_znt + kMaxHamTerms);          // [kMaxHamTerms] weights
+    A *t_weff = t_w + kMaxHamTerms;                                // [kMaxHamTerms] this tile
+    uint32_t *t_zl = reinterpret_cast<uint32_t *>(t_weff + kMaxHamTerms);
+    uint32_t *g_xl = t_zl + kMaxHamTerms;
+    uint32_t *g_t0 = g_xl + kMaxHamGroups;
+    uint32_t *g_nt = g_t0 + kMaxHamGroups;
+    __shared__ double wsum[NT / 32];
+    const HPass &P = hp[pi];
+    const int tid = threadIdx.x;
+    for (int r = tid; r < IO::ROWS; r += NT) {
+        uint64_t off = 0;
+        for (int i = 0; i < K - L; ++i)
+            if ((r >> i) & 1) off |= 1ull << P.high[i];
+        row_off[r] = off;
+    }
+    const int ng = P.n_group;
+    const int term_base = ng ? groups[P.group0].term0 : 0;
+    const int n_terms = ng ? groups[P.group0 + ng - 1].term0 + groups[P.group0 + ng - 1].n_term - term_base : 0;
+    for (int g = tid; g < ng; g += NT) {
+        const HGroup G = groups[P.group0 + g];
+        g_xl[g] = G.xl;
+        g_t0[g] = (uint32_t)(G.term0 - term_base);
+        g_nt[g] = (uint32_t)G.n_term;
+    }
+    for (int k = tid; k < n_terms; k += NT) {
+        const HTerm tm = terms[term_base + k];
+        t_znt[k] = tm.znt;
+        t_zl[k] = tm.zl;
+        if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
+        else t_w[k] = mk<T>(tm.wr, tm.wi);
+    }
+    const bool first = P.first;
+    double eacc = 0.0;
+    __syncthreads();
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const uint64_t base = tile_base(ti, P.nontile, P.n_nontile);
+        IO::load(tile, psi, base, row_off, tid, NT);
+        for (int k = tid; k < n_terms; k += NT) {
+            const A w = t_w[k];
+            t_weff[k] = (__popcll(base & t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;
+        }
+        __syncthreads();
+        T run = 0;
+#pragma unroll 1
+        for (int b0 = 0; b0 < CPT; b0 += BCH) {
+            uint32_t t[BA];
+            uint64_t gch[BCH];
+            A mine[BA], out[BA];
+#pragma unroll
+            for (int i = 0; i < BCH; ++i) {
+                const int c = tid + NT * (b0 + i);
+                const int row = c / IO::CPR, col = c % IO::CPR;
+                const uint32_t t0 = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
+                gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
+                union {
+                    float4 f;
+                    A a[IO::CA];
+                } u;
+                if (!first) u.f = __ldcs(reinterpret_cast<const float4 *>(lam + gch[i]));
+#pragma unroll
+                for (int e = 0; e < IO::CA; ++e) {
+                    t[i * IO::CA + e] = t0 + e;
+                    mine[i * IO::CA + e] = tile[swz<AB>(t0 + e)];
+                    out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : u.a[e];
+                }
+            }
+            for (int g = 0; g < ng; ++g) {
+                const uint32_t xl = g_xl[g];
+                const int j0 = g_t0[g], j1 = j0 + g_nt[g];
+                A f[BA], src[BA];
+#pragma unroll
+                for (int k = 0; k < BA; ++k) {
+                    src[k] = tile[swz<AB>(t[k] ^ xl)];
+                    f[k] = mk<T>((T)0, (T)0);
+                }
+                for (int j = j0; j < j1; ++j) {
+                    const uint32_t zl = t_zl[j];
+                    const A w = t_weff[j];
+#pragma unroll
+                    for (int k = 0; k < BA; ++k) {
+                        const bool odd = __popc(t[k] & zl) & 1;
+                        f[k].x += odd ? -w.x : w.x;
+                        f[k].y += odd ? -w.y : w.y;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < BA; ++k) {
+                    const A d = cmul<T>(f[k], src[k]);
+                    out[k] = cadd<T>(out[k], d);
+                    run += mine[k].x * d.x + mine[k].y * d.y;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < BCH; ++i) {
+                union {
+                    float4 f;
+                    A a[IO::CA];
+                } u;
+#pragma unroll
+                for (int e = 0; e < IO::CA; ++e) u.a[e] = out[i * IO::CA + e];
+                __stcs(reinterpret_cast<float4 *>(lam + gch[i]), u.f);
+            }
+        }
+        eacc += (double)warp_tree<T>(run);
+        __syncthreads();
+    }
+    if ((tid & 31) == 0) wsum[tid >> 5] = eacc;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += wsum[w];
+        partials[(size_t)P.eslot * nb + blockIdx.x] = s;
+    }
+}
+
+}  // namespace vqg

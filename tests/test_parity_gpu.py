@@ -212,3 +212,23 @@ def test_unused_parameter_has_zero_gradient():
         e, g = c.energy_and_gradient(th)
         assert g[1] == 0.0
         assert_parity("c128", e, g, e_ref, g_ref)
+
+
+@pytest.mark.parametrize("dtype,K,Rf,Rr", [("c64", 12, 4, 3), ("c64", 13, 4, 4), ("c64", 10, 5, 3),
+                                           ("c128", 11, 3, 2), ("c128", 12, 3, 3), ("c128", 10, 4, 2)])
+@pytest.mark.parametrize("case", ["cfg3", "cfg5", "random"])
+def test_fused_register_variants(case, dtype, K, Rf, Rr):
+    """Every compiled register-qubit variant of the fused passes against the oracle."""
+    n = 14
+    if case == "random":
+        rng = np.random.default_rng(99 + K + Rf)
+        gates, P = W.random_circuit(rng, n, 120, share_params=True)
+        theta = rng.uniform(0, 2 * np.pi, P)
+        terms = W.random_paulis(rng, n, 25, 4)
+    else:
+        w = W.config(int(case[3]), n=n, layers=3)
+        gates, P, theta, terms = w.gates, w.n_params, w.theta, w.terms
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, dtype, terms, tile_qubits=K, fwd_reg_qubits=Rf, rev_reg_qubits=Rr) as c:
+        e, g = c.energy_and_gradient(theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, f"{case} K={K} R=({Rf},{Rr})")

@@ -55,3 +55,28 @@ def test_dry_run_rejects_bad_input():
         B.plan_dry_run(4, [("RX", 9, -1, (0, -1, -1))], 1, [], "c64")
     with pytest.raises(B.VqgError):
         B.plan_dry_run(4, [("RX", 0, -1, (0, -1, -1))], 1, [(1.0, ((5, "Z"),))], "c64")
+
+
+def test_wide_flip_masks_fall_back_to_group_passes():
+    """A string with X on more qubits than a tile holds cannot be fused; the planner
+    keeps one pass per group instead of looping."""
+    w = W.config(3)
+    terms = [(0.5, tuple((q, "X") for q in range(w.n)))] + w.terms[:5]
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, terms, "c64")
+    assert info["hamiltonian_passes"] == info["hamiltonian_groups"]
+
+
+@pytest.mark.parametrize("dtype,K,Rf,Rr,ok", [("c64", 13, 5, 4, True), ("c64", 13, 4, 4, True),
+                                              ("c64", 12, 5, 3, True), ("c64", 13, 5, 3, False),
+                                              ("c64", 13, 3, 4, False), ("c128", 12, 4, 3, True),
+                                              ("c128", 11, 3, 2, True), ("c128", 12, 4, 2, False)])
+def test_register_variants(dtype, K, Rf, Rr, ok):
+    w = W.config(3)
+    if ok:
+        info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype, tile_qubits=K,
+                              fwd_reg_qubits=Rf, rev_reg_qubits=Rr)
+        assert info["tile_qubits"] == K
+    else:
+        with pytest.raises(B.VqgError):
+            B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype, tile_qubits=K,
+                           fwd_reg_qubits=Rf, rev_reg_qubits=Rr)
