@@ -176,6 +176,42 @@ int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_par
 const char *vqg_last_error(void);
 const char *vqg_status_string(int status);
 
+/* ---------------------------------------------------------------- batched launch
+ * Many independent circuits (each with its own parameters and Pauli-sum Hamiltonian),
+ * every one evaluated by Algorithm 1 (energy and full gradient), in ONE persistent
+ * kernel launch replayed from a CUDA graph.  complex64 amplitudes with FP64 reductions;
+ * 12 <= n_qubits <= 30 per circuit.  Work is split into (circuit, phase, chunk of tiles)
+ * tasks claimed from a device queue; a task waits (bounded) only for its own circuit's
+ * earlier phases.
+ *
+ * vqg_batch_create: circuit b has n_qubits[b] qubits, gates gates[gate_offsets[b] ..
+ *   gate_offsets[b+1]) (parameter indices local to the circuit) and n_params[b]
+ *   parameters.  Arrays are host memory, copied.  dtype must be VQG_C64.
+ * vqg_batch_set_hamiltonian: as vqg_set_hamiltonian for circuit `circuit`; all circuits
+ *   need one before the first evaluation, after which they are fixed.
+ * vqg_batch_energy_and_gradient: theta = the circuits' parameter vectors concatenated
+ *   (host, sum n_params doubles); energies: n_circuits doubles; grads: concatenated like
+ *   theta.  Blocks until done.  VQG_ERR_TIMEOUT if a task's bounded wait ran out (the
+ *   context stays usable; results are then incomplete).
+ * _device: the same with device pointers on the batch's stream, no synchronisation.
+ * vqg_batch_set_wait_limit: spin limit of the dependency waits; stall_circuit >= 0 makes
+ *   that circuit's later phases wait for a count that is never reached (a test hook for
+ *   the timeout path); -1 disables it.
+ * vqg_batch_info: task count, persistent grid size, total parameters. */
+typedef struct vqg_batch vqg_batch;
+int vqg_batch_create(int n_circuits, const int *n_qubits, const vqg_gate *gates,
+                     const int *gate_offsets, const int *n_params, int dtype, vqg_batch **out);
+int vqg_batch_set_hamiltonian(vqg_batch *b, int circuit, int n_terms, const uint64_t *x_mask,
+                              const uint64_t *z_mask, const double *coef);
+int vqg_batch_set_stream(vqg_batch *b, void *stream);
+int vqg_batch_set_wait_limit(vqg_batch *b, long long spins, int stall_circuit);
+int vqg_batch_energy_and_gradient(vqg_batch *b, const double *theta, double *energies,
+                                  double *grads);
+int vqg_batch_energy_and_gradient_device(vqg_batch *b, const double *theta_dev,
+                                         double *energies_dev, double *grads_dev);
+int vqg_batch_info(vqg_batch *b, int *n_tasks, int *grid, int *total_params);
+int vqg_batch_destroy(vqg_batch *b);
+
 /* ---------------------------------------------------------------- allocation-free step
  * The paper has no counterpart to this entry point; it exists for callers that must
  * not allocate device memory while they run: a process whose device memory is owned

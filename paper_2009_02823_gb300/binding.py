@@ -92,6 +92,14 @@ def lib():
             "vqg_status_string": (ctypes.c_char_p, [i]),
             "vqg_reverse_noalloc": (i, [i, i, p, i, p, i, p, p, p, p]),
             "vqg_plan_dry_run": (i, [i, p, i, i, i, p, i, p, p, p, p]),
+            "vqg_batch_create": (i, [i, p, p, p, p, i, pp]),
+            "vqg_batch_set_hamiltonian": (i, [p, i, i, p, p, p]),
+            "vqg_batch_set_stream": (i, [p, p]),
+            "vqg_batch_set_wait_limit": (i, [p, ctypes.c_longlong, i]),
+            "vqg_batch_energy_and_gradient": (i, [p, p, p, p]),
+            "vqg_batch_energy_and_gradient_device": (i, [p, p, p, p]),
+            "vqg_batch_info": (i, [p, p, p, p]),
+            "vqg_batch_destroy": (i, [p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)

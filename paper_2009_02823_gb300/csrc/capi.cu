@@ -434,14 +434,52 @@ int Circuit::issue_finalize(double *energy_dev, double *grad_dev, const double *
     return check_launch("finalize");
 }
 
-int Circuit::run_gradient(const double *theta_dev, double *energy_dev, double *grad_dev) {
-    if (!has_ham) return set_error(VQG_ERR_STATE, "no Hamiltonian set");
+int Circuit::issue_gradient(const double *theta_dev, double *energy_dev, double *grad_dev) {
     int st;
     if ((st = issue_table(theta_dev, -1, -1, 0.0))) return st;
     if ((st = issue_forward(true))) return st;
     if ((st = issue_hamiltonian(true))) return st;
     if ((st = issue_reverse())) return st;
     return issue_finalize(energy_dev, grad_dev, theta_dev);
+}
+
+// With use_graph, the launch sequence of one call (it does not depend on theta: the
+// gate matrices are rebuilt on the device from theta_dev) is captured once per set of
+// argument pointers and replayed afterwards.  Profiling runs eagerly (it needs events
+// between launches); the legacy default stream cannot be captured and also runs eagerly.
+int Circuit::run_gradient(const double *theta_dev, double *energy_dev, double *grad_dev) {
+    if (!has_ham) return set_error(VQG_ERR_STATE, "no Hamiltonian set");
+    const bool graphable = opt.use_graph && !profiling && stream != cudaStreamLegacy && stream != nullptr;
+    if (!graphable) return issue_gradient(theta_dev, energy_dev, grad_dev);
+    const void *key[3] = {theta_dev, energy_dev, grad_dev};
+    if (graph_exec_grad && std::memcmp(key, graph_key_grad, sizeof key) != 0) {
+        cudaGraphExecDestroy(graph_exec_grad);
+        graph_exec_grad = nullptr;
+    }
+    if (!graph_exec_grad) {
+        if (!graph_warm) {  // first call eagerly: sets kernel attributes outside capture
+            graph_warm = true;
+            return issue_gradient(theta_dev, energy_dev, grad_dev);
+        }
+        cudaGraph_t g = nullptr;
+        VQG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        int st = issue_gradient(theta_dev, energy_dev, grad_dev);
+        cudaError_t e = cudaStreamEndCapture(stream, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&graph_exec_grad, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            graph_exec_grad = nullptr;
+            return set_error(VQG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        std::memcpy(graph_key_grad, key, sizeof key);
+    }
+    VQG_CUDA(cudaGraphLaunch(graph_exec_grad, stream));
+    return VQG_OK;
 }
 
 int Circuit::run_energy(const double *theta_dev, double *energy_dev, int sg, int ss, double sh) {

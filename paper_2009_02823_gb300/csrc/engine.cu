@@ -19,6 +19,7 @@
 
 #include "engine.h"
 #include "fused.h"
+#include "plan.h"
 
 namespace vqg {
 
@@ -36,7 +37,7 @@ bool launch_fused_rev_c64(VQG_REV_ARGS);
 bool launch_fused_rev_c128(VQG_REV_ARGS);
 
 // Compiled (tile qubits, register qubits) variants; every one fits shared memory.
-static bool fused_supported(bool dbl, int K, int Rf, int Rr) {
+bool fused_supported(bool dbl, int K, int Rf, int Rr) {
     if (!dbl) return K >= 10 && K <= 13 && (Rf == 4 || Rf == 5) && (Rr == 4 || (Rr == 3 && K <= 12));
     return K >= 10 && K <= 12 && (Rf == 3 || Rf == 4) && (Rr == 3 || (Rr == 2 && K <= 11));
 }
@@ -89,32 +90,6 @@ static void greedy(const std::vector<vqg_gate> &gates, const std::vector<int> &o
         }
     }
 }
-
-struct Plan {
-    int K = 0, L = 0, Rf = 0, Rr = 0;
-    uint64_t n_tiles = 0;
-    int grid_fwd = 0;
-    std::vector<FPass> passes;
-    std::vector<FStage> stages;
-    std::vector<FOp> ops;
-    std::vector<FDiag> diags;
-    std::vector<FDItem> items;
-    std::vector<int> slot_map;
-    std::vector<int> ckpt_of_pass;  // checkpoint index storing the output of pass j, or -1
-    std::vector<HPass> hp;
-    std::vector<HGroup> hg;
-    std::vector<HTerm> ht;
-    FPass *d_passes = nullptr;
-    FStage *d_stages = nullptr;
-    FOp *d_ops = nullptr;
-    FDiag *d_diags = nullptr;
-    FDItem *d_items = nullptr;
-    int *d_slot_map = nullptr;
-    HPass *d_hp = nullptr;
-    HGroup *d_hg = nullptr;
-    HTerm *d_ht = nullptr;
-    float *d_mats_f = nullptr;
-};
 
 // Tile layout of a pass: positions 0..L-1 are qubits 0..L-1, then `high` ascending.
 struct TileMap {
@@ -344,7 +319,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
 // Host-side check of every index a fused kernel derives from the plan: tile
 // geometry, register/thread bit assignment (a permutation of the K tile positions),
 // op fields, reduction slots and Hamiltonian masks.  Returns an empty string if valid.
-static std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
+std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
     char buf[256];
     const int K = pl.K, L = pl.L;
     auto fail = [&](const char *what, int a, int b) {
@@ -486,7 +461,7 @@ static int occupancy_grid(int num_sms, int per_sm, uint64_t n_tiles) {
 // Pure host planning of the gate passes (no device work).  Returns nullptr with an
 // empty `err` when no fused schedule applies (n or the tile below 10 qubits, fusion
 // off), nullptr with `err` set when the plan fails validation.
-static Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
+Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
                         int n_gslots, bool dbl, const vqg_options &opt, std::string &err) {
     err.clear();
     const int G = (int)gates.size();
@@ -599,7 +574,7 @@ int Circuit::build_plan() {
 // qubits are always inside; each pass adds the groups whose high flip bits fit).
 // Returns false (nothing planned) when some group cannot live in one tile: its flip
 // mask has more high bits than the tile has, or it has more terms than a pass holds.
-static bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
+bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
                              const std::vector<PauliTerm> &host_terms) {
     pl->hp.clear();
     pl->hg.clear();

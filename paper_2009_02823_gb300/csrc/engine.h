@@ -78,6 +78,8 @@ struct Circuit {
 
     // graphs
     cudaGraphExec_t graph_exec_grad = nullptr, graph_exec_energy = nullptr;
+    const void *graph_key_grad[3] = {nullptr, nullptr, nullptr};
+    bool graph_warm = false;
 
     // profiling
     bool profiling = false;
@@ -99,6 +101,7 @@ struct Circuit {
     int issue_hamiltonian(bool write_lam);
     int issue_reverse();
     int issue_finalize(double *energy_dev, double *grad_dev, const double *theta_dev);
+    int issue_gradient(const double *theta_dev, double *energy_dev, double *grad_dev);
     int run_gradient(const double *theta_dev, double *energy_dev, double *grad_dev);
     int run_energy(const double *theta_dev, double *energy_dev, int sg, int ss, double sh);
 

@@ -417,13 +417,15 @@ struct TileIO {
     static constexpr int CPR = (1 << L) / CA;   // chunks per 128-byte row
     static constexpr int CHUNKS = TILE / CA;
 
+    // L2ONLY: bypass L1 (needed when another block of the same launch wrote the data).
+    template <bool L2ONLY = false>
     static VQG_DEV void load(amp_t<T> *tile, const amp_t<T> *__restrict__ src, uint64_t base,
                              const uint64_t *row_off, int tid, int nt) {
         for (int c = tid; c < CHUNKS; c += nt) {
             const int row = c / CPR, col = c % CPR;
             const uint32_t t = (uint32_t)(row << L) | (uint32_t)(col * CA);
-            const float4 v = __ldcs(reinterpret_cast<const float4 *>(src + (base | row_off[row]) + col * CA));
-            put_chunk(tile, t, v);
+            const float4 *g = reinterpret_cast<const float4 *>(src + (base | row_off[row]) + col * CA);
+            put_chunk(tile, t, L2ONLY ? __ldcg(g) : __ldcs(g));
         }
     }
     static VQG_DEV void zero(amp_t<T> *tile, uint64_t base, int tid, int nt) {
@@ -495,6 +497,133 @@ VQG_DEV uint32_t reg_addr(uint32_t sb, const uint32_t (&w)[R], int j) {
     return ad;
 }
 
+// ------------------------------------------------------------------ per-tile bodies
+// One tile of a forward pass: load (or |0...0>), run the stages, store.
+template <typename T, int K, int R, bool L2ONLY>
+VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> &pg, int n_stage,
+                      uint64_t base, bool from_zero, const amp_t<T> *__restrict__ src,
+                      amp_t<T> *__restrict__ dst, int tid) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
+    if (from_zero) IO::zero(tile, base, tid, NT);
+    else IO::template load<L2ONLY>(tile, src, base, row_off, tid, NT);
+    __syncthreads();
+    for (int s = 0; s < n_stage; ++s) {
+        const FStage &st = pg.st[s];
+        uint32_t sb;
+        uint64_t gb;
+        thread_base<K, R, AB>(st, tid, base, sb, gb);
+        uint32_t w[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
+        A a[NA];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) a[j] = tile[reg_addr<R, NA>(sb, w, j)];
+        A phase = mk<T>((T)1, (T)0);
+        const int o0 = st.op0 - pg.op_base;
+        for (int o = o0; o < o0 + st.n_op; ++o) apply_fwd_op<R, NA, T>(a, pg, o, gb, phase);
+        asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
+#pragma unroll
+        for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = cmul<T>(phase, a[j]);
+        __syncthreads();
+    }
+    IO::store(tile, dst, base, row_off, tid, NT);
+    __syncthreads();
+}
+
+// One tile of a reverse pass; the block's reduction values accumulate in acc_w (this
+// warp's row of the FP64 accumulator).
+template <typename T, int K, int R, bool L2ONLY>
+VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, const Prog<T, R> &pg,
+                      int n_stage, uint64_t base, const amp_t<T> *__restrict__ phi_src,
+                      amp_t<T> *__restrict__ phi_dst, amp_t<T> *__restrict__ lam, double *acc_w, int tid) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
+    const int lane = tid & 31;
+    IO::template load<L2ONLY>(tphi, phi_src, base, row_off, tid, NT);
+    IO::template load<L2ONLY>(tlam, lam, base, row_off, tid, NT);
+    __syncthreads();
+    for (int s = 0; s < n_stage; ++s) {
+        const FStage &st = pg.st[s];
+        uint32_t sb;
+        uint64_t gb;
+        thread_base<K, R, AB>(st, tid, base, sb, gb);
+        uint32_t w[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
+        A a[NA], l[NA];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+            a[j] = tphi[ad];
+            l[j] = tlam[ad];
+        }
+        A phase = mk<T>((T)1, (T)0);
+        const int o0 = st.op0 - pg.op_base;
+        for (int o = o0; o < o0 + st.n_op; ++o) {
+            const FOp op = pg.op[o];
+            const A *m = pg.prm + 4 * o;
+            T v1 = 0;
+            bool red1 = false;
+            switch (op.type) {
+            case OP_RY: {
+                const A cs = m[0];
+                with_k<R>(op.k, [&](auto kb) { v1 = rev_ry<decltype(kb)::value, NA, T>(a, l, cs.x, cs.y); });
+                red1 = true;
+                break;
+            }
+            case OP_RX: {
+                const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+                with_k<R>(op.k, [&](auto kb) { v1 = rev_rx<decltype(kb)::value, NA, T>(a, l, ud); });
+                red1 = true;
+                break;
+            }
+            case OP_U3: {
+                const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+                T v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                with_k<R>(op.k, [&](auto kb) { rev_u3<decltype(kb)::value, NA, T>(a, l, ud, v8); });
+                const T tot = warp_reduce8<T>(v8);
+                if ((lane & 3) == 0) {
+                    const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                    acc_w[op.lslot + vi] += (double)tot;
+                }
+                break;
+            }
+            case OP_CNOT: {
+                const bool c = op.rm0 ? false : ((gb >> op.cq) & 1ull) != 0;
+                with_k<R>(op.k, [&](auto kb) {
+                    op_cnot<decltype(kb)::value, NA, T>(a, op.rm0, c);
+                    op_cnot<decltype(kb)::value, NA, T>(l, op.rm0, c);
+                });
+                break;
+            }
+            case OP_DIAG:
+                rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, acc_w, phase);
+                break;
+            default:
+                break;
+            }
+            if (red1) {
+                const T tot = warp_tree<T>(v1);
+                if (lane == 0) acc_w[op.lslot] += (double)tot;
+            }
+        }
+        asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+            tphi[ad] = cmul<T>(phase, a[j]);
+            tlam[ad] = cmul<T>(phase, l[j]);
+        }
+        __syncthreads();
+    }
+    IO::store(tphi, phi_dst, base, row_off, tid, NT);
+    IO::store(tlam, lam, base, row_off, tid, NT);
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ forward pass
 template <typename T, int K, int R>
 struct FwdCfg {
@@ -512,9 +641,8 @@ __global__ void __launch_bounds__(1 << (K - R), 2)
                 const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
                 const FDItem *__restrict__ items, const T *__restrict__ mats, uint64_t n_tiles) {
     using A = amp_t<T>;
-    using IO = TileIO<T, K>;
     using C = FwdCfg<T, K, R>;
-    constexpr int AB = FT<T>::AB, NT = C::NT, NA = 1 << R;
+    constexpr int NT = C::NT;
     extern __shared__ __align__(16) unsigned char smem[];
     A *tile = reinterpret_cast<A *>(smem);
     uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
@@ -524,36 +652,10 @@ __global__ void __launch_bounds__(1 << (K - R), 2)
     const int tid = threadIdx.x;
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
     load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, stages, ops, diags, items, mats, false, tid, NT);
-    const int n_stage = P.n_stage, n_nontile = P.n_nontile;
-    const bool from_zero = P.from_zero;
     __syncthreads();
-    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        const uint64_t base = tile_base(ti, P.nontile, n_nontile);
-        if (from_zero) IO::zero(tile, base, tid, NT);
-        else IO::load(tile, src, base, row_off, tid, NT);
-        __syncthreads();
-        for (int s = 0; s < n_stage; ++s) {
-            const FStage &st = pg.st[s];
-            uint32_t sb;
-            uint64_t gb;
-            thread_base<K, R, AB>(st, tid, base, sb, gb);
-            uint32_t w[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
-            A a[NA];
-#pragma unroll
-            for (int j = 0; j < NA; ++j) a[j] = tile[reg_addr<R, NA>(sb, w, j)];
-            A phase = mk<T>((T)1, (T)0);
-            const int o0 = st.op0 - pg.op_base;
-            for (int o = o0; o < o0 + st.n_op; ++o) apply_fwd_op<R, NA, T>(a, pg, o, gb, phase);
-            asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
-#pragma unroll
-            for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = cmul<T>(phase, a[j]);
-            __syncthreads();
-        }
-        IO::store(tile, dst, base, row_off, tid, NT);
-        __syncthreads();
-    }
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x)
+        fwd_tile<T, K, R, false>(tile, row_off, pg, P.n_stage, tile_base(ti, P.nontile, P.n_nontile),
+                                 P.from_zero != 0, src, dst, tid);
 }
 
 // ------------------------------------------------------------------ reverse pass
@@ -577,9 +679,8 @@ __global__ void __launch_bounds__(1 << (K - R))
                 const int *__restrict__ slot_map, const T *__restrict__ mats, uint64_t n_tiles,
                 double *__restrict__ partials, int nb) {
     using A = amp_t<T>;
-    using IO = TileIO<T, K>;
     using C = RevCfg<T, K, R>;
-    constexpr int AB = FT<T>::AB, NT = C::NT, NA = 1 << R, NW = C::NW;
+    constexpr int NT = C::NT, NW = C::NW;
     extern __shared__ __align__(16) unsigned char smem[];
     A *tphi = reinterpret_cast<A *>(smem);
     A *tlam = tphi + (1 << K);
@@ -589,98 +690,16 @@ __global__ void __launch_bounds__(1 << (K - R))
     double *acc = reinterpret_cast<double *>(smem + C::o_acc);
     int *smap = reinterpret_cast<int *>(smem + C::o_map);
     const FPass &P = passes[pi];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_stage = P.n_rstage, n_ls = P.n_lslots;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n_ls = P.n_lslots;
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
     for (int i = tid; i < NW * n_ls; i += NT) acc[i] = 0.0;
     for (int i = tid; i < n_ls; i += NT) smap[i] = slot_map[P.slotmap0 + i];
-    load_prog<T, R>(pg, P.rstage0, n_stage, P.rdiag0, P.n_rdiag, stages, ops, diags, items, mats, true, tid, NT);
-    double *acc_w = acc + warp * n_ls;
-    const int n_nontile = P.n_nontile;
+    load_prog<T, R>(pg, P.rstage0, P.n_rstage, P.rdiag0, P.n_rdiag, stages, ops, diags, items, mats, true, tid, NT);
     __syncthreads();
-    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        const uint64_t base = tile_base(ti, P.nontile, n_nontile);
-        IO::load(tphi, phi_src, base, row_off, tid, NT);
-        IO::load(tlam, lam, base, row_off, tid, NT);
-        __syncthreads();
-        for (int s = 0; s < n_stage; ++s) {
-            const FStage &st = pg.st[s];
-            uint32_t sb;
-            uint64_t gb;
-            thread_base<K, R, AB>(st, tid, base, sb, gb);
-            uint32_t w[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
-            A a[NA], l[NA];
-#pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
-                a[j] = tphi[ad];
-                l[j] = tlam[ad];
-            }
-            A phase = mk<T>((T)1, (T)0);
-            const int o0 = st.op0 - pg.op_base;
-            for (int o = o0; o < o0 + st.n_op; ++o) {
-                const FOp op = pg.op[o];
-                const A *m = pg.prm + 4 * o;
-                T v1 = 0;
-                bool red1 = false;
-                switch (op.type) {
-                case OP_RY: {
-                    const A cs = m[0];
-                    with_k<R>(op.k, [&](auto kb) { v1 = rev_ry<decltype(kb)::value, NA, T>(a, l, cs.x, cs.y); });
-                    red1 = true;
-                    break;
-                }
-                case OP_RX: {
-                    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
-                    with_k<R>(op.k, [&](auto kb) { v1 = rev_rx<decltype(kb)::value, NA, T>(a, l, ud); });
-                    red1 = true;
-                    break;
-                }
-                case OP_U3: {
-                    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
-                    T v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    with_k<R>(op.k, [&](auto kb) { rev_u3<decltype(kb)::value, NA, T>(a, l, ud, v8); });
-                    const T tot = warp_reduce8<T>(v8);
-                    if ((lane & 3) == 0) {
-                        const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                        acc_w[op.lslot + vi] += (double)tot;
-                    }
-                    break;
-                }
-                case OP_CNOT: {
-                    const bool c = op.rm0 ? false : ((gb >> op.cq) & 1ull) != 0;
-                    with_k<R>(op.k, [&](auto kb) {
-                        op_cnot<decltype(kb)::value, NA, T>(a, op.rm0, c);
-                        op_cnot<decltype(kb)::value, NA, T>(l, op.rm0, c);
-                    });
-                    break;
-                }
-                case OP_DIAG:
-                    rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, acc_w, phase);
-                    break;
-                default:
-                    break;
-                }
-                if (red1) {
-                    const T tot = warp_tree<T>(v1);
-                    if (lane == 0) acc_w[op.lslot] += (double)tot;
-                }
-            }
-            asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
-#pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
-                tphi[ad] = cmul<T>(phase, a[j]);
-                tlam[ad] = cmul<T>(phase, l[j]);
-            }
-            __syncthreads();
-        }
-        IO::store(tphi, phi_dst, base, row_off, tid, NT);
-        IO::store(tlam, lam, base, row_off, tid, NT);
-        __syncthreads();
-    }
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x)
+        rev_tile<T, K, R, false>(tphi, tlam, row_off, pg, P.n_rstage, tile_base(ti, P.nontile, P.n_nontile),
+                                 phi_src, phi_dst, lam, acc + warp * n_ls, tid);
     __syncthreads();
     for (int i = tid; i < n_ls; i += NT) {
         double s = 0.0;
@@ -699,12 +718,133 @@ __global__ void __launch_bounds__(1 << (K - R))
 template <typename T, int K>
 struct HamCfg {
     static constexpr int NT = 256;
-    static constexpr size_t smem() {
-        return (size_t)(1 << K) * FT<T>::AB + sizeof(uint64_t) * (1 << (K - FT<T>::L)) +
-               (sizeof(uint32_t) * 3) * kMaxHamGroups +
-               (sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
+    static constexpr size_t o_row = (size_t)(1 << K) * FT<T>::AB;
+    static constexpr size_t o_tab = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
+    static constexpr size_t tab_bytes = (sizeof(uint32_t) * 3) * kMaxHamGroups +
+                                        (sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
+    static constexpr size_t smem() { return o_tab + tab_bytes; }
+};
+
+template <typename T>
+struct HamTab {
+    uint64_t *t_znt;
+    amp_t<T> *t_w, *t_weff;
+    uint32_t *t_zl, *g_xl, *g_t0, *g_nt;
+    int ng, n_terms;
+    VQG_DEV void bind(unsigned char *p) {
+        t_znt = reinterpret_cast<uint64_t *>(p);
+        t_w = reinterpret_cast<amp_t<T> *>(t_znt + kMaxHamTerms);
+        t_weff = t_w + kMaxHamTerms;
+        t_zl = reinterpret_cast<uint32_t *>(t_weff + kMaxHamTerms);
+        g_xl = t_zl + kMaxHamTerms;
+        g_t0 = g_xl + kMaxHamGroups;
+        g_nt = g_t0 + kMaxHamGroups;
+    }
+    VQG_DEV void load(const HPass &P, const HGroup *__restrict__ groups, const HTerm *__restrict__ terms,
+                      int tid, int nt) {
+        ng = P.n_group;
+        const int term_base = ng ? groups[P.group0].term0 : 0;
+        n_terms = ng ? groups[P.group0 + ng - 1].term0 + groups[P.group0 + ng - 1].n_term - term_base : 0;
+        for (int g = tid; g < ng; g += nt) {
+            const HGroup G = groups[P.group0 + g];
+            g_xl[g] = G.xl;
+            g_t0[g] = (uint32_t)(G.term0 - term_base);
+            g_nt[g] = (uint32_t)G.n_term;
+        }
+        for (int k = tid; k < n_terms; k += nt) {
+            const HTerm tm = terms[term_base + k];
+            t_znt[k] = tm.znt;
+            t_zl[k] = tm.zl;
+            if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
+            else t_w[k] = mk<T>(tm.wr, tm.wi);
+        }
     }
 };
+
+// One tile of a Hamiltonian pass; returns this thread's FP32/FP64 partial of Re<psi|dlam>.
+template <typename T, int K, bool L2ONLY>
+VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T> &tb, uint64_t base, bool first,
+                   const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam, int tid) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
+    constexpr int CPT = IO::CHUNKS / NT;                      // chunks per thread per tile
+    constexpr int BCH = CPT < 8 / IO::CA ? CPT : 8 / IO::CA;  // chunks per batch
+    constexpr int BA = BCH * IO::CA;                          // amplitudes per batch
+    static_assert(CPT % BCH == 0, "batching");
+    IO::template load<L2ONLY>(tile, psi, base, row_off, tid, NT);
+    for (int k = tid; k < tb.n_terms; k += NT) {
+        const A w = tb.t_w[k];
+        tb.t_weff[k] = (__popcll(base & tb.t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;
+    }
+    __syncthreads();
+    T run = 0;
+#pragma unroll 1
+    for (int b0 = 0; b0 < CPT; b0 += BCH) {
+        uint32_t t[BA];
+        uint64_t gch[BCH];
+        A mine[BA], out[BA];
+#pragma unroll
+        for (int i = 0; i < BCH; ++i) {
+            const int c = tid + NT * (b0 + i);
+            const int row = c / IO::CPR, col = c % IO::CPR;
+            const uint32_t t0 = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
+            gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
+            union {
+                float4 f;
+                A a[IO::CA];
+            } u;
+            if (!first) {
+                const float4 *g = reinterpret_cast<const float4 *>(lam + gch[i]);
+                u.f = L2ONLY ? __ldcg(g) : __ldcs(g);
+            }
+#pragma unroll
+            for (int e = 0; e < IO::CA; ++e) {
+                t[i * IO::CA + e] = t0 + e;
+                mine[i * IO::CA + e] = tile[swz<AB>(t0 + e)];
+                out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : u.a[e];
+            }
+        }
+        for (int g = 0; g < tb.ng; ++g) {
+            const uint32_t xl = tb.g_xl[g];
+            const int j0 = tb.g_t0[g], j1 = j0 + tb.g_nt[g];
+            A f[BA], src[BA];
+#pragma unroll
+            for (int k = 0; k < BA; ++k) {
+                src[k] = tile[swz<AB>(t[k] ^ xl)];
+                f[k] = mk<T>((T)0, (T)0);
+            }
+            for (int j = j0; j < j1; ++j) {
+                const uint32_t zl = tb.t_zl[j];
+                const A w = tb.t_weff[j];
+#pragma unroll
+                for (int k = 0; k < BA; ++k) {
+                    const bool odd = __popc(t[k] & zl) & 1;
+                    f[k].x += odd ? -w.x : w.x;
+                    f[k].y += odd ? -w.y : w.y;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < BA; ++k) {
+                const A d = cmul<T>(f[k], src[k]);
+                out[k] = cadd<T>(out[k], d);
+                run += mine[k].x * d.x + mine[k].y * d.y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < BCH; ++i) {
+            union {
+                float4 f;
+                A a[IO::CA];
+            } u;
+#pragma unroll
+            for (int e = 0; e < IO::CA; ++e) u.a[e] = out[i * IO::CA + e];
+            __stcs(reinterpret_cast<float4 *>(lam + gch[i]), u.f);
+        }
+    }
+    __syncthreads();
+    return run;
+}
 
 template <typename T, int K>
 __global__ void __launch_bounds__(256)
@@ -712,121 +852,24 @@ __global__ void __launch_bounds__(256)
                 const HPass *__restrict__ hp, int pi, const HGroup *__restrict__ groups,
                 const HTerm *__restrict__ terms, uint64_t n_tiles, double *__restrict__ partials, int nb) {
     using A = amp_t<T>;
-    using IO = TileIO<T, K>;
-    constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
-    constexpr int CPT = IO::CHUNKS / NT;                 // chunks per thread per tile
-    constexpr int BCH = CPT < 8 / IO::CA ? CPT : 8 / IO::CA;  // chunks per batch
-    constexpr int BA = BCH * IO::CA;                     // amplitudes per batch
-    static_assert(CPT % BCH == 0, "batching");
+    using C = HamCfg<T, K>;
+    constexpr int NT = 256;
     extern __shared__ __align__(16) unsigned char smem[];
     A *tile = reinterpret_cast<A *>(smem);
-    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + (size_t)(1 << K) * AB);
-    uint64_t *t_znt = row_off + IO::ROWS;                          // [kMaxHamTerms]
-    A *t_w = reinterpret_cast<A *>(t_znt + kMaxHamTerms);          // [kMaxHamTerms] weights
-    A *t_weff = t_w + kMaxHamTerms;                                // [kMaxHamTerms] this tile
-    uint32_t *t_zl = reinterpret_cast<uint32_t *>(t_weff + kMaxHamTerms);
-    uint32_t *g_xl = t_zl + kMaxHamTerms;
-    uint32_t *g_t0 = g_xl + kMaxHamGroups;
-    uint32_t *g_nt = g_t0 + kMaxHamGroups;
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
+    HamTab<T> tb;
+    tb.bind(smem + C::o_tab);
     __shared__ double wsum[NT / 32];
     const HPass &P = hp[pi];
     const int tid = threadIdx.x;
-    for (int r = tid; r < IO::ROWS; r += NT) {
-        uint64_t off = 0;
-        for (int i = 0; i < K - L; ++i)
-            if ((r >> i) & 1) off |= 1ull << P.high[i];
-        row_off[r] = off;
-    }
-    const int ng = P.n_group;
-    const int term_base = ng ? groups[P.group0].term0 : 0;
-    const int n_terms = ng ? groups[P.group0 + ng - 1].term0 + groups[P.group0 + ng - 1].n_term - term_base : 0;
-    for (int g = tid; g < ng; g += NT) {
-        const HGroup G = groups[P.group0 + g];
-        g_xl[g] = G.xl;
-        g_t0[g] = (uint32_t)(G.term0 - term_base);
-        g_nt[g] = (uint32_t)G.n_term;
-    }
-    for (int k = tid; k < n_terms; k += NT) {
-        const HTerm tm = terms[term_base + k];
-        t_znt[k] = tm.znt;
-        t_zl[k] = tm.zl;
-        if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
-        else t_w[k] = mk<T>(tm.wr, tm.wi);
-    }
-    const bool first = P.first;
+    fill_row_offsets<T, K>(P.high, row_off, tid, NT);
+    tb.load(P, groups, terms, tid, NT);
     double eacc = 0.0;
     __syncthreads();
     for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        const uint64_t base = tile_base(ti, P.nontile, P.n_nontile);
-        IO::load(tile, psi, base, row_off, tid, NT);
-        for (int k = tid; k < n_terms; k += NT) {
-            const A w = t_w[k];
-            t_weff[k] = (__popcll(base & t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;
-        }
-        __syncthreads();
-        T run = 0;
-#pragma unroll 1
-        for (int b0 = 0; b0 < CPT; b0 += BCH) {
-            uint32_t t[BA];
-            uint64_t gch[BCH];
-            A mine[BA], out[BA];
-#pragma unroll
-            for (int i = 0; i < BCH; ++i) {
-                const int c = tid + NT * (b0 + i);
-                const int row = c / IO::CPR, col = c % IO::CPR;
-                const uint32_t t0 = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
-                gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
-                union {
-                    float4 f;
-                    A a[IO::CA];
-                } u;
-                if (!first) u.f = __ldcs(reinterpret_cast<const float4 *>(lam + gch[i]));
-#pragma unroll
-                for (int e = 0; e < IO::CA; ++e) {
-                    t[i * IO::CA + e] = t0 + e;
-                    mine[i * IO::CA + e] = tile[swz<AB>(t0 + e)];
-                    out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : u.a[e];
-                }
-            }
-            for (int g = 0; g < ng; ++g) {
-                const uint32_t xl = g_xl[g];
-                const int j0 = g_t0[g], j1 = j0 + g_nt[g];
-                A f[BA], src[BA];
-#pragma unroll
-                for (int k = 0; k < BA; ++k) {
-                    src[k] = tile[swz<AB>(t[k] ^ xl)];
-                    f[k] = mk<T>((T)0, (T)0);
-                }
-                for (int j = j0; j < j1; ++j) {
-                    const uint32_t zl = t_zl[j];
-                    const A w = t_weff[j];
-#pragma unroll
-                    for (int k = 0; k < BA; ++k) {
-                        const bool odd = __popc(t[k] & zl) & 1;
-                        f[k].x += odd ? -w.x : w.x;
-                        f[k].y += odd ? -w.y : w.y;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < BA; ++k) {
-                    const A d = cmul<T>(f[k], src[k]);
-                    out[k] = cadd<T>(out[k], d);
-                    run += mine[k].x * d.x + mine[k].y * d.y;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < BCH; ++i) {
-                union {
-                    float4 f;
-                    A a[IO::CA];
-                } u;
-#pragma unroll
-                for (int e = 0; e < IO::CA; ++e) u.a[e] = out[i * IO::CA + e];
-                __stcs(reinterpret_cast<float4 *>(lam + gch[i]), u.f);
-            }
-        }
+        const T run = ham_tile<T, K, false>(tile, row_off, tb, tile_base(ti, P.nontile, P.n_nontile),
+                                            P.first != 0, psi, lam, tid);
         eacc += (double)warp_tree<T>(run);
-        __syncthreads();
     }
     if ((tid & 31) == 0) wsum[tid >> 5] = eacc;
     __syncthreads();

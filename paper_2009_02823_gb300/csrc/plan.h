@@ -1,0 +1,49 @@
+// Host-side execution plan of the fused sweeps (built by engine.cu, also used by the
+// batched launch in batch.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/vqg.h"
+#include "engine.h"
+#include "fused.h"
+
+namespace vqg {
+
+struct Plan {
+    int K = 0, L = 0, Rf = 0, Rr = 0;
+    uint64_t n_tiles = 0;
+    int grid_fwd = 0;
+    std::vector<FPass> passes;
+    std::vector<FStage> stages;
+    std::vector<FOp> ops;
+    std::vector<FDiag> diags;
+    std::vector<FDItem> items;
+    std::vector<int> slot_map;
+    std::vector<int> ckpt_of_pass;  // checkpoint index storing the output of pass j, or -1
+    std::vector<HPass> hp;
+    std::vector<HGroup> hg;
+    std::vector<HTerm> ht;
+    FPass *d_passes = nullptr;
+    FStage *d_stages = nullptr;
+    FOp *d_ops = nullptr;
+    FDiag *d_diags = nullptr;
+    FDItem *d_items = nullptr;
+    int *d_slot_map = nullptr;
+    HPass *d_hp = nullptr;
+    HGroup *d_hg = nullptr;
+    HTerm *d_ht = nullptr;
+    float *d_mats_f = nullptr;
+};
+
+// Plan the gate passes of one circuit (host only; nullptr + empty err: no fused
+// schedule applies; nullptr + err: the plan failed its checks).
+Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
+                 int n_gslots, bool dbl, const vqg_options &opt, std::string &err);
+// Hamiltonian tile passes of a plan; false if some group cannot live in one tile.
+bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham, const std::vector<PauliTerm> &host_terms);
+std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl);
+bool fused_supported(bool dbl, int K, int Rf, int Rr);
+
+}  // namespace vqg

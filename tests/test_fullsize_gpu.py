@@ -1,0 +1,91 @@
+"""Parity at the workloads' full sizes, in the configuration bench.py times.
+
+Expected values come from tests/golden/*.json, written by tests/golden/make_golden.py
+with the CPU oracle only (Algorithm 1 in complex128).  At n=30 the oracle gives the
+energy; the gradient there is checked by properties that hold at any size: equality
+with the complex128 path and with central finite differences of the complex128 energy
+on sampled parameters."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2009_02823_gb300 import workloads as W
+from tests.tolerances import TOL, assert_parity, energy_err, grad_err
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    path = os.path.join(GOLD, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"fixture {name} not generated")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def _circ(w, dtype, **kw):
+    from paper_2009_02823_gb300 import Circuit
+    c = Circuit(w.n, w.gates, w.n_params, dtype, **kw)
+    c.set_hamiltonian(w.terms)
+    return c
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("cfg", [2, 5])
+def test_full_gradient_vs_oracle(cfg, dtype):
+    w = W.config(cfg)
+    gold = _gold(f"cfg{cfg}_n{w.n}")
+    assert gold["workload"] == w.name
+    with _circ(w, dtype) as c:
+        e, g = c.energy_and_gradient(w.theta)
+    assert_parity(dtype, e, g, gold["energy"], np.array(gold["grad"]), w.name)
+
+
+def test_n30_bench_configuration():
+    """n=30, 745 gates, 200 Pauli strings, complex64 with the default fused schedule
+    and checkpoints (what bench.py times)."""
+    w = W.config(3)
+    gold = _gold(f"cfg3_n{w.n}_energy")
+    with _circ(w, "c64") as c:
+        e64, g64 = c.energy_and_gradient(w.theta)
+        assert c.plan()["checkpoints"] >= 1
+        e64b, g64b = c.energy_and_gradient(w.theta)
+    assert e64 == e64b and np.array_equal(g64, g64b)  # deterministic reductions
+    assert energy_err(e64, gold["energy"]) <= TOL["c64"]
+    with _circ(w, "c128") as c:
+        e128, g128 = c.energy_and_gradient(w.theta)
+        assert energy_err(e128, gold["energy"]) <= TOL["c128"]
+        assert grad_err(g64, g128) <= TOL["c64"]
+        rng = np.random.default_rng(2009)
+        d = 1e-4
+        for p in [0, w.n_params - 1] + list(rng.choice(w.n_params, 2, replace=False)):
+            tp, tm = w.theta.copy(), w.theta.copy()
+            tp[p] += d
+            tm[p] -= d
+            fd = (c.energy(tp) - c.energy(tm)) / (2 * d)
+            assert g128[p] == pytest.approx(fd, abs=1e-7)
+
+
+def test_cfg5_adam_full_size():
+    """n=26 U3 + CZ brickwork with TFIM: 50 Adam steps (lr 0.01) through autograd; the
+    step-0 gradient equals the oracle's."""
+    import torch
+
+    from paper_2009_02823_gb300.autograd import VariationalEnergy
+    w = W.config(5)
+    gold = _gold(f"cfg5_n{w.n}")
+    m = VariationalEnergy(w.n, w.gates, w.n_params, w.terms, "c64", theta0=w.theta, device="cuda")
+    opt = torch.optim.Adam(m.parameters(), lr=0.01)
+    energies = []
+    for step in range(50):
+        opt.zero_grad()
+        e = m()
+        e.backward()
+        if step == 0:
+            assert grad_err(m.theta.grad.cpu().numpy(), np.array(gold["grad"])) <= TOL["c64"]
+        opt.step()
+        energies.append(float(e))
+    assert np.all(np.isfinite(energies)) and energies[-1] < energies[0]

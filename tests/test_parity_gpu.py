@@ -232,3 +232,18 @@ def test_fused_register_variants(case, dtype, K, Rf, Rr):
     with _circ(n, gates, P, dtype, terms, tile_qubits=K, fwd_reg_qubits=Rf, rev_reg_qubits=Rr) as c:
         e, g = c.energy_and_gradient(theta)
         assert_parity(dtype, e, g, e_ref, g_ref, f"{case} K={K} R=({Rf},{Rr})")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_cuda_graph_replay(dtype):
+    """use_graph: the captured launch sequence replays with new theta values."""
+    import torch
+    w = W.config(3, n=13, layers=3)
+    s = torch.cuda.Stream()
+    with _circ(w.n, w.gates, w.n_params, dtype, w.terms, use_graph=True, stream=s) as c:
+        rng = np.random.default_rng(8)
+        for k in range(4):
+            th = w.theta if k == 0 else rng.uniform(0, 2 * np.pi, w.n_params)
+            e_ref, g_ref = _oracle(w.n, w.gates, th, w.n_params, w.terms)
+            e, g = c.energy_and_gradient(th)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"graph call {k}")
