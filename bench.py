@@ -107,7 +107,34 @@ class Clocks:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
-# ---------------------------------------------------------------- algorithmic bytes
+# ---------------------------------------------------------------- algorithmic work
+# Useful FP32 lane operations per amplitude (an FMA counts once) of each gate kind in the
+# fused sweeps: forward U applied to psi; reverse U^dagger applied to phi and lambda plus
+# the gradient products (Im<lambda|sigma|phi>: RY/RX 2, RZ 1; U3's four sums o_rc: 8).
+FWD_OPS = {"RY": 4, "RX": 8, "U3": 8, "RZ": 4, "CZ": 0, "CNOT": 0}
+REV_OPS = {"RY": 10, "RX": 18, "U3": 24, "RZ": 9, "CZ": 0, "CNOT": 0}
+
+
+def family_alu_ops(fam: str, w) -> float | None:
+    """Useful FP32 operations of one whole sweep of a kernel family (all its launches in
+    one gradient): per-amplitude counts x 2^n."""
+    amps = float(1 << w.n)
+    if fam in ("fwd_fused", "fwd_gate"):
+        return amps * sum(FWD_OPS[g[0]] for g in w.gates)
+    if fam in ("adj_fused", "adj_gate"):
+        return amps * sum(REV_OPS[g[0]] for g in w.gates)
+    if fam in ("ham_fused", "ham_group", "ham_diag"):
+        groups = len({tuple(sorted(q for q, l in ops if l in "XY")) for _c, ops in w.terms})
+        return amps * (2 * len(w.terms) + 8 * groups)  # sign-weighted sums; complex MAC + energy
+    return None
+
+
+def alu_peak(sm_mhz: float | None) -> tuple[float, str]:
+    """FP32 lane-op peak: 152 SMs x 128 FP32 lanes x SM clock (sampled during the run)."""
+    mhz = sm_mhz or 2070.0
+    return 152 * 128 * mhz * 1e6 / 1e9, f"152 SM x 128 FP32 lanes x {mhz:.0f} MHz (sampled)"
+
+
 def family_bytes(fam: str, w, S: int, plan: dict) -> float | None:
     """Algorithmic bytes per launch of a kernel family (one state traversal = S bytes
     read or written; Algorithm 1's cost unit, one gate primitive = O(2^n))."""
@@ -197,23 +224,54 @@ def run_ours(args, rank, world, dist):
     e2e = {"value": world * e2e_steps / t_e, "unit": UNIT,
            "h2d_bytes_per_step": 8 * w.n_params, "d2h_bytes_per_step": 8 * (w.n_params + 1)}
 
-    # roofline of the dominant kernel family
+    # roofline of the dominant kernel family (per-launch CUDA events inside the timed region)
     plan = circ.plan()
     peak, peak_kind = _peaks()
     fam, (launches, tot_ms) = max(stats.items(), key=lambda kv: kv[1][1])
-    per = family_bytes(fam, w, S, plan)
     roof = None
-    if per is not None and launches:
+    per_family = {}
+    total_ms = max(sum(v[1] for v in stats.values()), 1e-9)
+    for f, (nl, ms) in stats.items():
+        if not nl or ms <= 0:
+            continue
+        per = family_bytes(f, w, S, plan)
+        ops = family_alu_ops(f, w)
+        ent = {"launches": nl, "ms": round(ms, 3), "share": round(ms / total_ms, 4)}
+        if per is not None:
+            ent["hbm_gbs"] = round(per / (ms / nl / 1e3) / 1e9, 1)
+            ent["hbm_frac"] = round(ent["hbm_gbs"] / peak, 4)
+        if ops is not None:
+            gops = ops * args.steps / (ms / 1e3) / 1e9
+            ent["alu_gops"] = round(gops, 1)
+            ent["alu_frac"] = round(gops / alu_peak(clk.get("sm_mhz"))[0], 4)
+        per_family[f] = ent
+    if launches:
         avg_s = tot_ms / launches / 1e3
-        ach = per / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": fam, "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
-                "traffic": None, "bytes_per_launch": per, "launches": launches,
-                "avg_launch_ms": round(tot_ms / launches, 4),
-                "share_of_step": round(tot_ms / max(sum(v[1] for v in stats.values()), 1e-9), 4)}
+        per = family_bytes(fam, w, S, plan)
+        hbm = per / avg_s / 1e9 if per else None
+        fused = fam.endswith("_fused")
+        ops = family_alu_ops(fam, w)
+        if fused and ops:
+            apk, apk_src = alu_peak(clk.get("sm_mhz"))
+            ach = ops * args.steps / (tot_ms / 1e3) / 1e9
+            roof = {"bound": "alu", "kernel": fam, "achieved": round(ach, 1), "peak": round(apk, 1),
+                    "unit": "GFLOP32-lane-op/s", "frac": round(ach / apk, 4), "peak_source": apk_src,
+                    "ops_per_launch": ops / max(launches / args.steps, 1),
+                    "hbm": {"achieved": round(hbm, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(hbm / peak, 4), "peak_source": peak_kind,
+                            "bytes_per_launch": per},
+                    "traffic": None, "launches": launches, "avg_launch_ms": round(tot_ms / launches, 4),
+                    "share_of_step": round(tot_ms / total_ms, 4)}
+        elif per is not None:
+            roof = {"bound": "hbm", "kernel": fam, "achieved": round(hbm, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(hbm / peak, 4), "peak_source": peak_kind,
+                    "traffic": None, "bytes_per_launch": per, "launches": launches,
+                    "avg_launch_ms": round(tot_ms / launches, 4), "share_of_step": round(tot_ms / total_ms, 4)}
     gpu_launches = int(sum(v[0] for v in stats.values()))
 
     extra = {}
+    if rank == 0 and not args.no_batch:
+        extra["batched"] = batched_rate(args)
     if rank == 0 and not args.no_ps:
         extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
     if rank == 0 and not args.no_cpu:
@@ -228,12 +286,43 @@ def run_ours(args, rank, world, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic (seeded; no dataset)", "config": _config(args, w, {"plan": plan}),
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
-            "kernel_families_ms": {k: [v[0], round(v[1], 3)] for k, v in stats.items()},
-            "energy": e_val}
+            "kernel_families": per_family, "energy": e_val}
     if cpu:
         line["cpu_baseline"] = cpu
     line.update(extra)
     return line
+
+
+def batched_rate(args):
+    """512-circuit batch (n 12..20, 4..16 layers, TFIM): circuit gradients per second
+    through one persistent launch replayed from a CUDA graph (device buffers)."""
+    import torch
+
+    from paper_2009_02823_gb300 import workloads as W
+    from paper_2009_02823_gb300.batch import Batch
+    ws = W.batched()
+    stream = torch.cuda.Stream()
+    b = Batch(ws, stream=stream)
+    th = torch.tensor(np.concatenate([w.theta for w in ws]), dtype=torch.float64, device="cuda")
+    e = torch.zeros(len(ws), dtype=torch.float64, device="cuda")
+    g = torch.zeros(th.numel(), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):
+        b.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    t0.record(stream)
+    for _ in range(reps):
+        b.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    info = b.info()
+    b.close()
+    return {"workload": "512 circuits, n 12..20, 4..16 layers RY/RZ + CNOT ladder, TFIM h~U[0.5,1.5]",
+            "ms_per_batch": round(ms, 3), "circuit_gradients_per_s": round(len(ws) / (ms / 1e3), 1),
+            "tasks": info["tasks"], "grid": info["grid"], "launches_per_batch": 2}
 
 
 def param_shift_baseline(args, circ, w, theta_h, adjoint_rate):
@@ -370,6 +459,7 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--layers", type=int, default=None)
     ap.add_argument("--no-ps", action="store_true", help="skip the GPU parameter-shift baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch figure")
     ap.add_argument("--ps-evals", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

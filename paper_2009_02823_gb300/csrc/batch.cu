@@ -175,23 +175,19 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             Prog<T, R> pg;
             pg.bind(smem + RC::o_prog);
             double *acc = reinterpret_cast<double *>(smem + RC::o_acc);
+            T *stash = reinterpret_cast<T *>(smem + RC::o_stash);
             int *smap = reinterpret_cast<int *>(smem + RC::o_map);
             const int n_ls = P.n_lslots;
             fill_row_offsets<T, K>(P.high, row_off, tid, kBNT);
-            for (int i = tid; i < NW * n_ls; i += kBNT) acc[i] = 0.0;
-            for (int i = tid; i < n_ls; i += kBNT) smap[i] = a.slot_map[P.slotmap0 + i];
+            for (int i = tid; i < n_ls; i += kBNT) acc[i] = 0.0, smap[i] = a.slot_map[P.slotmap0 + i];
             load_prog<T, R>(pg, P.rstage0, P.n_rstage, P.rdiag0, P.n_rdiag, a.stages, a.ops, a.diags, a.items,
                             a.mats, true, tid, kBNT);
             __syncthreads();
             for (int ti = t0; ti < t1; ++ti)
                 rev_tile<T, K, R, true>(tphi, tlam, row_off, pg, P.n_rstage, tile_base(ti, P.nontile, P.n_nontile),
-                                        psi, psi, lam, acc + warp * n_ls, tid);
+                                        psi, psi, lam, acc, stash, tid);
             __syncthreads();
-            for (int i = tid; i < n_ls; i += kBNT) {
-                double s = 0.0;
-                for (int w = 0; w < NW; ++w) s += acc[w * n_ls + i];
-                part[(size_t)(H + smap[i]) * C.chunks + tk.chunk] = s;
-            }
+            for (int i = tid; i < n_ls; i += kBNT) part[(size_t)(H + smap[i]) * C.chunks + tk.chunk] = acc[i];
         } else if (ok) {  // finalize: E and the gradient of this circuit (fixed-order sums)
             if (tid == 0) {
                 double e = 0.0;

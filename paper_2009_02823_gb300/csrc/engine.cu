@@ -168,7 +168,8 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             if (!isreg[p]) isreg[p] = 1, regs.push_back(p);
         std::vector<char> inS(n, 0);
         for (int p : regs) inS[tm.qubit_of[p]] = 1;
-        greedy(gates, uns, inS, n, kMaxPassOps, kMaxPassSlots, applied, left);
+        greedy(gates, uns, inS, n, kMaxPassOps,
+               reverse ? (dbl ? kMaxStageRowsDbl : kMaxStageRows) : kMaxPassSlots, applied, left);
         const int NL = dbl ? 3 : 4, MOD = dbl ? 3 : 4;
         std::vector<int> thr;
         std::vector<char> used(K, 0);
@@ -237,6 +238,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             }
         }
         st.op0 = (int)pl.ops.size();
+        int rows = 0;
         for (const StageItem &it : out) {
             FOp op;
             std::memset(&op, 0, sizeof op);
@@ -265,7 +267,11 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                     const int nv = red_values(g.kind);
                     if (nv) {
                         op.lslot = (int16_t)n_lslots;
-                        for (int v = 0; v < nv; ++v) pl.slot_map.push_back(slot_base[i] + v);
+                        op.row = (int8_t)rows;
+                        for (int v = 0; v < nv; ++v) {
+                            pl.slot_map.push_back(slot_base[i] + v);
+                            st.row_slot[rows++] = (int16_t)(n_lslots + v);
+                        }
                         n_lslots += nv;
                     }
                 }
@@ -273,6 +279,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                 op.type = OP_DIAG;
                 op.gate = -1;
                 op.cq = -1;
+                op.row = (int8_t)rows;
                 op.diag = (int16_t)((int)pl.diags.size() - diag0);
                 FDiag d;
                 std::memset(&d, 0, sizeof d);
@@ -292,6 +299,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                             if (reverse) {
                                 x.lslot = n_lslots++;
                                 pl.slot_map.push_back(slot_base[i]);
+                                st.row_slot[rows++] = (int16_t)x.lslot;
                             }
                             d.n_rz++;
                         } else {
@@ -309,6 +317,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             pl.ops.push_back(op);
         }
         st.n_op = (int)pl.ops.size() - st.op0;
+        st.n_rows = rows;
         pl.stages.push_back(st);
         ++n_stage;
         uns.swap(left);
@@ -381,6 +390,12 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                     if (v >> K) return fail("swizzled mask range", s, (int)v);
                 for (int k = 0; k < K - R; ++k)
                     if (st.thr_q[k] < 0 || st.thr_q[k] >= n) return fail("thread qubit", s, st.thr_q[k]);
+                if (dir) {
+                    if (st.n_rows < 0 || st.n_rows > (dbl ? kMaxStageRowsDbl : kMaxStageRows))
+                        return fail("stage rows", s, st.n_rows);
+                    for (int r = 0; r < st.n_rows; ++r)
+                        if (st.row_slot[r] < 0 || st.row_slot[r] >= p.n_lslots) return fail("row slot", s, st.row_slot[r]);
+                }
                 for (int o = st.op0; o < st.op0 + st.n_op; ++o) {
                     const FOp &op = pl.ops[o];
                     if (op.type < OP_RY || op.type > OP_DIAG) return fail("op type", o, op.type);
@@ -392,6 +407,11 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                     if (dir && op.lslot >= 0) {
                         const int nv = op.type == OP_U3 ? 8 : 1;
                         if (op.lslot + nv > p.n_lslots) return fail("local slot", o, op.lslot);
+                        if (op.row < 0 || op.row + nv > st.n_rows) return fail("stash row", o, op.row);
+                    }
+                    if (dir && op.type == OP_DIAG) {
+                        const FDiag &D = pl.diags[p.rdiag0 + op.diag];
+                        if (op.row < 0 || op.row + D.n_rz > st.n_rows) return fail("diag stash row", o, op.row);
                     }
                     if (op.type == OP_DIAG) {
                         const int d0 = dir ? p.rdiag0 : p.diag0, nd = dir ? p.n_rdiag : p.n_diag;
@@ -449,7 +469,6 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
             if (G0.term0 < 0 || G0.term0 + G0.n_term > (int)pl.ht.size()) return fail("term range", g, G0.term0);
         }
     }
-    (void)dbl;
     return "";
 }
 

@@ -25,6 +25,8 @@ constexpr int kMaxPassDiags = 48;    // diagonal blocks per pass
 constexpr int kMaxPassItems = 320;   // diagonal-block items per pass
 constexpr int kMaxDiagRz = 8;        // RZ gates per diagonal block
 constexpr int kMaxDiagCz = 16;       // CZ gates per diagonal block
+constexpr int kMaxStageRows = 16;    // reverse reduction values per register stage (complex64)
+constexpr int kMaxStageRowsDbl = 8;  // the same for complex128 (FP64 stash)
 constexpr int kMaxHamGroups = 256;   // groups per Hamiltonian pass
 constexpr int kMaxHamTerms = 1024;   // terms per Hamiltonian pass
 
@@ -64,12 +66,14 @@ struct FStage {
     uint16_t reg_sw[kMaxRegBits + 3];    // swizzled tile-local mask of register bit k
     int8_t thr_q[kMaxThreadBits];        // global qubit of thread bit b
     int32_t op0, n_op;
+    int16_t row_slot[kMaxStageRows];     // reverse: local reduction slot of each stash row
+    int32_t n_rows;                      // reverse: stash rows used by this stage
 };
 
 struct FOp {          // 16 bytes: one shared-memory vector load
     int8_t type, k;   // k: register bit of the non-diagonal target
     int8_t cq;        // CNOT: global qubit of a control that is not a register bit, else -1
-    int8_t pad;
+    int8_t row;       // reverse: first stash row of this op's reduction values
     int16_t diag;     // OP_DIAG: block index within the pass
     int16_t lslot;    // reverse: first local reduction value (-1: none)
     uint32_t rm0;     // CNOT: register mask of the control (0: control not a register bit)

@@ -14,8 +14,9 @@
 //                 the tile, lambda (+)= sum_g f_g(j^x) psi[j^x], with E = Re<psi|lambda>.
 //
 // Reduction precision (complex64 amplitudes): products in FP32, per-thread runs of at
-// most 16 terms in FP32, the 32-lane warp tree in FP32, then every warp sum is added
-// into an FP64 accumulator (shared memory), and block / grid levels are FP64.
+// most 16 terms in FP32; in the reverse pass the block's per-thread partials of one tile
+// are summed in FP32 (lane runs of NT/32 values, then the 32-lane tree) and added to an
+// FP64 accumulator per tile; block and grid levels are FP64.
 #pragma once
 #include <type_traits>
 
@@ -352,7 +353,7 @@ VQG_DEV void rev_u3(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud, T (
 // bit k needs sum_j (-1)^{j_k} p_j and an RZ on a thread-level qubit +-sum_j p_j.
 template <int R, int NA, typename T>
 VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg, const FDiag &D,
-                      int di, uint64_t gb, double *acc_w, amp_t<T> &phase) {
+                      int di, uint64_t gb, T *stash_row, int nt, amp_t<T> &phase) {
     if (D.n_rz > 0) {
         T S = 0, H[R];
 #pragma unroll
@@ -383,15 +384,9 @@ VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg
                 }
             }
         }
-        const int lane = threadIdx.x & 31;
-        if (D.n_rz == 1) {
-            const T tot = warp_tree<T>(v[0]);
-            if (lane == 0) acc_w[pg.it[i0].lslot] += (double)tot;
-        } else {
-            const T tot = warp_reduce8<T>(v);
-            const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-            if ((lane & 3) == 0 && vi < D.n_rz) acc_w[pg.it[i0 + vi].lslot] += (double)tot;
-        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (r < D.n_rz) stash_row[r * nt] = v[r];
     }
     amp_t<T> tau;
     uint32_t c;
@@ -532,16 +527,33 @@ VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> 
     __syncthreads();
 }
 
-// One tile of a reverse pass; the block's reduction values accumulate in acc_w (this
-// warp's row of the FP64 accumulator).
+// Reduce a stage's stash rows (per-thread FP32 partials) into the per-slot FP64
+// accumulators: one warp per row, lanes sum NT/32 partials each, then the 32-lane tree;
+// fixed order, so results are reproducible.
+template <typename T, int NT>
+VQG_DEV void reduce_stash(const T *stash, const FStage &st, double *acc, int tid) {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < st.n_rows; r += NT / 32) {
+        T v = 0;
+        for (int i = lane; i < NT; i += 32) v += stash[r * NT + i];
+        v = warp_tree<T>(v);
+        if (lane == 0) acc[st.row_slot[r]] += (double)v;
+    }
+}
+
+template <typename T> constexpr int stash_rows() { return sizeof(T) == 4 ? kMaxStageRows : kMaxStageRowsDbl; }
+
+// One tile of a reverse pass.  Each op stores its per-thread FP32 partial(s) in the
+// stage's stash rows (no cross-lane dependency in the op loop); after the stage the
+// rows are reduced into acc (FP64, one value per local slot).
 template <typename T, int K, int R, bool L2ONLY>
 VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, const Prog<T, R> &pg,
                       int n_stage, uint64_t base, const amp_t<T> *__restrict__ phi_src,
-                      amp_t<T> *__restrict__ phi_dst, amp_t<T> *__restrict__ lam, double *acc_w, int tid) {
+                      amp_t<T> *__restrict__ phi_dst, amp_t<T> *__restrict__ lam, double *acc,
+                      T *stash, int tid) {
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
     constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
-    const int lane = tid & 31;
     IO::template load<L2ONLY>(tphi, phi_src, base, row_off, tid, NT);
     IO::template load<L2ONLY>(tlam, lam, base, row_off, tid, NT);
     __syncthreads();
@@ -584,11 +596,8 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
                 const Mat2<T> ud = dagger<T>(mat_of<T>(m));
                 T v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 with_k<R>(op.k, [&](auto kb) { rev_u3<decltype(kb)::value, NA, T>(a, l, ud, v8); });
-                const T tot = warp_reduce8<T>(v8);
-                if ((lane & 3) == 0) {
-                    const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                    acc_w[op.lslot + vi] += (double)tot;
-                }
+#pragma unroll
+                for (int x = 0; x < 8; ++x) stash[(op.row + x) * NT + tid] = v8[x];
                 break;
             }
             case OP_CNOT: {
@@ -600,15 +609,12 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
                 break;
             }
             case OP_DIAG:
-                rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, acc_w, phase);
+                rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, stash + op.row * NT + tid, NT, phase);
                 break;
             default:
                 break;
             }
-            if (red1) {
-                const T tot = warp_tree<T>(v1);
-                if (lane == 0) acc_w[op.lslot] += (double)tot;
-            }
+            if (red1) stash[op.row * NT + tid] = v1;
         }
         asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
 #pragma unroll
@@ -618,6 +624,10 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             tlam[ad] = cmul<T>(phase, l[j]);
         }
         __syncthreads();
+        if (st.n_rows) {
+            reduce_stash<T, NT>(stash, st, acc, tid);
+            __syncthreads();
+        }
     }
     IO::store(tphi, phi_dst, base, row_off, tid, NT);
     IO::store(tlam, lam, base, row_off, tid, NT);
@@ -635,7 +645,7 @@ struct FwdCfg {
 };
 
 template <typename T, int K, int R>
-__global__ void __launch_bounds__(1 << (K - R), 2)
+__global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
     k_fused_fwd(const amp_t<T> *__restrict__ src, amp_t<T> *__restrict__ dst,
                 const FPass *__restrict__ passes, int pi, const FStage *__restrict__ stages,
                 const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
@@ -665,7 +675,8 @@ struct RevCfg {
     static constexpr size_t o_row = 2 * (size_t)(1 << K) * FT<T>::AB;
     static constexpr size_t o_prog = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
     static constexpr size_t o_acc = o_prog + Prog<T, R>::bytes;
-    static constexpr size_t o_map = o_acc + sizeof(double) * (size_t)NW * kMaxPassSlots;
+    static constexpr size_t o_stash = o_acc + sizeof(double) * kMaxPassSlots;
+    static constexpr size_t o_map = o_stash + sizeof(T) * (size_t)stash_rows<T>() * NT;
     static constexpr size_t smem() { return o_map + sizeof(int) * kMaxPassSlots; }
     static_assert(o_map + sizeof(int) * kMaxPassSlots <= 227 * 1024, "reverse pass exceeds shared memory");
 };
@@ -688,24 +699,21 @@ __global__ void __launch_bounds__(1 << (K - R))
     Prog<T, R> pg;
     pg.bind(smem + C::o_prog);
     double *acc = reinterpret_cast<double *>(smem + C::o_acc);
+    T *stash = reinterpret_cast<T *>(smem + C::o_stash);
     int *smap = reinterpret_cast<int *>(smem + C::o_map);
     const FPass &P = passes[pi];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int n_ls = P.n_lslots;
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
-    for (int i = tid; i < NW * n_ls; i += NT) acc[i] = 0.0;
-    for (int i = tid; i < n_ls; i += NT) smap[i] = slot_map[P.slotmap0 + i];
+    for (int i = tid; i < n_ls; i += NT) acc[i] = 0.0, smap[i] = slot_map[P.slotmap0 + i];
     load_prog<T, R>(pg, P.rstage0, P.n_rstage, P.rdiag0, P.n_rdiag, stages, ops, diags, items, mats, true, tid, NT);
     __syncthreads();
     for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x)
         rev_tile<T, K, R, false>(tphi, tlam, row_off, pg, P.n_rstage, tile_base(ti, P.nontile, P.n_nontile),
-                                 phi_src, phi_dst, lam, acc + warp * n_ls, tid);
+                                 phi_src, phi_dst, lam, acc, stash, tid);
     __syncthreads();
-    for (int i = tid; i < n_ls; i += NT) {
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += acc[w * n_ls + i];
-        partials[(size_t)smap[i] * nb + blockIdx.x] = s;
-    }
+    for (int i = tid; i < n_ls; i += NT) partials[(size_t)smap[i] * nb + blockIdx.x] = acc[i];
+    (void)NW;
 }
 
 // ------------------------------------------------------------------ Hamiltonian pass
