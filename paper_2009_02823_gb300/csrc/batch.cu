@@ -149,10 +149,11 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             const HPass &P = a.hp[C.hpass0 + tk.phase - F];
             A *tile = reinterpret_cast<A *>(smem);
             uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + HC::o_row);
-            HamTab<T> tb;
+            HamTab<T, K> tb;
             tb.bind(smem + HC::o_tab);
             fill_row_offsets<T, K>(P.high, row_off, tid, kBNT);
-            tb.load(P, a.hg, a.ht, tid, kBNT);
+            using G = HamGeo<T, K>;
+            tb.template load<G::D, G::SH, G::E0>(P, a.hg, a.ht, tid, kBNT);
             __syncthreads();
             double eacc = 0.0;
             for (int ti = t0; ti < t1; ++ti) {

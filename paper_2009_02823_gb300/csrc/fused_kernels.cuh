@@ -729,25 +729,32 @@ struct HamCfg {
     static constexpr size_t o_row = (size_t)(1 << K) * FT<T>::AB;
     static constexpr size_t o_tab = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
     static constexpr size_t tab_bytes = (sizeof(uint32_t) * 3) * kMaxHamGroups +
-                                        (sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
+                                        (2 * sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
     static constexpr size_t smem() { return o_tab + tab_bytes; }
 };
 
-template <typename T>
+// Shared-memory tables of one Hamiltonian pass.  Per term: the non-tile part of z (for
+// the per-tile sign), the tile-local part z_l, the weight, and its "class": the bits of
+// z_l at the positions where the amplitudes of one register batch differ (see
+// ham_tile), with the matching sign pattern over the batch.
+template <typename T, int K>
 struct HamTab {
+    static constexpr int AB = FT<T>::AB;
     uint64_t *t_znt;
     amp_t<T> *t_w, *t_weff;
-    uint32_t *t_zl, *g_xl, *g_t0, *g_nt;
+    uint32_t *t_zl, *t_cls, *g_xs, *g_t0, *g_nt;
     int ng, n_terms;
     VQG_DEV void bind(unsigned char *p) {
         t_znt = reinterpret_cast<uint64_t *>(p);
         t_w = reinterpret_cast<amp_t<T> *>(t_znt + kMaxHamTerms);
         t_weff = t_w + kMaxHamTerms;
         t_zl = reinterpret_cast<uint32_t *>(t_weff + kMaxHamTerms);
-        g_xl = t_zl + kMaxHamTerms;
-        g_t0 = g_xl + kMaxHamGroups;
+        t_cls = t_zl + kMaxHamTerms;
+        g_xs = t_cls + kMaxHamTerms;
+        g_t0 = g_xs + kMaxHamGroups;
         g_nt = g_t0 + kMaxHamGroups;
     }
+    template <int D, int SH, int E0>
     VQG_DEV void load(const HPass &P, const HGroup *__restrict__ groups, const HTerm *__restrict__ terms,
                       int tid, int nt) {
         ng = P.n_group;
@@ -755,7 +762,7 @@ struct HamTab {
         n_terms = ng ? groups[P.group0 + ng - 1].term0 + groups[P.group0 + ng - 1].n_term - term_base : 0;
         for (int g = tid; g < ng; g += nt) {
             const HGroup G = groups[P.group0 + g];
-            g_xl[g] = G.xl;
+            g_xs[g] = swz<AB>(G.xl);  // swz is linear: swz(t ^ x) = swz(t) ^ swz(x)
             g_t0[g] = (uint32_t)(G.term0 - term_base);
             g_nt[g] = (uint32_t)G.n_term;
         }
@@ -763,23 +770,50 @@ struct HamTab {
             const HTerm tm = terms[term_base + k];
             t_znt[k] = tm.znt;
             t_zl[k] = tm.zl;
+            // class bit d = bit of z_l at the d-th varying position of a batch
+            uint32_t cls = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int pos = (E0 && d == 0) ? 0 : SH + d - E0;
+                cls |= ((tm.zl >> pos) & 1u) << d;
+            }
+            t_cls[k] = cls;
             if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
             else t_w[k] = mk<T>(tm.wr, tm.wi);
         }
     }
 };
 
-// One tile of a Hamiltonian pass; returns this thread's FP32/FP64 partial of Re<psi|dlam>.
+// Batch geometry of the Hamiltonian pass: each thread owns CPT 16-byte chunks per tile
+// (chunk c = tid + 256 m) and treats BCH of them (BA amplitudes) at a time.  Inside a
+// batch the tile-local indices are t = t0 ^ delta with delta spanning D bits: bit 0 (the
+// second amplitude of a complex64 chunk, E0 = 1) and the low bits of m above position
+// SH.  Hence parity(t & z_l) = parity(t0 & z_l) ^ parity(d & cls(z_l)), d = the batch
+// index, and a group's f over the batch is an 8-point Walsh-Hadamard transform of its
+// terms' signed weights accumulated per class.
+template <typename T, int K>
+struct HamGeo {
+    using IO = TileIO<T, K>;
+    static constexpr int NT = 256;
+    static constexpr int CPT = IO::CHUNKS / NT;
+    static constexpr int BCH = CPT < 8 / IO::CA ? CPT : 8 / IO::CA;
+    static constexpr int BA = BCH * IO::CA;
+    static constexpr int D = BA == 8 ? 3 : (BA == 4 ? 2 : (BA == 2 ? 1 : 0));
+    static constexpr int E0 = IO::CA == 2 ? 1 : 0;
+    static constexpr int LOG_NT_ROWS = 5;  // log2(NT / CPR), CPR = 8 chunks per row
+    static constexpr int SH = FT<T>::L + LOG_NT_ROWS;
+};
+
+// One tile of a Hamiltonian pass; returns this thread's partial of Re<psi|dlam>.
 template <typename T, int K, bool L2ONLY>
-VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T> &tb, uint64_t base, bool first,
+VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, uint64_t base, bool first,
                    const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam, int tid) {
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
+    using G = HamGeo<T, K>;
     constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
-    constexpr int CPT = IO::CHUNKS / NT;                      // chunks per thread per tile
-    constexpr int BCH = CPT < 8 / IO::CA ? CPT : 8 / IO::CA;  // chunks per batch
-    constexpr int BA = BCH * IO::CA;                          // amplitudes per batch
-    static_assert(CPT % BCH == 0, "batching");
+    constexpr int CPT = G::CPT, BCH = G::BCH, BA = G::BA;
+    static_assert(CPT % BCH == 0 && (1 << G::D) == BA, "batching");
     IO::template load<L2ONLY>(tile, psi, base, row_off, tid, NT);
     for (int k = tid; k < tb.n_terms; k += NT) {
         const A w = tb.t_w[k];
@@ -789,14 +823,15 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T> &tb, uint6
     T run = 0;
 #pragma unroll 1
     for (int b0 = 0; b0 < CPT; b0 += BCH) {
-        uint32_t t[BA];
+        uint32_t t0, sw[BA];
         uint64_t gch[BCH];
         A mine[BA], out[BA];
 #pragma unroll
         for (int i = 0; i < BCH; ++i) {
             const int c = tid + NT * (b0 + i);
             const int row = c / IO::CPR, col = c % IO::CPR;
-            const uint32_t t0 = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
+            const uint32_t tc = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
+            if (i == 0) t0 = tc;
             gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
             union {
                 float4 f;
@@ -808,33 +843,51 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T> &tb, uint6
             }
 #pragma unroll
             for (int e = 0; e < IO::CA; ++e) {
-                t[i * IO::CA + e] = t0 + e;
-                mine[i * IO::CA + e] = tile[swz<AB>(t0 + e)];
+                sw[i * IO::CA + e] = swz<AB>(tc + e);
+                mine[i * IO::CA + e] = tile[sw[i * IO::CA + e]];
                 out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : u.a[e];
             }
         }
         for (int g = 0; g < tb.ng; ++g) {
-            const uint32_t xl = tb.g_xl[g];
-            const int j0 = tb.g_t0[g], j1 = j0 + tb.g_nt[g];
-            A f[BA], src[BA];
+            const uint32_t xs = tb.g_xs[g];
+            const int j0 = tb.g_t0[g], nt_g = tb.g_nt[g];
+            A f[BA];
+            if (nt_g == 1) {  // one term: f = +-w with the sign pattern of its class
+                const uint32_t zl = tb.t_zl[j0], cls = tb.t_cls[j0];
+                const A w = tb.t_weff[j0];
+                uint32_t m = (__popc(t0 & zl) & 1) ? 0xFFu : 0u;
+                if (cls & 1u) m ^= 0xAAu;
+                if (cls & 2u) m ^= 0xCCu;
+                if (cls & 4u) m ^= 0xF0u;
 #pragma unroll
-            for (int k = 0; k < BA; ++k) {
-                src[k] = tile[swz<AB>(t[k] ^ xl)];
-                f[k] = mk<T>((T)0, (T)0);
-            }
-            for (int j = j0; j < j1; ++j) {
-                const uint32_t zl = tb.t_zl[j];
-                const A w = tb.t_weff[j];
+                for (int k = 0; k < BA; ++k) f[k] = ((m >> k) & 1u) ? mk<T>(-w.x, -w.y) : w;
+            } else {  // class accumulators, then the Walsh-Hadamard transform over the batch
+                A U[BA];
 #pragma unroll
-                for (int k = 0; k < BA; ++k) {
-                    const bool odd = __popc(t[k] & zl) & 1;
-                    f[k].x += odd ? -w.x : w.x;
-                    f[k].y += odd ? -w.y : w.y;
+                for (int c = 0; c < BA; ++c) U[c] = mk<T>((T)0, (T)0);
+                for (int j = j0; j < j0 + nt_g; ++j) {
+                    const A w = tb.t_weff[j];
+                    const A u = (__popc(t0 & tb.t_zl[j]) & 1) ? mk<T>(-w.x, -w.y) : w;
+                    const uint32_t cls = tb.t_cls[j];
+#pragma unroll
+                    for (int c = 0; c < BA; ++c)
+                        if (cls == (uint32_t)c) U[c] = cadd<T>(U[c], u);
                 }
+#pragma unroll
+                for (int h = 1; h < BA; h <<= 1)
+#pragma unroll
+                    for (int c = 0; c < BA; ++c)
+                        if (!(c & h)) {
+                            const A x = U[c], y = U[c | h];
+                            U[c] = cadd<T>(x, y);
+                            U[c | h] = mk<T>(x.x - y.x, x.y - y.y);
+                        }
+#pragma unroll
+                for (int k = 0; k < BA; ++k) f[k] = U[k];
             }
 #pragma unroll
             for (int k = 0; k < BA; ++k) {
-                const A d = cmul<T>(f[k], src[k]);
+                const A d = cmul<T>(f[k], tile[sw[k] ^ xs]);
                 out[k] = cadd<T>(out[k], d);
                 run += mine[k].x * d.x + mine[k].y * d.y;
             }
@@ -865,13 +918,14 @@ __global__ void __launch_bounds__(256)
     extern __shared__ __align__(16) unsigned char smem[];
     A *tile = reinterpret_cast<A *>(smem);
     uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
-    HamTab<T> tb;
+    HamTab<T, K> tb;
     tb.bind(smem + C::o_tab);
     __shared__ double wsum[NT / 32];
     const HPass &P = hp[pi];
     const int tid = threadIdx.x;
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
-    tb.load(P, groups, terms, tid, NT);
+    using G = HamGeo<T, K>;
+    tb.template load<G::D, G::SH, G::E0>(P, groups, terms, tid, NT);
     double eacc = 0.0;
     __syncthreads();
     for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
