@@ -25,6 +25,9 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from paper_2009_02823_gb300.replicas import (circuit_cost, max_over_ranks, partition,  # noqa: E402
+                                             replica_theta)
+
 METRIC = "adjoint gradients/s at n=30,P=600"
 UNIT = "gradients/s"
 
@@ -168,7 +171,7 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream()  # every kernel of the step and both timing events go here
     circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream)
     circ.set_hamiltonian(w.terms)
-    theta_h = np.ascontiguousarray(w.theta + 1e-3 * rank)
+    theta_h = replica_theta(w.theta, rank)
     theta_d = torch.tensor(theta_h, dtype=torch.float64, device="cuda")
     e_d = torch.zeros(1, dtype=torch.float64, device="cuda")
     g_d = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
@@ -200,11 +203,7 @@ def run_ours(args, rank, world, dist):
     dev_ms = t0.elapsed_time(t1)
     stats = circ.kernel_stats()
     circ.set_profiling(False)
-    ms_max = dev_ms
-    if dist:
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(dev_ms, dist, "cuda")
     value = world * args.steps / (ms_max / 1e3)
 
     # end to end through the public host call: H2D theta, D2H energy + gradient per step
@@ -216,11 +215,7 @@ def run_ours(args, rank, world, dist):
     t_e0 = time.perf_counter()
     for _ in range(e2e_steps):
         e_val, _g = circ.energy_and_gradient(theta_h, out=grad_h)
-    t_e = time.perf_counter() - t_e0
-    if dist:
-        t = torch.tensor([t_e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e = float(t.item())
+    t_e = max_over_ranks(time.perf_counter() - t_e0, dist, "cuda")
     e2e = {"value": world * e2e_steps / t_e, "unit": UNIT,
            "h2d_bytes_per_step": 8 * w.n_params, "d2h_bytes_per_step": 8 * (w.n_params + 1)}
 
@@ -270,8 +265,8 @@ def run_ours(args, rank, world, dist):
     gpu_launches = int(sum(v[0] for v in stats.values()))
 
     extra = {}
-    if rank == 0 and not args.no_batch:
-        extra["batched"] = batched_rate(args)
+    if not args.no_batch:
+        extra["batched"] = batched_rate(args, rank, world, dist)
     if rank == 0 and not args.no_ps:
         extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
     if rank == 0 and not args.no_cpu:
@@ -293,14 +288,18 @@ def run_ours(args, rank, world, dist):
     return line
 
 
-def batched_rate(args):
+def batched_rate(args, rank=0, world=1, dist=None):
     """512-circuit batch (n 12..20, 4..16 layers, TFIM): circuit gradients per second
-    through one persistent launch replayed from a CUDA graph (device buffers)."""
+    through one persistent launch replayed from a CUDA graph (device buffers).  With
+    several ranks the circuits are partitioned by cost and each rank runs its share;
+    the rate divides all 512 circuits by the slowest rank's time."""
     import torch
 
     from paper_2009_02823_gb300 import workloads as W
     from paper_2009_02823_gb300.batch import Batch
-    ws = W.batched()
+    ws_all = W.batched()
+    mine = partition([circuit_cost(w.n, w.n_gates, len(w.terms)) for w in ws_all], world)[rank]
+    ws = [ws_all[b] for b in mine]
     stream = torch.cuda.Stream()
     b = Batch(ws, stream=stream)
     th = torch.tensor(np.concatenate([w.theta for w in ws]), dtype=torch.float64, device="cuda")
@@ -317,11 +316,14 @@ def batched_rate(args):
         b.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
     t1.record(stream)
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / reps
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1) / reps, dist, "cuda")
     info = b.info()
     b.close()
     return {"workload": "512 circuits, n 12..20, 4..16 layers RY/RZ + CNOT ladder, TFIM h~U[0.5,1.5]",
-            "ms_per_batch": round(ms, 3), "circuit_gradients_per_s": round(len(ws) / (ms / 1e3), 1),
+            "ms_per_batch": round(ms, 3), "circuit_gradients_per_s": round(len(ws_all) / (ms / 1e3), 1),
+            "circuits_per_rank": len(ws),
             "tasks": info["tasks"], "grid": info["grid"], "launches_per_batch": 2}
 
 

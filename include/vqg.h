@@ -79,7 +79,8 @@ typedef struct vqg_options {
     int32_t checkpoint_interval; /* forward states stored every this many gates and used to
                                     restart phi in the reverse sweep; 0 = automatic (64 for
                                     complex64, none for complex128), -1 = none              */
-    int32_t tile_qubits;         /* qubits per fused tile; 0 = autotuned                     */
+    int32_t tile_qubits;         /* qubits per fused tile; 0 = built-in table: n - 8 clamped
+                                    to [10, 13] (complex64) or [10, 12] (complex128)        */
     int32_t use_graph;           /* 1: replay the launch sequence from a CUDA graph          */
     int32_t max_checkpoint_mib;  /* cap on checkpoint memory; 0 = fit in free memory         */
     int32_t fwd_reg_qubits;      /* qubits held in registers per forward stage; 0 = default  */
@@ -151,7 +152,9 @@ int vqg_kernel_stats(vqg_circuit *c, int max_entries, int *name_id, int *launche
 const char *vqg_kernel_family_name(int name_id);
 
 /* Per-call details of the schedule: number of forward passes, reverse passes,
- * Hamiltonian passes, kernel launches per energy_and_gradient, checkpoints. */
+ * Hamiltonian passes, kernel launches per energy_and_gradient, checkpoints, and the
+ * fused schedule's tile qubits and register qubits (0 when unfused).  The stage, op and
+ * diagonal-block counts are filled by vqg_plan_dry_run only. */
 typedef struct vqg_plan_info {
     int32_t forward_passes;
     int32_t hamiltonian_passes;
@@ -160,18 +163,50 @@ typedef struct vqg_plan_info {
     int32_t checkpoints;
     int32_t tile_qubits;
     int32_t hamiltonian_groups;
-    int32_t reserved[9];
+    int32_t fwd_reg_qubits;
+    int32_t rev_reg_qubits;
+    int32_t forward_stages;
+    int32_t reverse_stages;
+    int32_t stage_ops;
+    int32_t diag_blocks;
+    int32_t reserved[3];
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 
 /* Plan a circuit and Hamiltonian on the host only (no GPU is touched): the same tile
  * passes, register stages and Hamiltonian passes a vqg_circuit with these options
- * would run, checked index by index.  info->reserved[0] / [1] receive the forward /
- * reverse register-stage counts.  Returns VQG_ERR_INVALID for malformed input and
+ * would run, checked index by index, with the stage, op and diagonal-block counts
+ * filled in.  Returns VQG_ERR_INVALID for malformed input and
  * VQG_ERR_UNSUPPORTED if the schedule fails its checks. */
 int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype,
                      const vqg_options *opt, int n_terms, const uint64_t *x_mask,
                      const uint64_t *z_mask, const double *coef, vqg_plan_info *info);
+
+/* Schedule autotuner (no counterpart in the paper, which applies one gate at a time;
+ * it tunes the tile fusion of the sweeps).  Times whole energy-and-gradient
+ * evaluations of THIS circuit and Hamiltonian under candidate schedules -- tile qubits
+ * K, forward and reverse register-stage widths -- and keeps the fastest.  Candidates:
+ * the compiled (K, Rf, Rr) combinations with K in [Kmax - 2, Kmax] and K <= n; each K
+ * is run with two register choices, and per K the best forward and best reverse stage
+ * widths (timed per kernel family) are combined.  Results are kept in a process-wide
+ * table keyed by the circuit's structure (n, dtype, gates, Hamiltonian masks), so a
+ * second circuit of the same structure takes the stored choice without timing.
+ * theta: host, n_params doubles (NULL: all zeros).  out (nullable): the choice.
+ * Needs a Hamiltonian; no-op (candidates = 0, tile_qubits = 0) when the circuit runs
+ * unfused (n < 10 or fusion off) or was created with an explicit tile_qubits.
+ * Blocks until done; the circuit's checkpoints and graphs are rebuilt for the choice.
+ * Options.autotune = 1 runs this automatically on the first energy_and_gradient call. */
+typedef struct vqg_tune_result {
+    int32_t tile_qubits;
+    int32_t fwd_reg_qubits;
+    int32_t rev_reg_qubits;
+    int32_t candidates;   /* schedules timed; 0 when taken from the table or a no-op   */
+    double best_ms;       /* fused forward + Hamiltonian + reverse time of the choice   */
+    double default_ms;    /* the same for the built-in default schedule (0 if untimed)  */
+} vqg_tune_result;
+int vqg_autotune(vqg_circuit *c, const double *theta, vqg_tune_result *out);
+/* Drop every stored autotuner choice of this process. */
+void vqg_tune_table_clear(void);
 
 const char *vqg_last_error(void);
 const char *vqg_status_string(int status);

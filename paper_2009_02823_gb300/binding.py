@@ -50,7 +50,16 @@ class vqg_plan_info(ctypes.Structure):
     _fields_ = [("forward_passes", ctypes.c_int32), ("hamiltonian_passes", ctypes.c_int32),
                 ("reverse_passes", ctypes.c_int32), ("launches_per_gradient", ctypes.c_int32),
                 ("checkpoints", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
-                ("hamiltonian_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("hamiltonian_groups", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
+                ("rev_reg_qubits", ctypes.c_int32), ("forward_stages", ctypes.c_int32),
+                ("reverse_stages", ctypes.c_int32), ("stage_ops", ctypes.c_int32),
+                ("diag_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class vqg_tune_result(ctypes.Structure):
+    _fields_ = [("tile_qubits", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
+                ("rev_reg_qubits", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
 
 def declared_functions() -> list[str]:
@@ -88,6 +97,8 @@ def lib():
             "vqg_kernel_stats": (i, [p, i, p, p, p]),
             "vqg_kernel_family_name": (ctypes.c_char_p, [i]),
             "vqg_plan": (i, [p, p]),
+            "vqg_autotune": (i, [p, p, p]),
+            "vqg_tune_table_clear": (None, []),
             "vqg_last_error": (ctypes.c_char_p, []),
             "vqg_status_string": (ctypes.c_char_p, [i]),
             "vqg_reverse_noalloc": (i, [i, i, p, i, p, i, p, p, p, p]),
@@ -269,7 +280,15 @@ class Circuit:
     def plan(self) -> dict:
         info = vqg_plan_info()
         _check(lib().vqg_plan(self._h, ctypes.byref(info)))
-        return {k: getattr(info, k) for k, _t in vqg_plan_info._fields_ if k != "reserved"}
+        return {k: getattr(info, k) for k, _t in vqg_plan_info._fields_
+                if k not in ("reserved", "forward_stages", "reverse_stages", "stage_ops", "diag_blocks")}
+
+    def autotune(self, theta=None) -> dict:
+        """Time candidate fused schedules on this circuit and keep the fastest."""
+        r = vqg_tune_result()
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        _check(lib().vqg_autotune(self._h, None if th is None else _ptr(th), ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _t in vqg_tune_result._fields_}
 
     def set_profiling(self, enable: bool = True):
         _check(lib().vqg_set_profiling(self._h, int(enable)))
@@ -319,5 +338,4 @@ def plan_dry_run(n: int, gates, n_params: int, terms, dtype: str = "c64", *, fus
     _check(L.vqg_plan_dry_run(n, arr, len(gates), n_params, DTYPE[dtype], ctypes.byref(opt), len(c),
                               _ptr(x), _ptr(z), _ptr(c), ctypes.byref(info)))
     out = {k: getattr(info, k) for k, _t in vqg_plan_info._fields_ if k != "reserved"}
-    out["forward_stages"], out["reverse_stages"] = info.reserved[0], info.reserved[1]
     return out

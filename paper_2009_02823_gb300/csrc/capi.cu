@@ -213,6 +213,7 @@ int Circuit::init(int n_, const vqg_gate *gates_, int G_, int P_, int dtype_, co
     state_bytes = (size_t)amp_bytes << n;
     vqg_default_options(&opt);
     if (opt_) opt = *opt_;
+    tile_explicit = opt.tile_qubits > 0;
     VQG_CUDA(cudaGetDevice(&device));
     VQG_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
     VQG_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
@@ -268,34 +269,49 @@ int Circuit::init(int n_, const vqg_gate *gates_, int G_, int P_, int dtype_, co
 }
 
 // Forward states are stored every `interval` gates (per-gate schedule) or at the first
-// pass boundary after every `interval` gates (fused schedule), as many as fit.
+// pass boundary after every `interval` gates (fused schedule), as many as fit.  Buffers
+// already held (from an earlier schedule of the same circuit) are reused; surplus ones
+// are released.
 int Circuit::plan_checkpoints() {
     int interval = opt.checkpoint_interval;
     if (interval == 0) interval = dbl ? -1 : 64;
     ckpt_pos.clear();
-    if (interval < 0 || G < 2) return VQG_OK;
     const bool fused = opt.fusion && plan_ok;
     std::vector<int> want;
-    if (fused) want = fused_checkpoint_passes(interval);
-    else
-        for (int c = interval; c < G; c += interval) want.push_back(c);
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    const size_t headroom = (size_t)4 << 30;
-    size_t budget = free_b > headroom ? free_b - headroom : 0;
-    if (opt.max_checkpoint_mib > 0) budget = std::min(budget, (size_t)opt.max_checkpoint_mib << 20);
-    size_t fit = budget / state_bytes;
-    if (fit < want.size()) {  // keep evenly spread positions
+    if (interval >= 0 && G >= 2) {
+        if (fused) want = fused_checkpoint_passes(interval);
+        else
+            for (int c = interval; c < G; c += interval) want.push_back(c);
+    }
+    if (want.size() > ckpt_buf.size()) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const size_t headroom = (size_t)4 << 30;
+        size_t budget = free_b > headroom ? free_b - headroom : 0;
+        if (opt.max_checkpoint_mib > 0) {
+            const size_t cap = (size_t)opt.max_checkpoint_mib << 20, held = ckpt_buf.size() * state_bytes;
+            budget = std::min(budget, cap > held ? cap - held : 0);
+        }
+        const size_t fit = ckpt_buf.size() + budget / state_bytes;
+        while (ckpt_buf.size() < std::min(fit, want.size())) {
+            void *buf = nullptr;
+            if (dalloc(&buf, state_bytes) != VQG_OK) break;  // fewer checkpoints, still correct
+            ckpt_buf.push_back(buf);
+        }
+    }
+    if (want.size() > ckpt_buf.size()) {  // keep evenly spread positions
         std::vector<int> keep;
+        const size_t fit = ckpt_buf.size();
         for (size_t k = 0; k < fit; ++k) keep.push_back(want[(k + 1) * want.size() / (fit + 1)]);
         want.swap(keep);
     }
-    for (int pos : want) {
-        void *buf = nullptr;
-        if (dalloc(&buf, state_bytes) != VQG_OK) break;  // fewer checkpoints, still correct
-        if (fused) set_fused_checkpoint(pos, (int)ckpt_buf.size());
-        else ckpt_pos.push_back(pos);
-        ckpt_buf.push_back(buf);
+    while (ckpt_buf.size() > want.size()) {
+        dfree(ckpt_buf.back());
+        ckpt_buf.pop_back();
+    }
+    for (size_t k = 0; k < want.size(); ++k) {
+        if (fused) set_fused_checkpoint(want[k], (int)k);
+        else ckpt_pos.push_back(want[k]);
     }
     cudaGetLastError();
     g_last_error.clear();
@@ -354,6 +370,7 @@ int Circuit::set_groups(const std::vector<HamGroup> &groups, const std::vector<P
     host_terms = flat;
     n_eslots = std::max(n_eslots, (int)ham.size());
     has_ham = true;
+    tuned = false;
     if ((st = ensure_partials())) return st;
     invalidate_graphs();
     return build_plan();
@@ -449,6 +466,10 @@ int Circuit::issue_gradient(const double *theta_dev, double *energy_dev, double 
 // between launches); the legacy default stream cannot be captured and also runs eagerly.
 int Circuit::run_gradient(const double *theta_dev, double *energy_dev, double *grad_dev) {
     if (!has_ham) return set_error(VQG_ERR_STATE, "no Hamiltonian set");
+    if (opt.autotune && !tuned) {  // first evaluation picks the schedule (blocks once)
+        int st = autotune(theta_dev, nullptr);
+        if (st) return st;
+    }
     const bool graphable = opt.use_graph && !profiling && stream != cudaStreamLegacy && stream != nullptr;
     if (!graphable) return issue_gradient(theta_dev, energy_dev, grad_dev);
     const void *key[3] = {theta_dev, energy_dev, grad_dev};

@@ -295,7 +295,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                         if (g.kind == VQG_RZ) {
                             const int k = regbit(g.q0);
                             if (k >= 0) x.type = DI_RZ_REG, x.k0 = (int16_t)k;
-                            else x.type = DI_RZ_THR, x.g0 = 1ull << g.q0;
+                            else x.type = DI_RZ_THR, x.g0 = 1ull << g.q0, st.has_phase = 1;
                             if (reverse) {
                                 x.lslot = n_lslots++;
                                 pl.slot_map.push_back(slot_base[i]);
@@ -307,7 +307,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                             if (ka >= 0 && kb >= 0) x.type = DI_CZ_RR, x.k0 = (int16_t)ka, x.k1 = (int16_t)kb;
                             else if (ka >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)ka, x.g0 = 1ull << g.q1;
                             else if (kb >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)kb, x.g0 = 1ull << g.q0;
-                            else x.type = DI_CZ_TT, x.g0 = 1ull << g.q0, x.g1 = 1ull << g.q1;
+                            else x.type = DI_CZ_TT, x.g0 = 1ull << g.q0, x.g1 = 1ull << g.q1, st.has_phase = 1;
                         }
                         pl.items.push_back(x);
                     }
@@ -317,7 +317,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             pl.ops.push_back(op);
         }
         st.n_op = (int)pl.ops.size() - st.op0;
-        st.n_rows = rows;
+        st.n_rows = (int16_t)rows;
         pl.stages.push_back(st);
         ++n_stage;
         uns.swap(left);
@@ -472,6 +472,13 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
     return "";
 }
 
+// Built-in schedule table: the largest tile that still leaves 2^8 tiles for the SMs
+// (n - 8), within the compiled range [10, 13] (complex64) / [10, 12] (complex128).
+int default_tile_qubits(int n, bool dbl) {
+    const int Kmax = dbl ? 12 : 13;
+    return std::min(Kmax, std::max(10, n - 8));
+}
+
 static int occupancy_grid(int num_sms, int per_sm, uint64_t n_tiles) {
     const uint64_t g = (uint64_t)num_sms * (uint64_t)std::max(per_sm, 1);
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(g, n_tiles));
@@ -484,8 +491,7 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
                         int n_gslots, bool dbl, const vqg_options &opt, std::string &err) {
     err.clear();
     const int G = (int)gates.size();
-    const int Kmax = dbl ? 12 : 13;
-    int K = std::min(n, Kmax);
+    int K = std::min(n, default_tile_qubits(n, dbl));
     if (opt.tile_qubits > 0) K = std::min(opt.tile_qubits, n);
     const int Rf = opt.fwd_reg_qubits > 0 ? opt.fwd_reg_qubits : (dbl ? 4 : 5);
     const int Rr = opt.rev_reg_qubits > 0 ? opt.rev_reg_qubits : (dbl ? 3 : 4);
@@ -741,6 +747,17 @@ void Circuit::free_plan() {
     plan = nullptr;
 }
 
+// Release the plan with its device tables (the circuit's other buffers stay).
+void Circuit::drop_plan() {
+    if (!plan) return;
+    for (void *p : {(void *)plan->d_passes, (void *)plan->d_stages, (void *)plan->d_ops, (void *)plan->d_diags,
+                    (void *)plan->d_items, (void *)plan->d_slot_map, (void *)plan->d_hp, (void *)plan->d_hg,
+                    (void *)plan->d_ht, (void *)plan->d_mats_f})
+        dfree(p);
+    free_plan();
+    plan_ok = ham_plan_ok = false;
+}
+
 // Checkpoints of the fused schedule sit at pass boundaries: the output of pass j is
 // stored when at least `interval` gates have passed since the previous one (never the
 // last pass: its output is psi itself).
@@ -822,6 +839,8 @@ void Circuit::fill_plan_info(vqg_plan_info *info) const {
     }
     info->checkpoints = nck;
     info->tile_qubits = fused ? plan->K : 0;
+    info->fwd_reg_qubits = fused ? plan->Rf : 0;
+    info->rev_reg_qubits = fused ? plan->Rr : 0;
     info->hamiltonian_groups = (int)ham.size();
     info->launches_per_gradient = 1 + info->forward_passes + info->hamiltonian_passes + info->reverse_passes + 2 +
                                   (fused ? 0 : 1 + nck);
@@ -908,12 +927,14 @@ extern "C" int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates
     info->hamiltonian_passes = ham_fused ? (int)pl->hp.size() : (int)ham.size();
     info->hamiltonian_groups = (int)ham.size();
     info->tile_qubits = pl->K;
+    info->fwd_reg_qubits = pl->Rf;
+    info->rev_reg_qubits = pl->Rr;
     int fs = 0, rs = 0, fd = 0, rd = 0;
     for (const FPass &p : pl->passes) fs += p.n_stage, rs += p.n_rstage, fd += p.n_diag, rd += p.n_rdiag;
-    info->reserved[0] = fs;  // forward register stages
-    info->reserved[1] = rs;  // reverse register stages
-    info->reserved[2] = (int)pl->ops.size();  // register-stage ops, both directions
-    info->reserved[3] = fd + rd;              // diagonal blocks, both directions
+    info->forward_stages = fs;
+    info->reverse_stages = rs;
+    info->stage_ops = (int)pl->ops.size();  // register-stage ops, both directions
+    info->diag_blocks = fd + rd;            // diagonal blocks, both directions
     info->launches_per_gradient = 1 + 2 * info->forward_passes + info->hamiltonian_passes + 2;
     delete pl;
     return VQG_OK;

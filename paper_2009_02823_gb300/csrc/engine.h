@@ -109,6 +109,10 @@ struct Circuit {
     int build_plan();
     int build_ham_plan();
     void free_plan();
+    void drop_plan();
+    int autotune(const double *theta_dev, vqg_tune_result *out);
+    bool tuned = false;          // autotune ran (or was found a no-op) for this circuit
+    bool tile_explicit = false;  // the caller fixed tile_qubits: nothing to tune
     std::vector<int> fused_checkpoint_passes(int interval) const;
     void set_fused_checkpoint(int pass, int k);
     float *mats_f() const;

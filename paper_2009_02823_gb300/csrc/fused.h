@@ -67,7 +67,8 @@ struct FStage {
     int8_t thr_q[kMaxThreadBits];        // global qubit of thread bit b
     int32_t op0, n_op;
     int16_t row_slot[kMaxStageRows];     // reverse: local reduction slot of each stash row
-    int32_t n_rows;                      // reverse: stash rows used by this stage
+    int16_t n_rows;                      // reverse: stash rows used by this stage
+    int16_t has_phase;                   // a diagonal block of the stage has a per-thread phase
 };
 
 struct FOp {          // 16 bytes: one shared-memory vector load
@@ -125,7 +126,7 @@ struct HTerm {
 // touching indices whose varying bits have distinct residues mod 4 (mod 3) hit
 // distinct banks.  Linear over GF(2); keeps rows intact.
 template <int AMP_BYTES>
-__host__ __device__ inline uint32_t swz(uint32_t t) {
+__host__ __device__ constexpr uint32_t swz(uint32_t t) {
     if (AMP_BYTES == 8) return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12) ^ (t >> 16)) & 15u);
     return t ^ (((t >> 3) ^ (t >> 6) ^ (t >> 9) ^ (t >> 12) ^ (t >> 15)) & 7u);
 }

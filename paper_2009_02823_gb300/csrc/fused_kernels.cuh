@@ -412,47 +412,70 @@ struct TileIO {
     static constexpr int CPR = (1 << L) / CA;   // chunks per 128-byte row
     static constexpr int CHUNKS = TILE / CA;
 
+    // Thread tid moves chunks c = tid + NT*i.  Their rows are tid/CPR + (NT/CPR)*i and
+    // their column tid%CPR, so the shared-memory slot is swz(t0) ^ swz(i << SHI) (swz is
+    // linear) and the row offset row_off[row0] | row_off[(NT/CPR)*i] (the deposit of
+    // disjoint bits is linear too): one XOR per chunk instead of a full recomputation.
+    template <int NT>
+    struct Geo {
+        static_assert(NT % CPR == 0 && CHUNKS % NT == 0, "chunk geometry");
+        static constexpr int CPT = CHUNKS / NT, RSTEP = NT / CPR;
+        static constexpr int SHI = L + (RSTEP == 1 ? 0 : RSTEP == 2 ? 1 : RSTEP == 4 ? 2 : RSTEP == 8 ? 3 :
+                                        RSTEP == 16 ? 4 : RSTEP == 32 ? 5 : RSTEP == 64 ? 6 : 7);
+    };
+
     // L2ONLY: bypass L1 (needed when another block of the same launch wrote the data).
-    template <bool L2ONLY = false>
+    template <int NT, bool L2ONLY = false>
     static VQG_DEV void load(amp_t<T> *tile, const amp_t<T> *__restrict__ src, uint64_t base,
-                             const uint64_t *row_off, int tid, int nt) {
-        for (int c = tid; c < CHUNKS; c += nt) {
-            const int row = c / CPR, col = c % CPR;
-            const uint32_t t = (uint32_t)(row << L) | (uint32_t)(col * CA);
-            const float4 *g = reinterpret_cast<const float4 *>(src + (base | row_off[row]) + col * CA);
-            put_chunk(tile, t, L2ONLY ? __ldcg(g) : __ldcs(g));
+                             const uint64_t *row_off, int tid) {
+        using G = Geo<NT>;
+        const int row0 = tid / CPR, col = tid % CPR;
+        const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
+        const amp_t<T> *g0 = src + ((base | row_off[row0]) + col * CA);
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i) {
+            const float4 *g = reinterpret_cast<const float4 *>(g0 + row_off[G::RSTEP * i]);
+            const float4 v = L2ONLY ? __ldcg(g) : __ldcs(g);
+            put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), v);
         }
     }
-    static VQG_DEV void zero(amp_t<T> *tile, uint64_t base, int tid, int nt) {
-        for (int c = tid; c < CHUNKS; c += nt) put_chunk(tile, (uint32_t)(c * CA), make_float4(0.f, 0.f, 0.f, 0.f));
+    template <int NT>
+    static VQG_DEV void zero(amp_t<T> *tile, uint64_t base, int tid) {
+        using G = Geo<NT>;
+        const int row0 = tid / CPR, col = tid % CPR;
+        const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i) put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), make_float4(0.f, 0.f, 0.f, 0.f));
         if (base == 0 && tid == 0) tile[swz<AB>(0)] = mk<T>((T)1, (T)0);
     }
-    // A 16-byte chunk (two complex64 or one complex128 amplitudes starting at tile-local
-    // index t) to / from shared memory.  The complex64 swizzle may separate the two
-    // amplitudes (it folds higher bits into bit 0), so each goes to its own 8-byte slot.
-    static VQG_DEV void put_chunk(amp_t<T> *tile, uint32_t t, float4 v) {
+    // A 16-byte chunk (two complex64 or one complex128 amplitudes) at swizzled slot s of its
+    // first amplitude.  For complex64 the second amplitude sits at s ^ swz(1) = s ^ 1.
+    static VQG_DEV void put_chunk(amp_t<T> *tile, uint32_t s, float4 v) {
         if constexpr (AB == 8) {
-            tile[swz<AB>(t)] = mk<T>(v.x, v.y);
-            tile[swz<AB>(t + 1)] = mk<T>(v.z, v.w);
+            tile[s] = mk<T>(v.x, v.y);
+            tile[s ^ 1u] = mk<T>(v.z, v.w);
         } else {
-            *reinterpret_cast<float4 *>(tile + swz<AB>(t)) = v;
+            *reinterpret_cast<float4 *>(tile + s) = v;
         }
     }
-    static VQG_DEV float4 get_chunk(const amp_t<T> *tile, uint32_t t) {
+    static VQG_DEV float4 get_chunk(const amp_t<T> *tile, uint32_t s) {
         if constexpr (AB == 8) {
-            const amp_t<T> a = tile[swz<AB>(t)], b = tile[swz<AB>(t + 1)];
+            const amp_t<T> a = tile[s], b = tile[s ^ 1u];
             return make_float4(a.x, a.y, b.x, b.y);
         } else {
-            return *reinterpret_cast<const float4 *>(tile + swz<AB>(t));
+            return *reinterpret_cast<const float4 *>(tile + s);
         }
     }
+    template <int NT>
     static VQG_DEV void store(const amp_t<T> *tile, amp_t<T> *__restrict__ dst, uint64_t base,
-                              const uint64_t *row_off, int tid, int nt) {
-        for (int c = tid; c < CHUNKS; c += nt) {
-            const int row = c / CPR, col = c % CPR;
-            const uint32_t t = (uint32_t)(row << L) | (uint32_t)(col * CA);
-            __stcs(reinterpret_cast<float4 *>(dst + (base | row_off[row]) + col * CA), get_chunk(tile, t));
-        }
+                              const uint64_t *row_off, int tid) {
+        using G = Geo<NT>;
+        const int row0 = tid / CPR, col = tid % CPR;
+        const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
+        amp_t<T> *g0 = dst + ((base | row_off[row0]) + col * CA);
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i)
+            __stcs(reinterpret_cast<float4 *>(g0 + row_off[G::RSTEP * i]), get_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI)));
     }
 };
 
@@ -501,8 +524,8 @@ VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> 
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
     constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
-    if (from_zero) IO::zero(tile, base, tid, NT);
-    else IO::template load<L2ONLY>(tile, src, base, row_off, tid, NT);
+    if (from_zero) IO::template zero<NT>(tile, base, tid);
+    else IO::template load<NT, L2ONLY>(tile, src, base, row_off, tid);
     __syncthreads();
     for (int s = 0; s < n_stage; ++s) {
         const FStage &st = pg.st[s];
@@ -519,11 +542,16 @@ VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> 
         const int o0 = st.op0 - pg.op_base;
         for (int o = o0; o < o0 + st.n_op; ++o) apply_fwd_op<R, NA, T>(a, pg, o, gb, phase);
         asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
+        if (st.has_phase) {
 #pragma unroll
-        for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = cmul<T>(phase, a[j]);
+            for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = cmul<T>(phase, a[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = a[j];
+        }
         __syncthreads();
     }
-    IO::store(tile, dst, base, row_off, tid, NT);
+    IO::template store<NT>(tile, dst, base, row_off, tid);
     __syncthreads();
 }
 
@@ -533,9 +561,27 @@ VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> 
 template <typename T, int NT>
 VQG_DEV void reduce_stash(const T *stash, const FStage &st, double *acc, int tid) {
     const int lane = tid & 31, warp = tid >> 5;
+    constexpr int V = 16 / sizeof(T);  // values per 16-byte load
+    if constexpr (NT % (32 * V) != 0) {
+        for (int r = warp; r < st.n_rows; r += NT / 32) {
+            T v = 0;
+            for (int i = lane; i < NT; i += 32) v += stash[r * NT + i];
+            v = warp_tree<T>(v);
+            if (lane == 0) acc[st.row_slot[r]] += (double)v;
+        }
+        return;
+    }
     for (int r = warp; r < st.n_rows; r += NT / 32) {
         T v = 0;
-        for (int i = lane; i < NT; i += 32) v += stash[r * NT + i];
+#pragma unroll
+        for (int i = lane * V; i < NT; i += 32 * V) {
+            const float4 q = *reinterpret_cast<const float4 *>(stash + r * NT + i);
+            if constexpr (sizeof(T) == 4) v += (q.x + q.y) + (q.z + q.w);
+            else {
+                const double2 d = *reinterpret_cast<const double2 *>(&q);
+                v += d.x + d.y;
+            }
+        }
         v = warp_tree<T>(v);
         if (lane == 0) acc[st.row_slot[r]] += (double)v;
     }
@@ -554,8 +600,8 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
     constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
-    IO::template load<L2ONLY>(tphi, phi_src, base, row_off, tid, NT);
-    IO::template load<L2ONLY>(tlam, lam, base, row_off, tid, NT);
+    IO::template load<NT, L2ONLY>(tphi, phi_src, base, row_off, tid);
+    IO::template load<NT, L2ONLY>(tlam, lam, base, row_off, tid);
     __syncthreads();
     for (int s = 0; s < n_stage; ++s) {
         const FStage &st = pg.st[s];
@@ -617,11 +663,20 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             if (red1) stash[op.row * NT + tid] = v1;
         }
         asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
+        if (st.has_phase) {
 #pragma unroll
-        for (int j = 0; j < NA; ++j) {
-            const uint32_t ad = reg_addr<R, NA>(sb, w, j);
-            tphi[ad] = cmul<T>(phase, a[j]);
-            tlam[ad] = cmul<T>(phase, l[j]);
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                tphi[ad] = cmul<T>(phase, a[j]);
+                tlam[ad] = cmul<T>(phase, l[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                tphi[ad] = a[j];
+                tlam[ad] = l[j];
+            }
         }
         __syncthreads();
         if (st.n_rows) {
@@ -629,8 +684,8 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             __syncthreads();
         }
     }
-    IO::store(tphi, phi_dst, base, row_off, tid, NT);
-    IO::store(tlam, lam, base, row_off, tid, NT);
+    IO::template store<NT>(tphi, phi_dst, base, row_off, tid);
+    IO::template store<NT>(tlam, lam, base, row_off, tid);
     __syncthreads();
 }
 
@@ -679,6 +734,7 @@ struct RevCfg {
     static constexpr size_t o_map = o_stash + sizeof(T) * (size_t)stash_rows<T>() * NT;
     static constexpr size_t smem() { return o_map + sizeof(int) * kMaxPassSlots; }
     static_assert(o_map + sizeof(int) * kMaxPassSlots <= 227 * 1024, "reverse pass exceeds shared memory");
+    static_assert(o_stash % 16 == 0, "stash rows are read with 16-byte loads");
 };
 
 template <typename T, int K, int R>
@@ -814,7 +870,7 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
     constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
     constexpr int CPT = G::CPT, BCH = G::BCH, BA = G::BA;
     static_assert(CPT % BCH == 0 && (1 << G::D) == BA, "batching");
-    IO::template load<L2ONLY>(tile, psi, base, row_off, tid, NT);
+    IO::template load<NT, L2ONLY>(tile, psi, base, row_off, tid);
     for (int k = tid; k < tb.n_terms; k += NT) {
         const A w = tb.t_w[k];
         tb.t_weff[k] = (__popcll(base & tb.t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;

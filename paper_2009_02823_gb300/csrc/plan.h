@@ -45,5 +45,6 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
 bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham, const std::vector<PauliTerm> &host_terms);
 std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl);
 bool fused_supported(bool dbl, int K, int Rf, int Rr);
+int default_tile_qubits(int n, bool dbl);
 
 }  // namespace vqg

@@ -247,3 +247,34 @@ def test_cuda_graph_replay(dtype):
             e_ref, g_ref = _oracle(w.n, w.gates, th, w.n_params, w.terms)
             e, g = c.energy_and_gradient(th)
             assert_parity(dtype, e, g, e_ref, g_ref, f"graph call {k}")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_autotune_choice_and_parity(dtype):
+    """The autotuner times candidate schedules, keeps a compiled one, stores it in the
+    process-wide table (a second circuit of the same structure reuses it untimed), and
+    the tuned circuit still matches the oracle.  options.autotune runs it on the first
+    evaluation."""
+    from paper_2009_02823_gb300 import binding as B
+    B.lib().vqg_tune_table_clear()
+    w = W.config(2, n=16, layers=3)
+    e_ref, g_ref = _oracle(w.n, w.gates, w.theta, w.n_params, w.terms)
+    kmax = 13 if dtype == "c64" else 12
+    with _circ(w.n, w.gates, w.n_params, dtype, w.terms) as c:
+        r = c.autotune(w.theta)
+        assert r["candidates"] >= 3 and kmax - 2 <= r["tile_qubits"] <= kmax
+        assert 0 < r["best_ms"] and r["default_ms"] > 0
+        info = c.plan()
+        assert (info["tile_qubits"], info["fwd_reg_qubits"], info["rev_reg_qubits"]) == \
+            (r["tile_qubits"], r["fwd_reg_qubits"], r["rev_reg_qubits"])
+        e, g = c.energy_and_gradient(w.theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, "tuned")
+    with _circ(w.n, w.gates, w.n_params, dtype, w.terms, autotune=True) as c:
+        e, g = c.energy_and_gradient(w.theta)  # tunes first (from the table)
+        assert_parity(dtype, e, g, e_ref, g_ref, "autotune option")
+        r2 = c.autotune(w.theta)
+        assert r2["candidates"] == 0 and r2["tile_qubits"] == r["tile_qubits"]
+        assert c.plan()["tile_qubits"] == r["tile_qubits"]
+    with _circ(w.n, w.gates, w.n_params, dtype, w.terms, tile_qubits=11) as c:
+        r3 = c.autotune(w.theta)  # explicit tile: nothing to tune
+        assert r3["candidates"] == 0 and c.plan()["tile_qubits"] == 11

@@ -14,7 +14,8 @@ from paper_2009_02823_gb300 import workloads as W
 def test_workloads_plan(cfg, dtype):
     w = W.config(cfg)
     info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype)
-    assert info["tile_qubits"] == min(w.n, 13 if dtype == "c64" else 12)
+    assert info["tile_qubits"] == min(13 if dtype == "c64" else 12, max(10, w.n - 8))
+    assert (info["fwd_reg_qubits"], info["rev_reg_qubits"]) == ((5, 4) if dtype == "c64" else (4, 3))
     assert 1 <= info["forward_passes"] <= w.n_gates
     assert info["hamiltonian_passes"] >= 1
     assert info["forward_stages"] >= info["forward_passes"]
@@ -80,3 +81,16 @@ def test_register_variants(dtype, K, Rf, Rr, ok):
         with pytest.raises(B.VqgError):
             B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype, tile_qubits=K,
                            fwd_reg_qubits=Rf, rev_reg_qubits=Rr)
+
+
+@pytest.mark.parametrize("dtype,kmax", [("c64", 13), ("c128", 12)])
+def test_default_tile_table(dtype, kmax):
+    """Built-in table: tiles of n - 8 qubits (>= 2^8 tiles for the SMs), clamped to the
+    compiled range; no fused schedule below 10 qubits."""
+    rng = np.random.default_rng(7)
+    for n in range(8, 31):
+        gates, P = W.hea_ry_rz(n, 1)
+        terms = W.random_terms(rng, n, 4)
+        info = B.plan_dry_run(n, gates, P, terms, dtype)
+        want = 0 if n < 10 else min(kmax, max(10, n - 8))
+        assert info["tile_qubits"] == want, n
