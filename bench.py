@@ -302,6 +302,7 @@ def batched_rate(args, rank=0, world=1, dist=None):
     ws = [ws_all[b] for b in mine]
     stream = torch.cuda.Stream()
     b = Batch(ws, stream=stream)
+    tune = b.autotune([w.theta for w in ws])  # picks the tile geometry (outside the timed region)
     th = torch.tensor(np.concatenate([w.theta for w in ws]), dtype=torch.float64, device="cuda")
     e = torch.zeros(len(ws), dtype=torch.float64, device="cuda")
     g = torch.zeros(th.numel(), dtype=torch.float64, device="cuda")
@@ -324,6 +325,9 @@ def batched_rate(args, rank=0, world=1, dist=None):
     return {"workload": "512 circuits, n 12..20, 4..16 layers RY/RZ + CNOT ladder, TFIM h~U[0.5,1.5]",
             "ms_per_batch": round(ms, 3), "circuit_gradients_per_s": round(len(ws_all) / (ms / 1e3), 1),
             "circuits_per_rank": len(ws),
+            "autotune": {"tile_qubits": tune["tile_qubits"], "reg_qubits": tune["fwd_reg_qubits"],
+                         "candidates": tune["candidates"], "default_ms": round(tune["default_ms"], 3),
+                         "best_ms": round(tune["best_ms"], 3)},
             "tasks": info["tasks"], "grid": info["grid"], "launches_per_batch": 2}
 
 

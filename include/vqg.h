@@ -186,7 +186,8 @@ int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_par
  * it tunes the tile fusion of the sweeps).  Times whole energy-and-gradient
  * evaluations of THIS circuit and Hamiltonian under candidate schedules -- tile qubits
  * K, forward and reverse register-stage widths -- and keeps the fastest.  Candidates:
- * the compiled (K, Rf, Rr) combinations with K in [Kmax - 2, Kmax] and K <= n; each K
+ * the compiled (K, Rf, Rr) combinations with K from Kmax = min(n, 13 complex64 / 12
+ * complex128) down to Kmax - 2 or the built-in default, whichever is lower; each K
  * is run with two register choices, and per K the best forward and best reverse stage
  * widths (timed per kernel family) are combined.  Results are kept in a process-wide
  * table keyed by the circuit's structure (n, dtype, gates, Hamiltonian masks), so a
@@ -232,7 +233,15 @@ const char *vqg_status_string(int status);
  * vqg_batch_set_wait_limit: spin limit of the dependency waits; stall_circuit >= 0 makes
  *   that circuit's later phases wait for a count that is never reached (a test hook for
  *   the timeout path); -1 disables it.
- * vqg_batch_info: task count, persistent grid size, total parameters. */
+ * vqg_batch_info: task count, persistent grid size, total parameters.
+ * vqg_batch_autotune: evaluates the whole batch once per compiled tile geometry (tile
+ *   qubits 12 with 4 register qubits, the default, and 11 with 3), keeps the fastest and
+ *   reports it in `out` (nullable; fwd_reg_qubits = rev_reg_qubits = the register
+ *   qubits).  theta: host, concatenated like vqg_batch_energy_and_gradient (NULL: zeros).
+ *   Every circuit needs its Hamiltonian first.  Blocks; rebuilds the batch's device
+ *   buffers (device pointers of earlier outputs stay valid, a captured graph is redone).
+ * vqg_batch_set_tile_qubits: select a compiled geometry by its tile qubits (12 or 11;
+ *   VQG_ERR_UNSUPPORTED otherwise); the batch is rebuilt at its next evaluation. */
 typedef struct vqg_batch vqg_batch;
 int vqg_batch_create(int n_circuits, const int *n_qubits, const vqg_gate *gates,
                      const int *gate_offsets, const int *n_params, int dtype, vqg_batch **out);
@@ -245,6 +254,8 @@ int vqg_batch_energy_and_gradient(vqg_batch *b, const double *theta, double *ene
 int vqg_batch_energy_and_gradient_device(vqg_batch *b, const double *theta_dev,
                                          double *energies_dev, double *grads_dev);
 int vqg_batch_info(vqg_batch *b, int *n_tasks, int *grid, int *total_params);
+int vqg_batch_autotune(vqg_batch *b, const double *theta, vqg_tune_result *out);
+int vqg_batch_set_tile_qubits(vqg_batch *b, int tile_qubits);
 int vqg_batch_destroy(vqg_batch *b);
 
 /* ---------------------------------------------------------------- allocation-free step

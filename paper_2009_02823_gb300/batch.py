@@ -70,3 +70,17 @@ class Batch:
         nt, grid, tp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         B._check(B.lib().vqg_batch_info(self._h, ctypes.byref(nt), ctypes.byref(grid), ctypes.byref(tp)))
         return {"tasks": nt.value, "grid": grid.value, "total_params": tp.value}
+
+    def autotune(self, thetas=None) -> dict:
+        """Time every compiled tile geometry on this batch and keep the fastest."""
+        th = None
+        if thetas is not None:
+            th = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64).ravel() for t in thetas])
+                                      if isinstance(thetas, (list, tuple)) else thetas, dtype=np.float64)
+        r = B.vqg_tune_result()
+        B._check(B.lib().vqg_batch_autotune(self._h, None if th is None else B._ptr(th), ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _t in B.vqg_tune_result._fields_}
+
+    def set_tile_qubits(self, tile_qubits: int):
+        """Select a compiled tile geometry (12: 4 register qubits; 11: 3)."""
+        B._check(B.lib().vqg_batch_set_tile_qubits(self._h, tile_qubits))

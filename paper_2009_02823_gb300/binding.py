@@ -110,6 +110,8 @@ def lib():
             "vqg_batch_energy_and_gradient": (i, [p, p, p, p]),
             "vqg_batch_energy_and_gradient_device": (i, [p, p, p, p]),
             "vqg_batch_info": (i, [p, p, p, p]),
+            "vqg_batch_autotune": (i, [p, p, p]),
+            "vqg_batch_set_tile_qubits": (i, [p, i]),
             "vqg_batch_destroy": (i, [p]),
         }
         for name, (res, args) in sigs.items():

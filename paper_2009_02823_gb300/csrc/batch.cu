@@ -1,8 +1,10 @@
 // Batched launch: many independent circuits (energy + full gradient each) in one
 // persistent kernel.
 //
-// Every circuit is planned with the same tile geometry (complex64, K = 12, 4 register
-// qubits forward and reverse, 256 threads), and all plans are concatenated.  A task is
+// Every circuit is planned with the same tile geometry (complex64; K = 12 tile qubits
+// with 4 register qubits, or K = 11 with 3, both 256 threads; vqg_batch_autotune times
+// both), with a smaller shared-memory program than the single-circuit kernels so that
+// two or three blocks stay resident per SM, and all plans are concatenated.  A task is
 // (circuit, phase, chunk of tiles); the phases of a circuit are its forward passes,
 // its Hamiltonian passes, its reverse passes (last pass first) and a finalize step.
 // Tasks sit in one queue ordered by phase level, and resident blocks claim them with an
@@ -25,7 +27,10 @@
 
 namespace vqg {
 
-constexpr int kBK = 12, kBR = 4, kBNT = 256;
+constexpr int kBNT = 256;         // threads per block in every phase: 2^(K - R)
+constexpr int kBatchMinQubits = 12;
+// Compiled tile geometries (tile qubits K, register qubits R) of the batched kernel.
+constexpr int kBatchGeom[2][2] = {{12, 4}, {11, 3}};
 
 struct BCirc {
     uint64_t psi_off, lam_off;  // amplitude offsets into the state arena
@@ -71,8 +76,8 @@ struct BatchArgs {
 
 template <typename T, int K, int R>
 struct BatchCfg {
-    using FC = FwdCfg<T, K, R>;
-    using RC = RevCfg<T, K, R>;
+    using FC = FwdCfg<T, K, R, BatchCaps>;
+    using RC = RevCfg<T, K, R, BatchCaps>;
     using HC = HamCfg<T, K>;
     static constexpr size_t smem() {
         size_t m = FC::smem();
@@ -96,8 +101,8 @@ VQG_DEV bool wait_count(const unsigned long long *cnt, unsigned long long need, 
 template <typename T, int K, int R>
 __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
     using A = amp_t<T>;
-    using FC = FwdCfg<T, K, R>;
-    using RC = RevCfg<T, K, R>;
+    using FC = typename BatchCfg<T, K, R>::FC;
+    using RC = typename BatchCfg<T, K, R>::RC;
     using HC = HamCfg<T, K>;
     static_assert((1 << (K - R)) == kBNT, "one block size for every phase");
     constexpr int NW = kBNT / 32;
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             A *tile = reinterpret_cast<A *>(smem);
             uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + FC::o_row);
             Prog<T, R> pg;
-            pg.bind(smem + FC::o_prog);
+            pg.template bind<BatchCaps>(smem + FC::o_prog);
             fill_row_offsets<T, K>(P.high, row_off, tid, kBNT);
             load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, a.stages, a.ops, a.diags, a.items,
                             a.mats, false, tid, kBNT);
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             A *tlam = tphi + (1 << K);
             uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + RC::o_row);
             Prog<T, R> pg;
-            pg.bind(smem + RC::o_prog);
+            pg.template bind<BatchCaps>(smem + RC::o_prog);
             double *acc = reinterpret_cast<double *>(smem + RC::o_acc);
             T *stash = reinterpret_cast<T *>(smem + RC::o_stash);
             int *smap = reinterpret_cast<int *>(smem + RC::o_map);
@@ -246,6 +251,7 @@ struct vqg_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int num_sms = 1, grid = 1, n_tasks = 0, total_params = 0, total_gates = 0;
+    int bk = kBatchGeom[0][0], br = kBatchGeom[0][1];  // tile geometry
     bool built = false;
     long long spin_limit = 1ll << 26;
     int stall_circ = -1;
@@ -278,13 +284,24 @@ struct vqg_batch {
             return set_error(VQG_ERR_CUDA, "batch upload failed");
         return VQG_OK;
     }
-    ~vqg_batch() {
+    // Release everything build() made (plans, tables, state arena, graph).
+    void reset() {
+        if (stream) cudaStreamSynchronize(stream);
         if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+        graph_warm = false;
         for (void *p : allocs) cudaFree(p);
+        allocs.clear();
         if (h_pinned) cudaFreeHost(h_pinned);
+        h_pinned = nullptr;
+        built = false;
+    }
+    ~vqg_batch() {
+        reset();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
     int build();
+    int autotune(const double *theta, vqg_tune_result *out);
     int issue(const double *theta_dev, double *energy_dev, double *grad_dev);
     int run(const double *theta_dev, double *energy_dev, double *grad_dev);
 };
@@ -293,9 +310,9 @@ int vqg_batch::build() {
     if (built) return VQG_OK;
     vqg_options opt;
     vqg_default_options(&opt);
-    opt.tile_qubits = kBK;
-    opt.fwd_reg_qubits = kBR;
-    opt.rev_reg_qubits = kBR;
+    opt.tile_qubits = bk;
+    opt.fwd_reg_qubits = br;
+    opt.rev_reg_qubits = br;
     std::vector<FPass> passes;
     std::vector<FStage> stages;
     std::vector<FOp> ops;
@@ -316,7 +333,7 @@ int vqg_batch::build() {
         BatchCircuit &bc = c[b];
         if (!bc.has_ham) return set_error(VQG_ERR_STATE, "circuit %zu of the batch has no Hamiltonian", b);
         std::string err;
-        Plan *pl = plan_gates(bc.n, bc.gates, bc.slot_base, bc.n_gslots, false, opt, err);
+        Plan *pl = plan_gates(bc.n, bc.gates, bc.slot_base, bc.n_gslots, false, opt, err, BatchCaps::value(), false);
         if (!pl) return set_error(VQG_ERR_UNSUPPORTED, "batch circuit %zu: %s", b, err.empty() ? "no fused plan" : err.c_str());
         if (!plan_hamiltonian(pl, bc.n, bc.ham, bc.terms)) {
             delete pl;
@@ -378,7 +395,7 @@ int vqg_batch::build() {
         }
         occ_ptr.push_back((int)occ.size());
         C.n_gslots = bc.n_gslots;
-        C.n_tiles = 1 << (bc.n - kBK);
+        C.n_tiles = 1 << (bc.n - bk);
         const int chunks = std::min(C.n_tiles, 32);
         C.tch = (C.n_tiles + chunks - 1) / chunks;
         C.chunks = (C.n_tiles + C.tch - 1) / C.tch;
@@ -445,10 +462,12 @@ int vqg_batch::build() {
     if ((st = dalloc((void **)&d_out, sizeof(double) * (c.size() + param0)))) return st;
     if (cudaMallocHost((void **)&h_pinned, sizeof(double) * (c.size() + 2 * (size_t)param0 + 1)) != cudaSuccess)
         return set_error(VQG_ERR_OOM, "pinned staging allocation failed");
-    smem = BatchCfg<float, kBK, kBR>::smem();
-    cudaFuncSetAttribute(k_batch<float, kBK, kBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool g12 = bk == 12;
+    smem = g12 ? BatchCfg<float, 12, 4>::smem() : BatchCfg<float, 11, 3>::smem();
+    const void *fn = g12 ? (const void *)k_batch<float, 12, 4> : (const void *)k_batch<float, 11, 3>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<float, kBK, kBR>, kBNT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBNT, smem);
     grid = num_sms * std::max(per_sm, 1);  // all blocks resident: waits only on running blocks
     built = true;
     return VQG_OK;
@@ -465,7 +484,8 @@ int vqg_batch::issue(const double *theta_dev, double *energy_dev, double *grad_d
     cudaMemsetAsync(A.done, 0, sizeof(unsigned long long) * c.size(), stream);
     cudaMemsetAsync(A.err, 0, sizeof(int), stream);
     launch_build_mats(theta_dev, d_gates, total_gates, d_mats, d_mats_f, -1, -1, 0.0, stream);
-    k_batch<float, kBK, kBR><<<grid, kBNT, smem, stream>>>(A);
+    if (bk == 12) k_batch<float, 12, 4><<<grid, kBNT, smem, stream>>>(A);
+    else k_batch<float, 11, 3><<<grid, kBNT, smem, stream>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     return VQG_OK;
@@ -511,6 +531,65 @@ int vqg_batch::run(const double *theta_dev, double *energy_dev, double *grad_dev
     return VQG_OK;
 }
 
+// Time one evaluation of the whole batch under each compiled tile geometry and keep the
+// fastest (the choice depends on the mix of circuit sizes and depths).
+int vqg_batch::autotune(const double *theta, vqg_tune_result *out) {
+    vqg_tune_result r;
+    std::memset(&r, 0, sizeof r);
+    double best = 1e300;
+    int bi = 0;
+    const int n_geom = (int)(sizeof kBatchGeom / sizeof kBatchGeom[0]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_error(VQG_ERR_CUDA, "batch autotune: event creation failed");
+    int st = VQG_OK;
+    for (int gi = 0; gi < n_geom && !st; ++gi) {
+        reset();
+        bk = kBatchGeom[gi][0];
+        br = kBatchGeom[gi][1];
+        if ((st = build())) break;
+        const int P = total_params, nc = (int)c.size();
+        if (theta) std::memcpy(h_pinned, theta, sizeof(double) * P);
+        else std::memset(h_pinned, 0, sizeof(double) * P);
+        cudaMemcpyAsync(d_theta, h_pinned, sizeof(double) * P, cudaMemcpyHostToDevice, stream);
+        if ((st = issue(d_theta, d_out, d_out + nc))) break;  // warm-up
+        cudaEventRecord(e0, stream);
+        if ((st = issue(d_theta, d_out, d_out + nc))) break;
+        cudaEventRecord(e1, stream);
+        int errflag = 0;
+        cudaMemcpyAsync(h_pinned + P, args.err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            st = set_error(VQG_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        std::memcpy(&errflag, h_pinned + P, sizeof(int));
+        if (errflag) {
+            st = set_error(VQG_ERR_TIMEOUT, "a batched task gave up waiting for its circuit's previous phase");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ++r.candidates;
+        if (gi == 0) r.default_ms = ms;
+        if (ms < best) best = ms, bi = gi;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (bk != kBatchGeom[bi][0]) {
+        reset();
+        bk = kBatchGeom[bi][0];
+        br = kBatchGeom[bi][1];
+        if ((st = build())) return st;
+    }
+    r.tile_qubits = bk;
+    r.fwd_reg_qubits = r.rev_reg_qubits = br;
+    r.best_ms = best;
+    if (out) *out = r;
+    return VQG_OK;
+}
+
 extern "C" int vqg_batch_create(int n_circuits, const int *n_qubits, const vqg_gate *gates,
                                 const int *gate_offsets, const int *n_params, int dtype, vqg_batch **out) {
     if (!out) return set_error(VQG_ERR_INVALID, "out is NULL");
@@ -522,8 +601,9 @@ extern "C" int vqg_batch_create(int n_circuits, const int *n_qubits, const vqg_g
     for (int b = 0; b < n_circuits; ++b) {
         const int G = gate_offsets[b + 1] - gate_offsets[b];
         if (G < 1) return set_error(VQG_ERR_INVALID, "circuit %d: no gates", b);
-        if (n_qubits[b] < kBK || n_qubits[b] > 30)
-            return set_error(VQG_ERR_INVALID, "circuit %d: n_qubits=%d outside %d..30", b, n_qubits[b], kBK);
+        if (n_qubits[b] < kBatchMinQubits || n_qubits[b] > 30)
+            return set_error(VQG_ERR_INVALID, "circuit %d: n_qubits=%d outside %d..30", b, n_qubits[b],
+                             kBatchMinQubits);
         const int st = vqg_validate_circuit(n_qubits[b], gates + gate_offsets[b], G, n_params[b], dtype);
         if (st) return st;
     }
@@ -637,4 +717,25 @@ extern "C" int vqg_batch_info(vqg_batch *b, int *n_tasks, int *grid, int *total_
     if (grid) *grid = b->grid;
     if (total_params) *total_params = b->total_params;
     return VQG_OK;
+}
+
+extern "C" int vqg_batch_autotune(vqg_batch *b, const double *theta, vqg_tune_result *out) {
+    if (!b) return set_error(VQG_ERR_INVALID, "batch is NULL");
+    for (const BatchCircuit &bc : b->c)
+        if (!bc.has_ham) return set_error(VQG_ERR_STATE, "every circuit needs a Hamiltonian first");
+    return b->autotune(theta, out);
+}
+
+extern "C" int vqg_batch_set_tile_qubits(vqg_batch *b, int tile_qubits) {
+    if (!b) return set_error(VQG_ERR_INVALID, "batch is NULL");
+    for (const auto &g : kBatchGeom)
+        if (g[0] == tile_qubits) {
+            if (b->bk != g[0]) {
+                b->reset();
+                b->bk = g[0];
+                b->br = g[1];
+            }
+            return VQG_OK;
+        }
+    return set_error(VQG_ERR_UNSUPPORTED, "no batched kernel with %d tile qubits", tile_qubits);
 }

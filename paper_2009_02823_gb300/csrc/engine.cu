@@ -355,7 +355,7 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
         const FPass &p = pl.passes[j];
         std::string e = check_geom(p.high, p.n_high, p.nontile, p.n_nontile);
         if (!e.empty()) return e;
-        if (p.n_stage < 1 || p.n_stage > kMaxPassStages || p.n_rstage < 1 || p.n_rstage > kMaxPassStages)
+        if (p.n_stage < 1 || p.n_stage > pl.caps.stages || p.n_rstage < 1 || p.n_rstage > pl.caps.stages)
             return fail("stage count", p.n_stage, p.n_rstage);
         if (p.n_lslots < 0 || p.n_lslots > kMaxPassSlots) return fail("slot count", (int)j, p.n_lslots);
         if (p.slotmap0 < 0 || p.slotmap0 + p.n_lslots > (int)pl.slot_map.size()) return fail("slot map", (int)j, p.slotmap0);
@@ -433,11 +433,11 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                     }
                 }
             }
-            if (op_total > kMaxPassOps) return fail("ops per pass", (int)j, op_total);
+            if (op_total > pl.caps.ops) return fail("ops per pass", (int)j, op_total);
         }
         for (int dir = 0; dir < 2; ++dir) {
             const int d0 = dir ? p.rdiag0 : p.diag0, nd = dir ? p.n_rdiag : p.n_diag;
-            if (nd > kMaxPassDiags) return fail("diagonal blocks per pass", (int)j, nd);
+            if (nd > pl.caps.diags) return fail("diagonal blocks per pass", (int)j, nd);
             if (nd) {
                 if (d0 < 0 || d0 + nd > (int)pl.diags.size()) return fail("diagonal range", d0, nd);
                 int it = pl.diags[d0].item0;
@@ -445,7 +445,7 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                     if (pl.diags[d].item0 != it) return fail("item contiguity", d, pl.diags[d].item0);
                     it += pl.diags[d].n_item;
                 }
-                if (it - pl.diags[d0].item0 > kMaxPassItems) return fail("items per pass", (int)j, it);
+                if (it - pl.diags[d0].item0 > pl.caps.items) return fail("items per pass", (int)j, it);
             }
         }
     }
@@ -488,7 +488,8 @@ static int occupancy_grid(int num_sms, int per_sm, uint64_t n_tiles) {
 // empty `err` when no fused schedule applies (n or the tile below 10 qubits, fusion
 // off), nullptr with `err` set when the plan fails validation.
 Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
-                        int n_gslots, bool dbl, const vqg_options &opt, std::string &err) {
+                        int n_gslots, bool dbl, const vqg_options &opt, std::string &err, const PassCaps &caps,
+                        bool single_kernels) {
     err.clear();
     const int G = (int)gates.size();
     int K = std::min(n, default_tile_qubits(n, dbl));
@@ -496,11 +497,14 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
     const int Rf = opt.fwd_reg_qubits > 0 ? opt.fwd_reg_qubits : (dbl ? 4 : 5);
     const int Rr = opt.rev_reg_qubits > 0 ? opt.rev_reg_qubits : (dbl ? 3 : 4);
     if (!opt.fusion || G == 0 || K < 10) return nullptr;
-    if (!fused_supported(dbl, K, Rf, Rr)) {
+    if (single_kernels ? !fused_supported(dbl, K, Rf, Rr)
+                       : (Rf < 1 || Rr < 1 || Rf > kMaxRegBits || Rr > kMaxRegBits || K > 13 ||
+                          K - Rf > kMaxThreadBits || K - Rr > kMaxThreadBits)) {
         err = "no compiled fused kernel for this tile / register-qubit choice";
         return nullptr;
     }
     Plan *pl = new Plan();
+    pl->caps = caps;
     pl->K = K;
     pl->L = dbl ? 3 : 4;
     pl->Rf = Rf;
@@ -515,7 +519,7 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
         std::vector<char> inS(n, 0);
         for (int q = 0; q < n; ++q) inS[q] = tm.pos_of[q] >= 0;
         // a pass must fit the kernels' shared-memory program budget; shrink it if not
-        for (int cap = kMaxPassOps;; cap = std::max(1, cap / 2)) {
+        for (int cap = caps.ops;; cap = std::max(1, cap / 2)) {
             greedy(gates, rem, inS, n, cap, kMaxPassSlots, applied, left);
             const size_t n_st = pl->stages.size(), n_op = pl->ops.size(), n_dg = pl->diags.size();
             const size_t n_it = pl->items.size(), n_sm = pl->slot_map.size();
@@ -537,10 +541,10 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
             auto items_of = [&](int d0, int nd) {
                 return nd ? pl->diags[d0 + nd - 1].item0 + pl->diags[d0 + nd - 1].n_item - pl->diags[d0].item0 : 0;
             };
-            const bool fits = p.n_stage <= kMaxPassStages && p.n_rstage <= kMaxPassStages &&
-                              p.n_diag <= kMaxPassDiags && p.n_rdiag <= kMaxPassDiags &&
-                              items_of(p.diag0, p.n_diag) <= kMaxPassItems &&
-                              items_of(p.rdiag0, p.n_rdiag) <= kMaxPassItems;
+            const bool fits = p.n_stage <= caps.stages && p.n_rstage <= caps.stages &&
+                              p.n_diag <= caps.diags && p.n_rdiag <= caps.diags &&
+                              items_of(p.diag0, p.n_diag) <= caps.items &&
+                              items_of(p.rdiag0, p.n_rdiag) <= caps.items;
             if (fits || cap == 1) {
                 pl->passes.push_back(p);
                 break;

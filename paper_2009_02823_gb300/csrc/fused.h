@@ -30,6 +30,20 @@ constexpr int kMaxStageRowsDbl = 8;  // the same for complex128 (FP64 stash)
 constexpr int kMaxHamGroups = 256;   // groups per Hamiltonian pass
 constexpr int kMaxHamTerms = 1024;   // terms per Hamiltonian pass
 
+// Per-pass program budget of a kernel's shared-memory program; the planner keeps every
+// pass within the budget of the kernel that will run it.
+struct PassCaps {
+    int ops, stages, diags, items;
+};
+template <int OPS, int STAGES, int DIAGS, int ITEMS>
+struct CapsT {
+    static constexpr int ops = OPS, stages = STAGES, diags = DIAGS, items = ITEMS;
+    static constexpr PassCaps value() { return {OPS, STAGES, DIAGS, ITEMS}; }
+};
+using FullCaps = CapsT<kMaxPassOps, kMaxPassStages, kMaxPassDiags, kMaxPassItems>;
+// The batched launch's smaller program keeps two 256-thread blocks resident per SM.
+using BatchCaps = CapsT<96, 32, 24, 160>;
+
 enum FOpType : int16_t {
     OP_RY = 0,    // real rotation on register bit k
     OP_RX = 1,    // RX on register bit k (complex matrix)

@@ -140,14 +140,18 @@ template <typename T, int R>
 struct Prog {
     static constexpr int AB = FT<T>::AB;
     static constexpr size_t align8(size_t x) { return (x + 15) & ~(size_t)15; }
-    static constexpr size_t o_st = 0;
-    static constexpr size_t o_op = align8(o_st + sizeof(FStage) * kMaxPassStages);
-    static constexpr size_t o_dg = align8(o_op + sizeof(FOp) * kMaxPassOps);
-    static constexpr size_t o_it = align8(o_dg + sizeof(FDiag) * kMaxPassDiags);
-    static constexpr size_t o_prm = align8(o_it + sizeof(FDItem) * kMaxPassItems);
-    static constexpr size_t o_iph = align8(o_prm + (size_t)AB * 4 * kMaxPassOps);
-    static constexpr size_t o_tab = align8(o_iph + (size_t)AB * 2 * kMaxPassItems);
-    static constexpr size_t bytes = align8(o_tab + (size_t)AB * (1 << R) * kMaxPassDiags);
+    // shared-memory layout for the program budget C
+    template <typename C = FullCaps>
+    struct Layout {
+        static constexpr size_t o_st = 0;
+        static constexpr size_t o_op = align8(o_st + sizeof(FStage) * C::stages);
+        static constexpr size_t o_dg = align8(o_op + sizeof(FOp) * C::ops);
+        static constexpr size_t o_it = align8(o_dg + sizeof(FDiag) * C::diags);
+        static constexpr size_t o_prm = align8(o_it + sizeof(FDItem) * C::items);
+        static constexpr size_t o_iph = align8(o_prm + (size_t)AB * 4 * C::ops);
+        static constexpr size_t o_tab = align8(o_iph + (size_t)AB * 2 * C::items);
+        static constexpr size_t bytes = align8(o_tab + (size_t)AB * (1 << R) * C::diags);
+    };
 
     FStage *st;
     FOp *op;
@@ -156,14 +160,16 @@ struct Prog {
     amp_t<T> *prm, *iph, *tab;
     int op_base, item_base;
 
+    template <typename C = FullCaps>
     VQG_DEV void bind(unsigned char *p) {
-        st = reinterpret_cast<FStage *>(p + o_st);
-        op = reinterpret_cast<FOp *>(p + o_op);
-        dg = reinterpret_cast<FDiag *>(p + o_dg);
-        it = reinterpret_cast<FDItem *>(p + o_it);
-        prm = reinterpret_cast<amp_t<T> *>(p + o_prm);
-        iph = reinterpret_cast<amp_t<T> *>(p + o_iph);
-        tab = reinterpret_cast<amp_t<T> *>(p + o_tab);
+        using Lo = Layout<C>;
+        st = reinterpret_cast<FStage *>(p + Lo::o_st);
+        op = reinterpret_cast<FOp *>(p + Lo::o_op);
+        dg = reinterpret_cast<FDiag *>(p + Lo::o_dg);
+        it = reinterpret_cast<FDItem *>(p + Lo::o_it);
+        prm = reinterpret_cast<amp_t<T> *>(p + Lo::o_prm);
+        iph = reinterpret_cast<amp_t<T> *>(p + Lo::o_iph);
+        tab = reinterpret_cast<amp_t<T> *>(p + Lo::o_tab);
     }
 };
 
@@ -690,13 +696,15 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
 }
 
 // ------------------------------------------------------------------ forward pass
-template <typename T, int K, int R>
+template <typename T, int K, int R, typename CAPS = FullCaps>
 struct FwdCfg {
+    using Caps = CAPS;
     static constexpr int NT = 1 << (K - R);
     static constexpr size_t o_row = (size_t)(1 << K) * FT<T>::AB;
     static constexpr size_t o_prog = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
-    static constexpr size_t smem() { return o_prog + Prog<T, R>::bytes; }
-    static_assert(o_prog + Prog<T, R>::bytes <= 227 * 1024, "forward pass exceeds shared memory");
+    static constexpr size_t prog_bytes = Prog<T, R>::template Layout<CAPS>::bytes;
+    static constexpr size_t smem() { return o_prog + prog_bytes; }
+    static_assert(o_prog + prog_bytes <= 227 * 1024, "forward pass exceeds shared memory");
 };
 
 template <typename T, int K, int R>
@@ -712,7 +720,7 @@ __global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
     A *tile = reinterpret_cast<A *>(smem);
     uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
     Prog<T, R> pg;
-    pg.bind(smem + C::o_prog);
+    pg.template bind<typename C::Caps>(smem + C::o_prog);
     const FPass &P = passes[pi];
     const int tid = threadIdx.x;
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
@@ -724,12 +732,13 @@ __global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
 }
 
 // ------------------------------------------------------------------ reverse pass
-template <typename T, int K, int R>
+template <typename T, int K, int R, typename CAPS = FullCaps>
 struct RevCfg {
+    using Caps = CAPS;
     static constexpr int NT = 1 << (K - R), NW = NT / 32;
     static constexpr size_t o_row = 2 * (size_t)(1 << K) * FT<T>::AB;
     static constexpr size_t o_prog = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
-    static constexpr size_t o_acc = o_prog + Prog<T, R>::bytes;
+    static constexpr size_t o_acc = o_prog + Prog<T, R>::template Layout<CAPS>::bytes;
     static constexpr size_t o_stash = o_acc + sizeof(double) * kMaxPassSlots;
     static constexpr size_t o_map = o_stash + sizeof(T) * (size_t)stash_rows<T>() * NT;
     static constexpr size_t smem() { return o_map + sizeof(int) * kMaxPassSlots; }
@@ -753,7 +762,7 @@ __global__ void __launch_bounds__(1 << (K - R))
     A *tlam = tphi + (1 << K);
     uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
     Prog<T, R> pg;
-    pg.bind(smem + C::o_prog);
+    pg.template bind<typename C::Caps>(smem + C::o_prog);
     double *acc = reinterpret_cast<double *>(smem + C::o_acc);
     T *stash = reinterpret_cast<T *>(smem + C::o_stash);
     int *smap = reinterpret_cast<int *>(smem + C::o_map);

@@ -13,6 +13,7 @@ namespace vqg {
 
 struct Plan {
     int K = 0, L = 0, Rf = 0, Rr = 0;
+    PassCaps caps = FullCaps::value();  // program budget of the kernels that run the passes
     uint64_t n_tiles = 0;
     int grid_fwd = 0;
     std::vector<FPass> passes;
@@ -38,9 +39,12 @@ struct Plan {
 };
 
 // Plan the gate passes of one circuit (host only; nullptr + empty err: no fused
-// schedule applies; nullptr + err: the plan failed its checks).
+// schedule applies; nullptr + err: the plan failed its checks).  single_kernels: the
+// (K, Rf, Rr) choice must be one the single-circuit launchers compiled; the batched
+// kernel passes false (it has its own instantiations).
 Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
-                 int n_gslots, bool dbl, const vqg_options &opt, std::string &err);
+                 int n_gslots, bool dbl, const vqg_options &opt, std::string &err,
+                 const PassCaps &caps = FullCaps::value(), bool single_kernels = true);
 // Hamiltonian tile passes of a plan; false if some group cannot live in one tile.
 bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham, const std::vector<PauliTerm> &host_terms);
 std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl);

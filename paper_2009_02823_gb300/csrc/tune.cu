@@ -133,7 +133,8 @@ int Circuit::autotune(const double *theta_dev, vqg_tune_result *out) {
     double best = 1e300;
     int bK = K0, bRf = Rf0, bRr = Rr0;
     bool warm = false;
-    for (int K = Kmax; K >= std::max(10, Kmax - 2); --K) {
+    const int Kmin = std::max(10, std::min(K0, Kmax - 2));  // the default is always a candidate
+    for (int K = Kmax; K >= Kmin; --K) {
         double best_f = 1e300, best_r = 1e300, ham_t = 0, best_pair = 1e300;
         int kRf = 0, kRr = 0, pRf = 0, pRr = 0;
         for (const auto &rp : reg_pairs) {

@@ -33,6 +33,40 @@ def test_small_batch_vs_oracle():
                 assert_parity("c64", e[k], g[k], e_ref, g_ref, f"batch circuit {k} call {call}")
 
 
+def test_batch_autotune_then_parity():
+    """The geometry autotuner times both compiled tile geometries, keeps one, and the
+    batch still matches the oracle afterwards (eager, captured and replayed calls)."""
+    from paper_2009_02823_gb300.batch import Batch
+    ws = _small_batch()
+    with Batch(ws) as b:
+        b.energy_and_gradient([w.theta for w in ws])  # built and run before tuning
+        r = b.autotune([w.theta for w in ws])
+        assert r["candidates"] == 2 and (r["tile_qubits"], r["fwd_reg_qubits"]) in ((12, 4), (11, 3))
+        assert r["best_ms"] > 0 and r["default_ms"] >= r["best_ms"]
+        for call in range(3):
+            thetas = [w.theta - 0.05 * call for w in ws]
+            e, g = b.energy_and_gradient(thetas)
+            for k, w in enumerate(ws):
+                e_ref, g_ref = oracle.gradient_alg1(w.n, w.gates, thetas[k], w.n_params, w.terms)
+                assert_parity("c64", e[k], g[k], e_ref, g_ref, f"tuned batch circuit {k} call {call}")
+
+
+def test_batch_both_geometries_match_oracle():
+    """Both compiled tile geometries give oracle results, whatever the tuner picks."""
+    from paper_2009_02823_gb300 import binding as B
+    from paper_2009_02823_gb300.batch import Batch
+    ws = _small_batch()[:4]
+    with Batch(ws) as b:
+        for K in (11, 12):
+            b.set_tile_qubits(K)
+            e, g = b.energy_and_gradient([w.theta for w in ws])
+            for k, w in enumerate(ws):
+                e_ref, g_ref = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
+                assert_parity("c64", e[k], g[k], e_ref, g_ref, f"tile qubits {K} circuit {k}")
+        with pytest.raises(B.VqgError):
+            b.set_tile_qubits(13)
+
+
 def test_wait_timeout_is_reported_and_recoverable():
     from paper_2009_02823_gb300.batch import Batch
     from paper_2009_02823_gb300.binding import VqgError
