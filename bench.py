@@ -18,6 +18,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -29,6 +30,16 @@ from paper_2009_02823_gb300.replicas import (circuit_cost, max_over_ranks, parti
                                              replica_theta)
 
 METRIC = "adjoint gradients/s at n=30,P=600"
+
+# DRAM bytes (read + write) per launch per amplitude of the state, from one ncu capture
+# of each fused complex64 kernel at n=26 (profiles/k_fused_*_n26_c64.md).  Every launch
+# streams whole states, so traffic scales with 2^n.  Reset an entry to None whenever
+# its kernel changes until it is captured again.
+NCU_TRAFFIC_PER_AMP_C64 = {
+    "adj_fused": (1.073967e9 + 1.016815e9) / 2**26,
+    "fwd_fused": (0.537456384e9 + 0.486807552e9) / 2**26,
+    "ham_fused": (1.073797e9 + 0.487862784e9) / 2**26,
+}
 UNIT = "gradients/s"
 
 
@@ -67,7 +78,9 @@ class Clocks:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # raw samples go to $VQG_CLOCKS_DIR (default: the system temp directory)
+        out_dir = os.environ.get("VQG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"vqg_clocks_rank{device_index}.csv")
 
     def start(self):
         try:
@@ -262,6 +275,11 @@ def run_ours(args, rank, world, dist):
                     "unit": "GB/s", "frac": round(hbm / peak, 4), "peak_source": peak_kind,
                     "traffic": None, "bytes_per_launch": per, "launches": launches,
                     "avg_launch_ms": round(tot_ms / launches, 4), "share_of_step": round(tot_ms / total_ms, 4)}
+    if roof is not None:
+        per_amp = NCU_TRAFFIC_PER_AMP_C64.get(fam) if args.dtype == "c64" else None
+        if per_amp is not None:
+            roof["traffic"] = round(per_amp * (1 << w.n))
+            roof["traffic_source"] = "ncu dram__bytes_read+write per launch at n=26, scaled by 2^(n-26)"
     gpu_launches = int(sum(v[0] for v in stats.values()))
 
     extra = {}
@@ -396,7 +414,7 @@ def cpu_baseline_sample(args, w, budget_s=20.0):
         per[kind] = (t1 - t0, t2 - t1)
         if time.perf_counter() - t_start > budget_s:
             break
-    # derivative step: clone + apply dU + inner product (Algorithm 1, lines 7-9)
+    # derivative step: clone + apply dU + inner product (Algorithm 1's derivative step)
     t0 = time.perf_counter()
     mu = psi.copy()
     d = oracle.gate_derivative("RY", 0, [0.3])

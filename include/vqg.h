@@ -115,7 +115,7 @@ int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *x_mask,
  * stream).  The caller keeps the stream alive while the circuit uses it. */
 int vqg_set_stream(vqg_circuit *c, void *stream);
 
-/* E(theta): forward sweep (Algorithm 1, line 2) then <psi|H|psi> with FP64 reduction.
+/* E(theta): forward sweep (Algorithm 1's forward sweep) then <psi|H|psi> with FP64 reduction.
  * theta: host array of n_params doubles.  energy: host double.  Blocks until done. */
 int vqg_energy(vqg_circuit *c, const double *theta, double *energy);
 

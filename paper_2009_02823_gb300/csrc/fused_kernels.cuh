@@ -4,11 +4,11 @@
 //
 //   k_fused_fwd : one forward pass -- every tile of 2^K amplitudes is read from HBM once,
 //                 a run of gates is applied in shared memory / registers, and the tile
-//                 is written once (Algorithm 1, line 2, many gates per state traversal).
+//                 is written once (Algorithm 1's forward sweep, many gates per state traversal).
 //   k_fused_rev : one reverse pass -- phi and lambda tiles are read once, and for each
 //                 gate of the run in reverse order the kernel reduces the gradient sums
 //                 from (phi_{i+1}, lambda_i) and un-applies U_i^dagger to both
-//                 (Algorithm 1, lines 6-11, with App. A's dR = -(i/2) sigma R so that
+//                 (Algorithm 1's reverse loop, with App. A's dR = -(i/2) sigma R so that
 //                 mu = dU phi is never formed; App. B.1 for U3).
 //   k_fused_ham : one Hamiltonian pass -- the Pauli groups whose flip mask lies inside
 //                 the tile, lambda (+)= sum_g f_g(j^x) psi[j^x], with E = Re<psi|lambda>.

@@ -1,5 +1,5 @@
-// One kernel per gate: the unfused forward sweep (Algorithm 1, line 2, "apply gate")
-// and the fused adjoint step (Algorithm 1, lines 6-11 in one pass):
+// One kernel per gate: the unfused forward sweep (Algorithm 1's forward sweep, "apply gate")
+// and the fused adjoint step (one step of Algorithm 1's reverse loop in one pass):
 //   read phi_{i+1} and lambda_i once, reduce the gradient sums, write
 //   phi_i = U_i^dag phi_{i+1} and lambda_{i-1} = U_i^dag lambda_i.
 // mu = dU_i phi_i is never stored (App. A: dR/dt = -(i/2) sigma R, so

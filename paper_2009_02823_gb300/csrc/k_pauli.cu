@@ -1,4 +1,4 @@
-// Hamiltonian application |lambda> = H|psi> for a Pauli sum (Algorithm 1, line 4) with
+// Hamiltonian application |lambda> = H|psi> for a Pauli sum (Algorithm 1, before the reverse loop) with
 // the energy E = Re <psi|lambda> fused in.
 //
 // A term coef * i^{popcount(x&z)} X^x Z^z maps psi to

@@ -43,7 +43,7 @@ def test_noalloc_matches_energy_and_gradient(dtype):
     with B.Circuit(n, gates, P, dtype) as c:
         c.set_hamiltonian(terms)
         e_ref, g_ref = c.energy_and_gradient(theta)
-    # psi and lambda = H psi as the reverse sweep starts (Algorithm 1, lines 1-4)
+    # psi and lambda = H psi as the reverse sweep starts (Algorithm 1, before the reverse loop)
     psi = oracle.state(n, gates, theta)
     lam = oracle.apply_hamiltonian(psi, terms)
     cdt = torch.complex64 if dtype == "c64" else torch.complex128
