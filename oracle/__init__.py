@@ -30,7 +30,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND = {"RX": 0, "RY": 1, "RZ": 2, "U3": 3, "CNOT": 4, "CZ": 5}
+KIND = {"RX": 0, "RY": 1, "RZ": 2, "U3": 3, "CNOT": 4, "CZ": 5,
+        "CRX": 6, "CRY": 7, "CRZ": 8, "PHASE": 9, "CPHASE": 10}
 LETTER = {"I": 0, "X": 1, "Y": 2, "Z": 3}
 
 
@@ -58,6 +59,8 @@ def _load():
             "oracle_gate_matrix": (None, [i, p, p]),
             "oracle_gate_derivative": (None, [i, i, p, p]),
             "oracle_apply_matrix_1q": (None, [i, p, i, p]),
+            "oracle_apply_controlled_1q": (None, [i, p, i, i, p]),
+            "oracle_apply_projected_1q": (None, [i, p, i, i, p]),
             "oracle_apply_gate": (None, [i, p, p, p, i]),
             "oracle_apply_gates": (None, [i, p, p, i, i, p]),
             "oracle_prepare_state": (None, [i, p, i, p, p]),

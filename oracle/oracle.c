@@ -24,11 +24,15 @@
  *   R_sigma(t) = exp(-i t sigma / 2), i.e. App. A's exp(alpha i t sigma) with alpha = -1/2;
  *   U3(t, f, l) = [[c, -e^{il} s], [e^{if} s, e^{i(f+l)} c]], c = cos(t/2), s = sin(t/2);
  *   CNOT(c -> t) flips t where c = 1; CZ(a, b) negates amplitudes with both bits 1;
+ *   CRX/CRY/CRZ(c -> t, t) apply R_sigma(t) to qubit t where qubit c = 1 (App. A's
+ *   C_c[U]); PHASE(t) = diag(1, e^{it}) (App. A); CPHASE(a, b, t) multiplies amplitudes
+ *   with both bits 1 by e^{it} (= C_a[PHASE on b]);
  *   a Pauli term is coef * (tensor product of per-qubit letters), applied here letter
  *   by letter as 2x2 matrices (no bit-mask algebra).
  *
  * Gate record: 6 int32 per gate = kind, q0, q1, param0, param1, param2
- *   kind 0 RX, 1 RY, 2 RZ, 3 U3, 4 CNOT, 5 CZ; unused params are -1.
+ *   kind 0 RX, 1 RY, 2 RZ, 3 U3, 4 CNOT, 5 CZ, 6 CRX, 7 CRY, 8 CRZ, 9 PHASE, 10 CPHASE;
+ *   controlled kinds: q0 = control, q1 = target; unused params are -1.
  * Hamiltonian: n_terms coefficients and an n_terms x n table of letters
  *   (0 = I, 1 = X, 2 = Y, 3 = Z), letters[t * n + q] acting on qubit q.
  */
@@ -43,24 +47,37 @@
 
 typedef double complex cplx;
 
-enum { OR_RX = 0, OR_RY = 1, OR_RZ = 2, OR_U3 = 3, OR_CNOT = 4, OR_CZ = 5 };
+enum {
+    OR_RX = 0, OR_RY = 1, OR_RZ = 2, OR_U3 = 3, OR_CNOT = 4, OR_CZ = 5,
+    OR_CRX = 6, OR_CRY = 7, OR_CRZ = 8, OR_PHASE = 9, OR_CPHASE = 10
+};
 
 #define PAR_FOR _Pragma("omp parallel for schedule(static) if (dim >= 16384)")
 
 static int n_params_of(int kind) {
     if (kind == OR_U3) return 3;
     if (kind == OR_RX || kind == OR_RY || kind == OR_RZ) return 1;
+    if (kind >= OR_CRX && kind <= OR_CPHASE) return 1;
     return 0;
 }
+
+/* Control qubit of a controlled parameterised gate (-1: none) and the qubit its 2x2
+ * matrix acts on. */
+static int control_of(const int32_t *g) {
+    return (g[0] >= OR_CRX && g[0] <= OR_CRZ) || g[0] == OR_CPHASE ? g[1] : -1;
+}
+static int target_of(const int32_t *g) { return control_of(g) >= 0 ? g[2] : g[1]; }
 
 int oracle_n_params_of_kind(int kind) { return n_params_of(kind); }
 
 /* ---------------------------------------------------------------- gate matrices */
 
 /* 2x2 matrix (row-major m[0]=m00, m[1]=m01, m[2]=m10, m[3]=m11) of a one-qubit gate
- * at angles a[0..2] (only a[0] for rotations). */
+ * at angles a[0..2] (only a[0] for rotations); for a controlled kind, the matrix applied
+ * to the target where the control is 1. */
 void oracle_gate_matrix(int kind, const double *a, cplx *m) {
     double c = cos(a[0] / 2.0), s = sin(a[0] / 2.0);
+    if (kind >= OR_CRX && kind <= OR_CRZ) kind -= OR_CRX - OR_RX;  /* same 2x2 as RX/RY/RZ */
     switch (kind) {
     case OR_RX: /* exp(-i t X / 2) = cos(t/2) I - i sin(t/2) X */
         m[0] = c; m[1] = -I * s; m[2] = -I * s; m[3] = c; break;
@@ -74,6 +91,9 @@ void oracle_gate_matrix(int kind, const double *a, cplx *m) {
         m[2] = cexp(I * a[1]) * s;
         m[3] = cexp(I * (a[1] + a[2])) * c;
         break;
+    case OR_PHASE:
+    case OR_CPHASE: /* diag(1, e^{it}) */
+        m[0] = 1; m[1] = 0; m[2] = 0; m[3] = cexp(I * a[0]); break;
     default:
         m[0] = 1; m[1] = 0; m[2] = 0; m[3] = 1;
     }
@@ -84,6 +104,7 @@ void oracle_gate_matrix(int kind, const double *a, cplx *m) {
 void oracle_gate_derivative(int kind, int slot, const double *a, cplx *d) {
     double c = cos(a[0] / 2.0), s = sin(a[0] / 2.0);
     cplx m[4];
+    if (kind >= OR_CRX && kind <= OR_CRZ) kind -= OR_CRX - OR_RX;  /* target part; App. A projects */
     switch (kind) {
     case OR_RX: /* (-i/2) X R */
         oracle_gate_matrix(kind, a, m);
@@ -116,6 +137,9 @@ void oracle_gate_derivative(int kind, int slot, const double *a, cplx *d) {
             d[3] = I * cexp(I * (a[1] + a[2])) * c;
         }
         break;
+    case OR_PHASE:
+    case OR_CPHASE: /* i e^{it} |1><1| (App. A) */
+        d[0] = 0; d[1] = 0; d[2] = 0; d[3] = I * cexp(I * a[0]); break;
     default:
         d[0] = d[1] = d[2] = d[3] = 0;
     }
@@ -134,6 +158,30 @@ void oracle_apply_matrix_1q(int n, cplx *psi, int q, const cplx *m) {
         psi[j] = m[0] * a0 + m[1] * a1;
         psi[j | bit] = m[2] * a0 + m[3] * a1;
     }
+}
+
+/* C_c[m]: the 2x2 matrix m on qubit t where qubit c is 1 (identity elsewhere). */
+void oracle_apply_controlled_1q(int n, cplx *psi, int c, int t, const cplx *m) {
+    const int64_t dim = (int64_t)1 << n;
+    const int64_t cb = (int64_t)1 << c, tb = (int64_t)1 << t;
+    PAR_FOR
+    for (int64_t j = 0; j < dim; ++j) {
+        if ((j & tb) || !(j & cb)) continue;
+        cplx a0 = psi[j], a1 = psi[j | tb];
+        psi[j] = m[0] * a0 + m[1] * a1;
+        psi[j | tb] = m[2] * a0 + m[3] * a1;
+    }
+}
+
+/* The derivative of a controlled gate (App. A): d on qubit t, then the amplitudes whose
+ * control qubit c is not 1 are overwritten with 0. */
+void oracle_apply_projected_1q(int n, cplx *psi, int c, int t, const cplx *d) {
+    const int64_t dim = (int64_t)1 << n;
+    const int64_t cb = (int64_t)1 << c;
+    oracle_apply_matrix_1q(n, psi, t, d);
+    PAR_FOR
+    for (int64_t j = 0; j < dim; ++j)
+        if (!(j & cb)) psi[j] = 0;
 }
 
 void oracle_apply_cnot(int n, cplx *psi, int control, int target) {
@@ -177,10 +225,21 @@ static void apply_gate_ex(int n, cplx *psi, const int32_t *g, const double *thet
     oracle_gate_matrix(kind, a, m);
     if (dagger) {
         cplx t[4] = {conj(m[0]), conj(m[2]), conj(m[1]), conj(m[3])};
-        oracle_apply_matrix_1q(n, psi, g[1], t);
-    } else {
-        oracle_apply_matrix_1q(n, psi, g[1], m);
+        m[0] = t[0]; m[1] = t[1]; m[2] = t[2]; m[3] = t[3];
     }
+    if (control_of(g) >= 0) oracle_apply_controlled_1q(n, psi, control_of(g), target_of(g), m);
+    else oracle_apply_matrix_1q(n, psi, target_of(g), m);
+}
+
+/* mu <- (dU_g / d slot) mu: the derivative matrix on the target, projected onto
+ * control = 1 for controlled kinds (App. A). */
+static void apply_gate_derivative(int n, cplx *mu, const int32_t *g, const double *theta, int slot) {
+    double a[3];
+    gate_angles(g, theta, a);
+    cplx d[4];
+    oracle_gate_derivative(g[0], slot, a, d);
+    if (control_of(g) >= 0) oracle_apply_projected_1q(n, mu, control_of(g), target_of(g), d);
+    else oracle_apply_matrix_1q(n, mu, target_of(g), d);
 }
 
 void oracle_apply_gate(int n, cplx *psi, const int32_t *g, const double *theta, int dagger) {
@@ -280,10 +339,18 @@ double oracle_energy(int n, const int32_t *gates, int n_gates, const double *the
     return e;
 }
 
-/* (a) Faithful gradient by the per-occurrence parameter-shift rule: every parameter
- * enters through a generator with eigenvalues +-1/2 (U3 = e^{i(f+l)/2} RZ(f) RY(t) RZ(l),
- * the phase being global), so [E(+pi/2) - E(-pi/2)] / 2 is exact per occurrence, and
- * occurrences of a shared parameter add by the chain rule (App. B.2).
+/* (a) Faithful gradient by per-occurrence parameter-shift rules, occurrences of a shared
+ * parameter adding by the chain rule (App. B.2).  As a function of one occurrence's angle
+ * t, E is a trigonometric polynomial whose frequencies are the differences of the
+ * generator's eigenvalues:
+ *   - RX/RY/RZ, U3 (= e^{i(f+l)/2} RZ(f) RY(t) RZ(l), global phase), PHASE (= e^{it/2}
+ *     RZ(t)) and CPHASE (generator |11><11|): eigenvalue differences {1}, so
+ *     E = a + b cos t + c sin t and dE/dt = [E(t + pi/2) - E(t - pi/2)] / 2 exactly;
+ *   - CRX/CRY/CRZ (generator (sigma/2) x |1><1|_c, eigenvalues 0, 0, +-1/2): frequencies
+ *     {1/2, 1}.  With D(s) = E(t + s) - E(t - s) = 2 sum_w sin(w s) [w-th derivative
+ *     term], requiring a1 D(pi/2) + a2 D(3pi/2) = dE/dt for w = 1/2 and w = 1 gives
+ *     a1 + a2 = 1/(2 sqrt 2), a1 - a2 = 1/2, i.e. a1 = (sqrt2 + 1)/(4 sqrt2),
+ *     a2 = -(sqrt2 - 1)/(4 sqrt2): a four-term rule, exact.
  * Optional: restrict to gate occurrences [g_first, g_last). */
 void oracle_gradient_parameter_shift(int n, const int32_t *gates, int n_gates,
                                      const double *theta, int n_params, int n_terms,
@@ -299,7 +366,15 @@ void oracle_gradient_parameter_shift(int n, const int32_t *gates, int n_gates,
         for (int j = 0; j < n_params_of(g[0]); ++j) {
             double ep = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, +h, psi);
             double em = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, -h, psi);
-            grad[g[3 + j]] += 0.5 * (ep - em);
+            if (g[0] >= OR_CRX && g[0] <= OR_CRZ) {
+                const double r2 = sqrt(2.0);
+                const double a1 = (r2 + 1.0) / (4.0 * r2), a2 = -(r2 - 1.0) / (4.0 * r2);
+                double ep3 = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, +3.0 * h, psi);
+                double em3 = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, -3.0 * h, psi);
+                grad[g[3 + j]] += a1 * (ep - em) + a2 * (ep3 - em3);
+            } else {
+                grad[g[3 + j]] += 0.5 * (ep - em);
+            }
         }
     }
     free(psi);
@@ -323,11 +398,7 @@ void oracle_gradient_alg2(int n, const int32_t *gates, int n_gates, const double
         for (int j = 0; j < n_params_of(g[0]); ++j) {
             oracle_zero_state(n, mu);
             oracle_apply_gates(n, mu, gates, 0, i, theta);
-            double a[3];
-            gate_angles(g, theta, a);
-            cplx d[4];
-            oracle_gate_derivative(g[0], j, a, d);
-            oracle_apply_matrix_1q(n, mu, g[1], d);
+            apply_gate_derivative(n, mu, g, theta, j);
             oracle_apply_gates(n, mu, gates, i + 1, n_gates, theta);
             grad[g[3 + j]] += 2.0 * creal(oracle_inner(n, lam, mu));
         }
@@ -357,12 +428,8 @@ void oracle_gradient_alg1(int n, const int32_t *gates, int n_gates, const double
         const int32_t *g = gates + 6 * i;
         oracle_apply_gate(n, phi, g, theta, 1);
         for (int j = 0; j < n_params_of(g[0]); ++j) {
-            double a[3];
-            gate_angles(g, theta, a);
-            cplx d[4];
-            oracle_gate_derivative(g[0], j, a, d);
             memcpy(mu, phi, sizeof(cplx) * (size_t)dim);
-            oracle_apply_matrix_1q(n, mu, g[1], d);
+            apply_gate_derivative(n, mu, g, theta, j);
             grad[g[3 + j]] += 2.0 * creal(oracle_inner(n, lam, mu));
         }
         if (i > 0) oracle_apply_gate(n, lam, g, theta, 1);

@@ -7,9 +7,10 @@ the CPU oracle may consume its output without sharing any computation.
 
 Neutral formats
 ---------------
-gate      : (kind, q0, q1, (p0, p1, p2)) with kind in {"RX","RY","RZ","U3","CNOT","CZ"};
-            q1 = -1 for one-qubit gates; unused parameter slots are -1.  For CNOT,
-            q0 is the control and q1 the target.  U3 parameter slots are (theta, phi, lam).
+gate      : (kind, q0, q1, (p0, p1, p2)) with kind in {"RX","RY","RZ","U3","CNOT","CZ",
+            "CRX","CRY","CRZ","PHASE","CPHASE"}; q1 = -1 for one-qubit gates; unused
+            parameter slots are -1.  For CNOT and the controlled rotations q0 is the
+            control and q1 the target.  U3 parameter slots are (theta, phi, lam).
 term      : (coef, ((qubit, letter), ...)) with letter in "XYZ"; qubits absent from
             the tuple carry the identity.  Duplicate strings are allowed (they add).
 
@@ -43,9 +44,11 @@ import numpy as np
 
 SEED_BASE = 2009_02823
 
-ONE_QUBIT = ("RX", "RY", "RZ", "U3")
+ONE_QUBIT = ("RX", "RY", "RZ", "U3", "PHASE")
 TWO_QUBIT = ("CNOT", "CZ")
-N_PARAMS_OF = {"RX": 1, "RY": 1, "RZ": 1, "U3": 3, "CNOT": 0, "CZ": 0}
+CONTROLLED = ("CRX", "CRY", "CRZ", "CPHASE")  # two-qubit, one parameter; q0 = control
+N_PARAMS_OF = {"RX": 1, "RY": 1, "RZ": 1, "U3": 3, "CNOT": 0, "CZ": 0,
+               "CRX": 1, "CRY": 1, "CRZ": 1, "PHASE": 1, "CPHASE": 1}
 
 
 @dataclass
@@ -81,6 +84,10 @@ class _Builder:
 
     def two(self, kind: str, a: int, b: int) -> None:
         self.gates.append((kind, a, b, (-1, -1, -1)))
+
+    def ctrl(self, kind: str, c: int, t: int) -> None:
+        self.gates.append((kind, c, t, (self.n_params, -1, -1)))
+        self.n_params += 1
 
 
 def cnot_ladder(b: _Builder) -> None:
@@ -218,6 +225,24 @@ def batched(count: int = 512, nmin: int = 12, nmax: int = 20, dmin: int = 4, dma
     return out
 
 
+def crx_ring(n: int, layers: int) -> tuple[list, int]:
+    """Controlled-rotation ansatz in the spirit of the paper's Circuit D: per layer RX(q),
+    RZ(q) on every qubit, then a ring of CRX gates with their own parameters; even layers
+    run q -> q+1, odd layers swap the roles of control and target and shift the ring by
+    one qubit (q+1 -> q+2 read backwards)."""
+    b = _Builder(n)
+    for layer in range(layers):
+        for q in range(n):
+            b.rot("RX", q)
+            b.rot("RZ", q)
+        for q in range(n):
+            c, t = q, (q + 1) % n
+            if layer % 2:
+                c, t = (q + 2) % n, (q + 1) % n
+            b.ctrl("CRX", c, t)
+    return b.gates, b.n_params
+
+
 def random_circuit(rng: np.random.Generator, n: int, n_gates: int, share_params: bool = False,
                    kinds=("RX", "RY", "RZ", "U3", "CNOT", "CZ")) -> tuple[list, int]:
     """A random gate list over all gate kinds and qubit positions (edge-case coverage).
@@ -226,13 +251,15 @@ def random_circuit(rng: np.random.Generator, n: int, n_gates: int, share_params:
     P = 0
     for _ in range(n_gates):
         kind = kinds[int(rng.integers(0, len(kinds)))]
-        if kind in TWO_QUBIT:
+        if kind in TWO_QUBIT or kind in CONTROLLED:
             if n < 2:
                 continue
             a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
-            gates.append((kind, a, b, (-1, -1, -1)))
-            continue
-        q = int(rng.integers(0, n))
+            if kind in TWO_QUBIT:
+                gates.append((kind, a, b, (-1, -1, -1)))
+                continue
+        else:
+            a, b = int(rng.integers(0, n)), -1
         k = N_PARAMS_OF[kind]
         ps = []
         for _j in range(k):
@@ -241,7 +268,7 @@ def random_circuit(rng: np.random.Generator, n: int, n_gates: int, share_params:
             else:
                 ps.append(P)
                 P += 1
-        gates.append((kind, q, -1, tuple(ps) + (-1,) * (3 - k)))
+        gates.append((kind, a, b, tuple(ps) + (-1,) * (3 - k)))
     return gates, P
 
 

@@ -53,7 +53,53 @@ def gate_unitary(gate, theta, n: int, shift=None) -> np.ndarray:
         return lift({q0: P0}, n) + lift({q0: P1, q1: X}, n)
     if kind == "CZ":
         return lift({}, n) - 2 * lift({q0: P1, q1: P1}, n)
+    if kind in GENERATED:
+        return expm(-1j * ang[0] * generator(gate, n))
     raise ValueError(kind)
+
+
+# Gates built as expm(-i t G) from a Hermitian generator G on the full space (App. A's
+# controlled construction is not used here): controlled rotations G = (sigma_t / 2) x
+# |1><1|_c, PHASE G = -|1><1|, CPHASE G = -|11><11|.
+GENERATED = ("CRX", "CRY", "CRZ", "PHASE", "CPHASE")
+
+
+def generator(gate, n: int) -> np.ndarray:
+    kind, q0, q1, _ps = gate
+    if kind in ("CRX", "CRY", "CRZ"):
+        sigma = {"CRX": X, "CRY": Y, "CRZ": Z}[kind]
+        return 0.5 * lift({q0: P1, q1: sigma}, n)
+    if kind == "PHASE":
+        return -lift({q0: P1}, n)
+    if kind == "CPHASE":
+        return -lift({q0: P1, q1: P1}, n)
+    raise ValueError(kind)
+
+
+def gradient_generator(n: int, gates, theta, n_params: int, terms) -> np.ndarray:
+    """dE/dtheta by inserting dU/dt = -i G U in place of each one-parameter gate built
+    from a generator (rotations use G = sigma/2): exact, no shift rule involved."""
+    h = hamiltonian(terms, n)
+    psi = state(n, gates, theta)
+    g = np.zeros(n_params)
+    gens = {"RX": X, "RY": Y, "RZ": Z}
+    for i, gate in enumerate(gates):
+        kind, q0, _q1, ps = gate
+        if kind in gens:
+            G = 0.5 * lift({q0: gens[kind]}, n)
+        elif kind in GENERATED:
+            G = generator(gate, n)
+        else:
+            if any(p >= 0 for p in ps):
+                raise ValueError(f"no generator route for {kind}")
+            continue
+        mu = np.zeros(1 << n, dtype=complex)
+        mu[0] = 1
+        for k, gk in enumerate(gates):
+            u = gate_unitary(gk, theta, n)
+            mu = (-1j * G @ u @ mu) if k == i else (u @ mu)
+        g[ps[0]] += 2 * np.real(psi.conj() @ h @ mu)
+    return g
 
 
 def hamiltonian(terms, n: int) -> np.ndarray:

@@ -270,3 +270,99 @@ def test_hermitian_gradient_is_real_and_energy_matches_expectation():
     assert e == pytest.approx(oracle.energy(w.n, w.gates, w.theta, w.terms), abs=1e-14)
     g_ref = D.gradient_shift(w.n, w.gates, w.theta, w.n_params, w.terms)
     assert np.allclose(oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)[1], g_ref, atol=1e-12)
+
+
+# ---------------------------------------------------------------- controlled and phase gates (App. A)
+@pytest.mark.parametrize("t", [0.0, 0.4, 1.7, 3.0, 5.2])
+def test_controlled_rx_closed_form(t):
+    """CRX(t) with the control prepared in |1> (RX(pi)) acts as RX(t) on the target:
+    <Z_t> = cos t, d/dt = -sin t; with the control in |0> nothing happens (E = 1, 0);
+    with the control in |+> (RY(pi/2)) the two branches average: (1 + cos t)/2."""
+    th = np.array([np.pi, t])
+    z_t = [(1.0, ((1, "Z"),))]
+    on = [("RX", 0, -1, (0, -1, -1)), ("CRX", 0, 1, (1, -1, -1))]
+    plus = [("RY", 0, -1, (0, -1, -1)), ("CRX", 0, 1, (1, -1, -1))]
+    off = [("CRX", 0, 1, (0, -1, -1))]
+    assert oracle.energy(2, on, th, z_t) == pytest.approx(math.cos(t), abs=1e-14)
+    assert oracle.energy(2, off, np.array([t]), z_t) == pytest.approx(1.0, abs=1e-14)
+    thp = np.array([np.pi / 2, t])
+    assert oracle.energy(2, plus, thp, z_t) == pytest.approx(0.5 * (1 + math.cos(t)), abs=1e-14)
+    for route in (oracle.gradient_parameter_shift, oracle.gradient_alg2, lambda *a: oracle.gradient_alg1(*a)[1]):
+        assert route(2, on, th, 2, z_t)[1] == pytest.approx(-math.sin(t), abs=1e-13)
+        assert route(2, off, np.array([t]), 1, z_t)[0] == pytest.approx(0.0, abs=1e-13)
+        assert route(2, plus, thp, 2, z_t)[1] == pytest.approx(-0.5 * math.sin(t), abs=1e-13)
+
+
+@pytest.mark.parametrize("t", [0.3, 1.9, 4.0])
+def test_phase_gate_closed_form(t):
+    """PHASE(t) on |+> = RY(pi/2)|0>: Bloch vector (cos t, sin t, 0)."""
+    gates = [("RY", 0, -1, (0, -1, -1)), ("PHASE", 0, -1, (1, -1, -1))]
+    th = np.array([np.pi / 2, t])
+    X, Y = [(1.0, ((0, "X"),))], [(1.0, ((0, "Y"),))]
+    assert oracle.energy(1, gates, th, X) == pytest.approx(math.cos(t), abs=1e-14)
+    assert oracle.energy(1, gates, th, Y) == pytest.approx(math.sin(t), abs=1e-14)
+    for route in (oracle.gradient_parameter_shift, oracle.gradient_alg2, lambda *a: oracle.gradient_alg1(*a)[1]):
+        assert route(1, gates, th, 2, X)[1] == pytest.approx(-math.sin(t), abs=1e-13)
+        assert route(1, gates, th, 2, Y)[1] == pytest.approx(math.cos(t), abs=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["CRX", "CRY", "CRZ", "PHASE", "CPHASE"])
+def test_controlled_gates_vs_expm(kind):
+    """Two-qubit unitary of each new kind (control 0, target 1; PHASE on qubit 0) against
+    expm of its generator on the full space, and the oracle's derivative route (App. A:
+    target derivative, then the control projection) against dU/dt = -i G U."""
+    rng = np.random.default_rng(3)
+    gate = (kind, 0, -1 if kind == "PHASE" else 1, (0, -1, -1))
+    n = 1 if kind == "PHASE" else 2
+    for _ in range(4):
+        t = float(rng.uniform(-7, 7))
+        U = D.gate_unitary(gate, [t], n)
+        cols = np.stack([oracle.apply_gate(np.eye(1 << n, dtype=complex)[:, k], gate, np.array([t]))
+                         for k in range(1 << n)], axis=1)
+        assert np.allclose(cols, U, atol=1e-14)
+        dU = -1j * D.generator(gate, n) @ U
+        # derivative route = Algorithm 2 on a one-gate circuit with H = |k><l| parts
+        for k in range(1 << n):
+            psi = np.eye(1 << n, dtype=complex)[:, k]
+            d = oracle.gate_derivative(kind, 0, [t])
+            out = oracle.apply_matrix_1q(psi, 1 if n == 2 else 0, d)
+            if kind != "PHASE":
+                out = np.where((np.arange(1 << n) & 1) != 0, out, 0)  # project control 0 onto 1
+            assert np.allclose(out, dU[:, k], atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_controlled_circuits_vs_dense(seed):
+    """Random circuits over every gate kind: state and energy against the dense route;
+    the three oracle gradient routes (including the four-term shift rule of the
+    controlled rotations) against the dense generator-insertion gradient and central
+    differences."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 6))
+    kinds = ("RX", "RY", "RZ", "CNOT", "CZ", "CRX", "CRY", "CRZ", "PHASE", "CPHASE")
+    gates, P = W.random_circuit(rng, n, 16, share_params=(seed % 2 == 1), kinds=kinds)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    terms = W.random_paulis(rng, n, 6, min(4, n))
+    psi = oracle.state(n, gates, theta)
+    assert np.allclose(psi, D.state(n, gates, theta), atol=1e-13)
+    e_ref = D.energy(n, gates, theta, terms)
+    assert oracle.energy(n, gates, theta, terms) == pytest.approx(e_ref, abs=1e-13)
+    g_ref = D.gradient_generator(n, gates, theta, P, terms)
+    assert np.allclose(g_ref, D.gradient_fd(n, gates, theta, P, terms), atol=1e-8)
+    e1, g1 = oracle.gradient_alg1(n, gates, theta, P, terms)
+    assert e1 == pytest.approx(e_ref, abs=1e-13)
+    assert np.allclose(g1, g_ref, atol=1e-12)
+    assert np.allclose(oracle.gradient_alg2(n, gates, theta, P, terms), g_ref, atol=1e-12)
+    assert np.allclose(oracle.gradient_parameter_shift(n, gates, theta, P, terms), g_ref, atol=1e-12)
+
+
+def test_two_term_shift_fails_for_controlled_rotation():
+    """The plain two-term rule is not exact for a controlled rotation (frequencies 1/2
+    and 1): a check that the four-term rule is needed, not an accident of the data."""
+    gates = [("U3", 0, -1, (0, 1, 2)), ("U3", 1, -1, (3, 4, 5)), ("CRY", 0, 1, (6, -1, -1))]
+    th = np.array([0.7, 0.4, 1.1, 1.3, 0.2, 2.1, 0.9])
+    terms = [(1.0, ((1, "X"),)), (0.6, ((1, "Z"),)), (0.3, ((0, "Y"), (1, "X")))]
+    g_ref = D.gradient_fd(2, gates, th, 7, terms)
+    two = 0.5 * (D.energy(2, gates, th, terms, (2, 0, np.pi / 2)) - D.energy(2, gates, th, terms, (2, 0, -np.pi / 2)))
+    assert abs(two - g_ref[6]) > 1e-3
+    assert oracle.gradient_parameter_shift(2, gates, th, 7, terms)[6] == pytest.approx(g_ref[6], abs=1e-9)
