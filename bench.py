@@ -285,6 +285,8 @@ def run_ours(args, rank, world, dist):
     extra = {}
     if not args.no_batch:
         extra["batched"] = batched_rate(args, rank, world, dist)
+    if rank == 0 and not args.no_extra:
+        extra["controlled"] = controlled_rate()
     if rank == 0 and not args.no_ps:
         extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
     if rank == 0 and not args.no_cpu:
@@ -347,6 +349,50 @@ def batched_rate(args, rank=0, world=1, dist=None):
                          "candidates": tune["candidates"], "default_ms": round(tune["default_ms"], 3),
                          "best_ms": round(tune["best_ms"], 3)},
             "tasks": info["tasks"], "grid": info["grid"], "launches_per_batch": 2}
+
+
+def workload_rate(w, dtype="c64", steps=3):
+    """Gradients/s of one more workload through the same device entry point (CUDA events
+    on a dedicated stream, one warm-up), with its per-family device times."""
+    import torch
+
+    from paper_2009_02823_gb300 import Circuit
+    stream = torch.cuda.Stream()
+    circ = Circuit(w.n, w.gates, w.n_params, dtype, stream=stream)
+    circ.set_hamiltonian(w.terms)
+    th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    circ.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        circ.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    circ.set_profiling(True)
+    circ.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    stats = circ.kernel_stats()
+    plan = circ.plan()
+    circ.close()
+    return {"workload": w.name, "n_qubits": w.n, "n_params": w.n_params, "n_gates": w.n_gates,
+            "dtype": dtype, "ms_per_gradient": round(ms, 3), "gradients_per_s": round(1e3 / ms, 4),
+            "family_ms": {f: round(v[1], 3) for f, v in stats.items() if v[1] > 0.01},
+            "passes": {"forward": plan["forward_passes"], "hamiltonian": plan["hamiltonian_passes"],
+                       "reverse": plan["reverse_passes"]}}
+
+
+def controlled_rate():
+    """Controlled-rotation ansatz (RX, RZ layers + CRX rings, App. A's controlled gates):
+    n=30, 6 layers, P=540, TFIM."""
+    from paper_2009_02823_gb300 import workloads as W
+    gates, P = W.crx_ring(30, 6)
+    rng = np.random.default_rng(W.SEED_BASE + 6)
+    w = W.Workload("crx_ring_n30_L6_tfim", 30, gates, P, W.draw_theta(rng, P), W.tfim(30, 1.0))
+    return workload_rate(w)
 
 
 def param_shift_baseline(args, circ, w, theta_h, adjoint_rate):
@@ -485,6 +531,7 @@ def main():
     ap.add_argument("--no-ps", action="store_true", help="skip the GPU parameter-shift baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch figure")
     ap.add_argument("--ps-evals", type=int, default=16)
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra-workload figures")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

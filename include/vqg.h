@@ -19,6 +19,10 @@
  *   U3(t, f, l) = [[cos t/2, -e^{il} sin t/2], [e^{if} sin t/2, e^{i(f+l)} cos t/2]],
  *                 parameter slots (t, f, l) in that order
  *   CNOT(q0 -> q1): flips q1 where q0 = 1.   CZ(q0, q1): -1 where both are 1.
+ *   CRX/CRY/CRZ(q0 -> q1, t): R_sigma(t) on q1 where q0 = 1 (App. A's C_c[U]; the
+ *                 derivative is projected onto q0 = 1).
+ *   PHASE(q0, t) = diag(1, e^{it}) (App. A; derivative i e^{it}|1><1|).
+ *   CPHASE(q0, q1, t): e^{it} where both are 1 (= PHASE on q1 controlled by q0).
  *   Pauli term (x_mask, z_mask, coef): coef * i^{popcount(x & z)} X^x Z^z, i.e. the
  *   tensor product with X where only the x bit is set, Z where only the z bit is set,
  *   Y where both are set.
@@ -55,7 +59,8 @@ typedef enum vqg_status {
 } vqg_status;
 
 typedef enum vqg_gate_kind {
-    VQG_RX = 0, VQG_RY = 1, VQG_RZ = 2, VQG_U3 = 3, VQG_CNOT = 4, VQG_CZ = 5
+    VQG_RX = 0, VQG_RY = 1, VQG_RZ = 2, VQG_U3 = 3, VQG_CNOT = 4, VQG_CZ = 5,
+    VQG_CRX = 6, VQG_CRY = 7, VQG_CRZ = 8, VQG_PHASE = 9, VQG_CPHASE = 10
 } vqg_gate_kind;
 
 typedef enum vqg_dtype {
@@ -63,8 +68,10 @@ typedef enum vqg_dtype {
     VQG_C128 = 1  /* complex128 amplitudes and arithmetic                            */
 } vqg_dtype;
 
-/* One gate.  q1 = -1 for one-qubit gates.  param[j] is the parameter index of slot j
- * (RX/RY/RZ use slot 0, U3 slots 0..2); unused slots are ignored (use -1). */
+/* One gate.  q1 = -1 for one-qubit gates (RX, RY, RZ, U3, PHASE); for CNOT and the
+ * controlled kinds q0 is the control and q1 the target.  param[j] is the parameter
+ * index of slot j (every parameterised kind uses slot 0, U3 slots 0..2); unused slots
+ * are ignored (use -1). */
 typedef struct vqg_gate {
     int32_t kind;
     int32_t q0;
@@ -133,7 +140,9 @@ int vqg_energy_and_gradient_device(vqg_circuit *c, const double *theta_dev, doub
 /* Faithful O(G^2) baseline on the GPU: per-occurrence parameter shift,
  * g_p += [E(theta_o + pi/2) - E(theta_o - pi/2)] / 2 over every parameter slot o of
  * gate occurrences [first_gate, last_gate) (last_gate < 0: all), each evaluation a
- * full forward sweep plus expectation (Sec. 1, Sec. 3).  grad: host, n_params doubles,
+ * full forward sweep plus expectation (Sec. 1, Sec. 3).  Controlled rotations use the
+ * exact four-term rule a1 [E(+pi/2) - E(-pi/2)] + a2 [E(+3pi/2) - E(-3pi/2)],
+ * a1 = (sqrt2 + 1)/(4 sqrt2), a2 = -(sqrt2 - 1)/(4 sqrt2).  grad: host, n_params doubles,
  * overwritten (entries of parameters outside the range are 0).  Blocks until done. */
 int vqg_gradient_parameter_shift(vqg_circuit *c, const double *theta, int first_gate,
                                  int last_gate, double *grad);

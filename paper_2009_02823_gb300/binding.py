@@ -21,7 +21,8 @@ _lib = None
 VQG_OK = 0
 STATUS = {0: "VQG_OK", -1: "VQG_ERR_INVALID", -2: "VQG_ERR_OOM", -3: "VQG_ERR_CUDA",
           -4: "VQG_ERR_TIMEOUT", -5: "VQG_ERR_UNSUPPORTED", -6: "VQG_ERR_STATE"}
-KIND = {"RX": 0, "RY": 1, "RZ": 2, "U3": 3, "CNOT": 4, "CZ": 5}
+KIND = {"RX": 0, "RY": 1, "RZ": 2, "U3": 3, "CNOT": 4, "CZ": 5,
+        "CRX": 6, "CRY": 7, "CRZ": 8, "PHASE": 9, "CPHASE": 10}
 DTYPE = {"c64": 0, "complex64": 0, "c128": 1, "complex128": 1}
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "vqg.h")

@@ -385,7 +385,7 @@ int vqg_batch::build() {
         // occurrences (App. B.2 chain-rule sum), per circuit
         std::vector<std::vector<Occurrence>> by(bc.P);
         for (int i = 0; i < (int)bc.gates.size(); ++i) {
-            const int k = bc.gates[i].kind == VQG_U3 ? 3 : (bc.gates[i].kind <= VQG_RZ ? 1 : 0);
+            const int k = params_of(bc.gates[i].kind);
             for (int j = 0; j < k; ++j) by[bc.gates[i].param[j]].push_back({i, j});
         }
         C.occ_ptr0 = (int)occ_ptr.size();

@@ -161,8 +161,8 @@ int Circuit::ensure_partials() {
 }
 
 // ------------------------------------------------------------------ create / destroy
-static bool is_1q(int k) { return k >= VQG_RX && k <= VQG_U3; }
-static int nparams_of(int k) { return k == VQG_U3 ? 3 : (is_1q(k) ? 1 : 0); }
+static bool is_1q(int k) { return (k >= VQG_RX && k <= VQG_U3) || k == VQG_PHASE; }
+static int nparams_of(int k) { return params_of(k); }
 
 int vqg::vqg_validate_circuit(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype) {
     if (n_qubits < 1 || n_qubits > 34) return set_error(VQG_ERR_INVALID, "n_qubits=%d outside 1..34", n_qubits);
@@ -171,7 +171,7 @@ int vqg::vqg_validate_circuit(int n_qubits, const vqg_gate *gates, int n_gates, 
     if (dtype != VQG_C64 && dtype != VQG_C128) return set_error(VQG_ERR_INVALID, "dtype=%d", dtype);
     for (int i = 0; i < n_gates; ++i) {
         const vqg_gate &g = gates[i];
-        if (g.kind < VQG_RX || g.kind > VQG_CZ) return set_error(VQG_ERR_INVALID, "gate %d: kind %d", i, g.kind);
+        if (g.kind < VQG_RX || g.kind > VQG_CPHASE) return set_error(VQG_ERR_INVALID, "gate %d: kind %d", i, g.kind);
         if (g.q0 < 0 || g.q0 >= n_qubits) return set_error(VQG_ERR_INVALID, "gate %d: qubit %d out of range", i, g.q0);
         if (!is_1q(g.kind)) {
             if (g.q1 < 0 || g.q1 >= n_qubits) return set_error(VQG_ERR_INVALID, "gate %d: qubit %d out of range", i, g.q1);
@@ -580,21 +580,35 @@ extern "C" int vqg_gradient_parameter_shift(vqg_circuit *c, const double *theta,
     if ((!theta && P > 0) || (!grad && P > 0)) return set_error(VQG_ERR_INVALID, "null pointer");
     if (last_gate < 0 || last_gate > G) last_gate = G;
     if (first_gate < 0 || first_gate > last_gate) return set_error(VQG_ERR_INVALID, "bad gate range");
-    std::vector<std::pair<int, int>> occs;
+    // Shift rules: E as a function of one occurrence's angle has the frequencies of its
+    // generator's eigenvalue differences.  Rotations, U3 slots and phase gates: {1}, so
+    // dE/dt = [E(t + pi/2) - E(t - pi/2)] / 2.  Controlled rotations ((sigma/2) x
+    // |1><1|): {1/2, 1}, so dE/dt = a1 [E(t + pi/2) - E(t - pi/2)] + a2 [E(t + 3pi/2) -
+    // E(t - 3pi/2)] with a1 + a2 = 1/(2 sqrt 2), a1 - a2 = 1/2 (solving the two
+    // frequencies' equations).
+    struct Shift { int gate, slot, e0, n_e; };
+    std::vector<Shift> occs;
+    int n_e = 0;
     for (int i = first_gate; i < last_gate; ++i)
-        for (int j = 0; j < nparams_of(cc->gates[i].kind); ++j) occs.push_back({i, j});
+        for (int j = 0; j < nparams_of(cc->gates[i].kind); ++j) {
+            const int k = cc->gates[i].kind;
+            const int ne = (k >= VQG_CRX && k <= VQG_CRZ) ? 4 : 2;
+            occs.push_back({i, j, n_e, ne});
+            n_e += ne;
+        }
     double *d_e = nullptr;
-    if ((st = cc->dalloc((void **)&d_e, sizeof(double) * std::max<size_t>(2 * occs.size(), 1)))) return st;
+    if ((st = cc->dalloc((void **)&d_e, sizeof(double) * std::max(n_e, 1)))) return st;
     if (P) {
         std::memcpy(cc->h_pinned, theta, sizeof(double) * P);
         VQG_CUDA(cudaMemcpyAsync(cc->d_theta, cc->h_pinned, sizeof(double) * P, cudaMemcpyHostToDevice, cc->stream));
     }
     const double h = M_PI / 2.0;
     for (size_t k = 0; k < occs.size() && !st; ++k) {
-        st = cc->run_energy(cc->d_theta, d_e + 2 * k, occs[k].first, occs[k].second, +h);
-        if (!st) st = cc->run_energy(cc->d_theta, d_e + 2 * k + 1, occs[k].first, occs[k].second, -h);
+        const Shift &o = occs[k];
+        const double sh[4] = {+h, -h, +3.0 * h, -3.0 * h};
+        for (int x = 0; x < o.n_e && !st; ++x) st = cc->run_energy(cc->d_theta, d_e + o.e0 + x, o.gate, o.slot, sh[x]);
     }
-    std::vector<double> e(2 * occs.size());
+    std::vector<double> e(n_e);
     if (!st && !occs.empty()) {
         cudaError_t ce = cudaMemcpyAsync(e.data(), d_e, sizeof(double) * e.size(), cudaMemcpyDeviceToHost, cc->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(cc->stream);
@@ -605,8 +619,12 @@ extern "C" int vqg_gradient_parameter_shift(vqg_circuit *c, const double *theta,
     cc->dfree(d_e);
     if (st) return st;
     for (int p = 0; p < P; ++p) grad[p] = 0.0;
-    for (size_t k = 0; k < occs.size(); ++k)
-        grad[cc->gates[occs[k].first].param[occs[k].second]] += 0.5 * (e[2 * k] - e[2 * k + 1]);
+    const double r2 = std::sqrt(2.0), a1 = (r2 + 1.0) / (4.0 * r2), a2 = -(r2 - 1.0) / (4.0 * r2);
+    for (const Shift &o : occs) {
+        const double *v = e.data() + o.e0;
+        const double d = o.n_e == 4 ? a1 * (v[0] - v[1]) + a2 * (v[2] - v[3]) : 0.5 * (v[0] - v[1]);
+        grad[cc->gates[o.gate].param[o.slot]] += d;
+    }
     return VQG_OK;
 }
 

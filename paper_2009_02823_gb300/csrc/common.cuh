@@ -94,14 +94,30 @@ VQG_DEV void block_reduce_store(const double (&acc)[NV], double *__restrict__ pa
 }
 
 // Gate kinds (mirror of vqg_gate_kind; the ABI header is C, kernels use these).
-enum : int { K_RX = 0, K_RY = 1, K_RZ = 2, K_U3 = 3, K_CNOT = 4, K_CZ = 5 };
+enum : int {
+    K_RX = 0, K_RY = 1, K_RZ = 2, K_U3 = 3, K_CNOT = 4, K_CZ = 5,
+    K_CRX = 6, K_CRY = 7, K_CRZ = 8, K_PHASE = 9, K_CPHASE = 10
+};
+
+// Controlled kinds with a parameter: their 2x2 matrix acts on q1 where q0 is 1.
+__host__ __device__ constexpr bool is_controlled_param(int kind) {
+    return (kind >= K_CRX && kind <= K_CRZ) || kind == K_CPHASE;
+}
+// Kinds with a parameter-dependent 2x2 matrix in the gate table.
+__host__ __device__ constexpr bool has_matrix(int kind) { return kind <= K_U3 || kind >= K_CRX; }
+// Parameters of a kind (parameter slots used).
+__host__ __device__ constexpr int params_of(int kind) {
+    return kind == K_U3 ? 3 : (has_matrix(kind) ? 1 : 0);
+}
 
 // Number of reduction values a gate contributes in the reverse sweep:
-// rotations reduce Im<lambda|sigma|phi> (1 value); a general one-qubit gate reduces
-// the four complex sums o_rc = sum conj(lambda_r) phi_c (8 values) that its
-// derivative matrices are contracted with afterwards; entanglers reduce nothing.
+// rotations (controlled or not) reduce Im<lambda|P sigma|phi> and phase gates
+// -2 Im<lambda|P|1><1|phi> (1 value; P projects onto control = 1, App. A); a general
+// one-qubit gate reduces the four complex sums o_rc = sum conj(lambda_r) phi_c
+// (8 values) that its derivative matrices are contracted with afterwards; entanglers
+// reduce nothing.
 __host__ __device__ constexpr int reduce_values_of(int kind) {
-    return kind == K_U3 ? 8 : (kind <= K_RZ ? 1 : 0);
+    return kind == K_U3 ? 8 : (has_matrix(kind) ? 1 : 0);
 }
 
 // One Pauli term of an x-group: w = coef * i^{popcount(x & z)}.

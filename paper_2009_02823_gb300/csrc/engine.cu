@@ -50,17 +50,24 @@ struct QUse {
     bool diag;
 };
 
+// Qubit uses of a gate: a "diagonal" use (RZ, CZ, a control) commutes with every other
+// diagonal use of that qubit; a non-diagonal use (a target) must sit in registers.
+// PHASE and the targets of CRZ / CPHASE are diagonal too but are planned as targets
+// (conservative: fewer reorderings, never a wrong one).
 static int uses_of(const vqg_gate &g, QUse *u) {
     switch (g.kind) {
-    case VQG_RX: case VQG_RY: case VQG_U3: u[0] = {g.q0, false}; return 1;
+    case VQG_RX: case VQG_RY: case VQG_U3: case VQG_PHASE: u[0] = {g.q0, false}; return 1;
     case VQG_RZ: u[0] = {g.q0, true}; return 1;
     case VQG_CZ: u[0] = {g.q0, true}; u[1] = {g.q1, true}; return 2;
-    case VQG_CNOT: u[0] = {g.q0, true}; u[1] = {g.q1, false}; return 2;
+    case VQG_CNOT: case VQG_CRX: case VQG_CRY: case VQG_CRZ: case VQG_CPHASE:
+        u[0] = {g.q0, true}; u[1] = {g.q1, false}; return 2;
     default: return 0;
     }
 }
 
-static int red_values(int kind) { return kind == VQG_U3 ? 8 : (kind <= VQG_RZ ? 1 : 0); }
+static bool has_control(int kind) { return kind == VQG_CNOT || is_controlled_param(kind); }
+
+static int red_values(int kind) { return reduce_values_of(kind); }
 
 // One greedy sweep over `order` with non-diagonal set `inS` (indexed by qubit).
 // Applied gates go to `applied` (in order), the rest to `left`.  `cap_ops` /
@@ -229,8 +236,8 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             } else {
                 StageItem it;
                 it.diag = false;
-                it.nd = 1ull << (g.kind == VQG_CNOT ? g.q1 : g.q0);
-                it.dq = g.kind == VQG_CNOT ? 1ull << g.q0 : 0ull;
+                it.nd = 1ull << (has_control(g.kind) ? g.q1 : g.q0);
+                it.dq = has_control(g.kind) ? 1ull << g.q0 : 0ull;
                 it.gates.push_back(i);
                 size_t pos = out.size();
                 while (pos > 0 && out[pos - 1].diag && !(out[pos - 1].dq & it.nd)) --pos;
@@ -253,14 +260,20 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                 case VQG_RY: op.type = OP_RY; op.k = (int8_t)regbit(g.q0); break;
                 case VQG_RX: op.type = OP_RX; op.k = (int8_t)regbit(g.q0); break;
                 case VQG_U3: op.type = OP_U3; op.k = (int8_t)regbit(g.q0); break;
-                case VQG_CNOT: {
+                case VQG_CNOT:
+                case VQG_CRX:
+                case VQG_CRY:
+                case VQG_CRZ:
+                case VQG_CPHASE: {
                     const int kc = regbit(g.q0);
-                    op.type = OP_CNOT;
+                    op.type = g.kind == VQG_CNOT ? OP_CNOT : g.kind == VQG_CRX ? OP_CRX : g.kind == VQG_CRY ? OP_CRY
+                            : g.kind == VQG_CRZ ? OP_CRZ : OP_PH;
                     op.k = (int8_t)regbit(g.q1);
                     op.cq = -1;
                     if (kc >= 0) op.rm0 = 1u << kc; else op.cq = (int8_t)g.q0;
                     break;
                 }
+                case VQG_PHASE: op.type = OP_PH; op.k = (int8_t)regbit(g.q0); op.cq = -1; break;
                 default: break;
                 }
                 if (reverse) {
@@ -398,11 +411,16 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                 }
                 for (int o = st.op0; o < st.op0 + st.n_op; ++o) {
                     const FOp &op = pl.ops[o];
-                    if (op.type < OP_RY || op.type > OP_DIAG) return fail("op type", o, op.type);
+                    if (op.type < OP_RY || op.type > OP_LAST) return fail("op type", o, op.type);
                     if (op.type != OP_DIAG && (op.k < 0 || op.k >= R)) return fail("register bit", o, op.k);
                     if (op.rm0 >> R) return fail("register mask", o, (int)op.rm0);
-                    if (op.type == OP_CNOT && op.rm0 == (1u << op.k)) return fail("control = target", o, op.k);
+                    const bool ctl_op = op.type == OP_CNOT || op.type >= OP_CRX;
+                    if (ctl_op && op.rm0 == (1u << op.k)) return fail("control = target", o, op.k);
                     if (op.type == OP_CNOT && !op.rm0 && (op.cq < 0 || op.cq >= n)) return fail("control qubit", o, op.cq);
+                    if (op.type >= OP_CRX && op.type <= OP_CRZ && !op.rm0 && (op.cq < 0 || op.cq >= n))
+                        return fail("control qubit", o, op.cq);
+                    if (op.type == OP_PH && !op.rm0 && (op.cq < -1 || op.cq >= n)) return fail("control qubit", o, op.cq);
+                    if (!ctl_op && (op.rm0 || op.cq != -1)) return fail("stray control", o, op.cq);
                     if (op.type != OP_DIAG && (op.gate < 0)) return fail("gate index", o, op.gate);
                     if (dir && op.lslot >= 0) {
                         const int nv = op.type == OP_U3 ? 8 : 1;
@@ -578,20 +596,22 @@ int Circuit::build_plan() {
         }
         pl->grid_fwd = occupancy_grid(num_sms, 2, pl->n_tiles);
         int st;
-        auto up = [&](void **d, const void *h, size_t bytes) -> int {
-            int s2 = dalloc(d, bytes);
+        // allocate at least one element (a valid pointer for empty tables), copy what exists
+        auto up = [&](void **d, const auto &vec) -> int {
+            const size_t elem = sizeof(vec[0]);
+            int s2 = dalloc(d, elem * std::max<size_t>(vec.size(), 1));
             if (s2) return s2;
-            if (bytes && cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            if (!vec.empty() && cudaMemcpy(*d, vec.data(), elem * vec.size(), cudaMemcpyHostToDevice) != cudaSuccess)
                 return set_error(VQG_ERR_CUDA, "plan upload failed");
             return VQG_OK;
         };
         plan = pl;
-        if ((st = up((void **)&pl->d_passes, pl->passes.data(), sizeof(FPass) * pl->passes.size()))) return st;
-        if ((st = up((void **)&pl->d_stages, pl->stages.data(), sizeof(FStage) * pl->stages.size()))) return st;
-        if ((st = up((void **)&pl->d_ops, pl->ops.data(), sizeof(FOp) * std::max<size_t>(pl->ops.size(), 1)))) return st;
-        if ((st = up((void **)&pl->d_slot_map, pl->slot_map.data(), sizeof(int) * std::max<size_t>(pl->slot_map.size(), 1)))) return st;
-        if ((st = up((void **)&pl->d_diags, pl->diags.data(), sizeof(FDiag) * std::max<size_t>(pl->diags.size(), 1)))) return st;
-        if ((st = up((void **)&pl->d_items, pl->items.data(), sizeof(FDItem) * std::max<size_t>(pl->items.size(), 1)))) return st;
+        if ((st = up((void **)&pl->d_passes, pl->passes))) return st;
+        if ((st = up((void **)&pl->d_stages, pl->stages))) return st;
+        if ((st = up((void **)&pl->d_ops, pl->ops))) return st;
+        if ((st = up((void **)&pl->d_slot_map, pl->slot_map))) return st;
+        if ((st = up((void **)&pl->d_diags, pl->diags))) return st;
+        if ((st = up((void **)&pl->d_items, pl->items))) return st;
         if (!dbl && (st = dalloc((void **)&pl->d_mats_f, sizeof(float) * 8 * std::max(G, 1)))) return st;
         plan_ok = true;
     }

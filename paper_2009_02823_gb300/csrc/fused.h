@@ -49,7 +49,15 @@ enum FOpType : int16_t {
     OP_RX = 1,    // RX on register bit k (complex matrix)
     OP_U3 = 2,    // general 2x2 on register bit k (three parameters)
     OP_CNOT = 3,  // swap on target register bit k where the control is set
-    OP_DIAG = 4   // a block of commuting diagonal gates (RZ, CZ): table x per-thread factor
+    OP_DIAG = 4,  // a block of commuting diagonal gates (RZ, CZ): table x per-thread factor
+    // 2x2 matrix on target register bit k where the control is set (rm0: control register
+    // mask; else cq: control qubit, -1 = no control); they differ in the reverse
+    // reduction: Im<l|P X|phi>, Im<l|P Y|phi>, Im<l|P Z|phi>, -2 Im<l|P |1><1| phi>
+    OP_CRX = 5,
+    OP_CRY = 6,
+    OP_CRZ = 7,
+    OP_PH = 8,    // phase gate (uncontrolled: PHASE; controlled: CPHASE)
+    OP_LAST = OP_PH
 };
 
 // Items of a diagonal block.  RZ items come first (they carry reverse reductions).

@@ -103,6 +103,23 @@ VQG_DEV void op_cnot(amp_t<T> (&a)[NA], uint32_t rc, bool thr_c) {
     }
 }
 
+// Controlled 2x2 (controlled rotations, phase gates): u on the pair where the control
+// is set -- register mask rc, else the thread-level flag thr_c.
+template <int KB, int NA, typename T>
+VQG_DEV void op_cgen(amp_t<T> (&a)[NA], const Mat2<T> &u, uint32_t rc, bool thr_c) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const bool c = rc ? ((j & rc) != 0) : thr_c;
+        if (c) apply2<T>(u, a[j], a[j | (1 << KB)]);
+    }
+}
+
+// Control flag of an op whose control is not a register bit (cq < 0: no control).
+VQG_DEV bool thread_control(const FOp &op, uint64_t gb) {
+    return op.rm0 ? false : (op.cq < 0 ? true : ((gb >> op.cq) & 1ull) != 0);
+}
+
 template <typename T> VQG_DEV Mat2<T> mat_of(const amp_t<T> *__restrict__ m) {
     Mat2<T> u;
 #pragma unroll
@@ -286,6 +303,15 @@ VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64
         with_k<R>(op.k, [&](auto kb) { op_cnot<decltype(kb)::value, NA, T>(a, op.rm0, c); });
         break;
     }
+    case OP_CRX:
+    case OP_CRY:
+    case OP_CRZ:
+    case OP_PH: {
+        const Mat2<T> u = mat_of<T>(m);
+        const bool c = thread_control(op, gb);
+        with_k<R>(op.k, [&](auto kb) { op_cgen<decltype(kb)::value, NA, T>(a, u, op.rm0, c); });
+        break;
+    }
     case OP_DIAG: {
         amp_t<T> tau;
         uint32_t c;
@@ -351,6 +377,30 @@ VQG_DEV void rev_u3(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud, T (
         apply2<T>(ud, a[j], a[j1]);
         apply2<T>(ud, l[j], l[j1]);
     }
+}
+
+// Controlled 2x2 in reverse (App. A: the derivative of C_c[U] is dU projected onto
+// control = 1, so only pairs with the control set contribute).  G selects the value:
+// 0: Im<l|X|phi>, 1: Im<l|Y|phi>, 2: Im<l|Z|phi> (controlled rotations, as for RX/RY/RZ);
+// 3: -2 Im(conj(l1) phi1) (phase gates: dP/dt = i e^{it}|1><1|).
+template <int G, int KB, int NA, typename T>
+VQG_DEV T rev_cgen(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud, uint32_t rc, bool thr_c) {
+    T v = 0;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const bool c = rc ? ((j & rc) != 0) : thr_c;
+        if (!c) continue;
+        const int j1 = j | (1 << KB);
+        const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+        if constexpr (G == 0) v += (l0.x * a1.y - l0.y * a1.x) + (l1.x * a0.y - l1.y * a0.x);
+        else if constexpr (G == 1) v += (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
+        else if constexpr (G == 2) v += (l0.x * a0.y - l0.y * a0.x) - (l1.x * a1.y - l1.y * a1.x);
+        else v += (T)-2 * (l1.x * a1.y - l1.y * a1.x);
+        apply2<T>(ud, a[j], a[j1]);
+        apply2<T>(ud, l[j], l[j1]);
+    }
+    return v;
 }
 
 // Reverse diagonal block.  Every RZ of the block gets Im <lambda| Z_q |phi> from the
@@ -658,6 +708,22 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
                     op_cnot<decltype(kb)::value, NA, T>(a, op.rm0, c);
                     op_cnot<decltype(kb)::value, NA, T>(l, op.rm0, c);
                 });
+                break;
+            }
+            case OP_CRX:
+            case OP_CRY:
+            case OP_CRZ:
+            case OP_PH: {
+                const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+                const bool c = thread_control(op, gb);
+                with_k<R>(op.k, [&](auto kb) {
+                    constexpr int KB = decltype(kb)::value;
+                    if (op.type == OP_CRX) v1 = rev_cgen<0, KB, NA, T>(a, l, ud, op.rm0, c);
+                    else if (op.type == OP_CRY) v1 = rev_cgen<1, KB, NA, T>(a, l, ud, op.rm0, c);
+                    else if (op.type == OP_CRZ) v1 = rev_cgen<2, KB, NA, T>(a, l, ud, op.rm0, c);
+                    else v1 = rev_cgen<3, KB, NA, T>(a, l, ud, op.rm0, c);
+                });
+                red1 = true;
                 break;
             }
             case OP_DIAG:

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_1q(amp_t<T> *__restrict__ psi,
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             if (base + k * stride >= units) continue;
-            if (KIND == K_RZ) {
+            if (KIND == K_RZ || KIND == K_PHASE) {  // diagonal
                 a0[k] = cmul<T>(u.m[0], a0[k]);
                 a1[k] = cmul<T>(u.m[3], a1[k]);
             } else if (KIND == K_RY) {  // real matrix
@@ -67,6 +67,24 @@ __global__ void __launch_bounds__(kThreads) k_fwd_cnot(amp_t<T> *__restrict__ ps
     }
 }
 
+// C_c[U]: the gate's 2x2 matrix on t where c = 1 (controlled rotations and the
+// controlled phase gate, App. A).  units = 2^{n-2}.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fwd_c1q(amp_t<T> *__restrict__ psi, int c, int t,
+                                                      const double *__restrict__ mat, uint64_t units) {
+    const Mat2<T> u = load_mat<T>(mat);
+    const int lo = c < t ? c : t, hi = c < t ? t : c;
+    const uint64_t cb = 1ull << c, tb = 1ull << t;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < units; v += stride) {
+        const uint64_t j = insert00(v, lo, hi) | cb;
+        amp_t<T> a0 = psi[j], a1 = psi[j | tb];
+        apply2<T>(u, a0, a1);
+        psi[j] = a0;
+        psi[j | tb] = a1;
+    }
+}
+
 // CZ(a, b): negate amplitudes with both bits set.  units = 2^{n-2}.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fwd_cz(amp_t<T> *__restrict__ psi, int a, int b,
@@ -93,6 +111,11 @@ static void fwd_gate_t(void *psi, int n, int kind, int q0, int q1, const double 
     case K_U3: k_fwd_1q<T, K_U3><<<nb, kThreads, 0, s>>>(p, q0, mat, pairs); break;
     case K_CNOT: k_fwd_cnot<T><<<nb, kThreads, 0, s>>>(p, q0, q1, pairs >> 1); break;
     case K_CZ: k_fwd_cz<T><<<nb, kThreads, 0, s>>>(p, q0, q1, pairs >> 1); break;
+    case K_PHASE: k_fwd_1q<T, K_PHASE><<<nb, kThreads, 0, s>>>(p, q0, mat, pairs); break;
+    case K_CRX:
+    case K_CRY:
+    case K_CRZ:
+    case K_CPHASE: k_fwd_c1q<T><<<nb, kThreads, 0, s>>>(p, q0, q1, mat, pairs >> 1); break;
     default: break;
     }
 }
@@ -115,12 +138,15 @@ template <typename T, int KIND> struct NV { static constexpr int value = reduce_
 template <typename T, int KIND>
 VQG_DEV void pair_values(const amp_t<T> &a0, const amp_t<T> &a1, const amp_t<T> &l0,
                          const amp_t<T> &l1, T *v) {
-    if (KIND == K_RX) {  // Im(conj(l0) a1 + conj(l1) a0)
+    if (KIND == K_RX || KIND == K_CRX) {  // Im(conj(l0) a1 + conj(l1) a0)
         v[0] = (l0.x * a1.y - l0.y * a1.x) + (l1.x * a0.y - l1.y * a0.x);
-    } else if (KIND == K_RY) {  // Re(conj(l1) a0) - Re(conj(l0) a1)
+    } else if (KIND == K_RY || KIND == K_CRY) {  // Re(conj(l1) a0) - Re(conj(l0) a1)
         v[0] = (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
-    } else if (KIND == K_RZ) {  // Im(conj(l0) a0) - Im(conj(l1) a1)
+    } else if (KIND == K_RZ || KIND == K_CRZ) {  // Im(conj(l0) a0) - Im(conj(l1) a1)
         v[0] = (l0.x * a0.y - l0.y * a0.x) - (l1.x * a1.y - l1.y * a1.x);
+    } else if (KIND == K_PHASE || KIND == K_CPHASE) {
+        // dP/dt = i e^{it}|1><1| (App. A): 2 Re<lambda| i |1><1| phi_{i+1}> = -2 Im(conj(l1) a1)
+        v[0] = (T)-2 * (l1.x * a1.y - l1.y * a1.x);
     } else if (KIND == K_U3) {  // o_rc = conj(l_r) a_c, order 00, 01, 10, 11
         const amp_t<T> o00 = cconjmul<T>(l0, a0), o01 = cconjmul<T>(l0, a1);
         const amp_t<T> o10 = cconjmul<T>(l1, a0), o11 = cconjmul<T>(l1, a1);
@@ -129,7 +155,9 @@ VQG_DEV void pair_values(const amp_t<T> &a0, const amp_t<T> &a1, const amp_t<T> 
     }
 }
 
-// Pairs on qubit q (for CNOT/CZ: on the target q1; q0 is the control / other qubit).
+// Pairs on qubit q (for CNOT/CZ and the controlled kinds: on the target q1; q0 is the
+// control / other qubit).  A controlled kind reduces and un-applies only the pairs whose
+// control is 1: its derivative is projected onto control = 1 (App. A).
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kThreads)
     k_adj(const amp_t<T> *__restrict__ phi_src, amp_t<T> *__restrict__ phi_dst,
@@ -137,11 +165,12 @@ __global__ void __launch_bounds__(kThreads)
           double *__restrict__ partials, int nb, int write_phi, int write_lam) {
     constexpr int NVAL = reduce_values_of(KIND);
     constexpr int NVA = NVAL > 0 ? NVAL : 1;
-    const int qp = (KIND == K_CNOT || KIND == K_CZ) ? q1 : q0;
+    constexpr bool CTRL = is_controlled_param(KIND);
+    const int qp = (KIND == K_CNOT || KIND == K_CZ || CTRL) ? q1 : q0;
     const uint64_t bit = 1ull << qp;
     const uint64_t cbit = 1ull << q0;
     Mat2<T> ud;
-    if (KIND <= K_U3) ud = load_mat_dagger<T>(mat);
+    if (has_matrix(KIND)) ud = load_mat_dagger<T>(mat);
     double acc[NVA];
     T run[NVA];
 #pragma unroll
@@ -166,7 +195,8 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             if (base + k * stride >= units) continue;
-            if (NVAL > 0) {
+            const bool active = !CTRL || (j0[k] & cbit) != 0;
+            if (NVAL > 0 && active) {
                 T v[NVA];
                 pair_values<T, KIND>(a0[k], a1[k], l0[k], l1[k], v);
 #pragma unroll
@@ -187,9 +217,14 @@ __global__ void __launch_bounds__(kThreads)
                     a1[k] = mk<T>(-a1[k].x, -a1[k].y);
                     l1[k] = mk<T>(-l1[k].x, -l1[k].y);
                 }
-            } else if (KIND == K_RZ) {
+            } else if (KIND == K_RZ || KIND == K_PHASE) {
                 a0[k] = cmul<T>(ud.m[0], a0[k]); a1[k] = cmul<T>(ud.m[3], a1[k]);
                 l0[k] = cmul<T>(ud.m[0], l0[k]); l1[k] = cmul<T>(ud.m[3], l1[k]);
+            } else if (CTRL) {
+                if (active) {
+                    apply2<T>(ud, a0[k], a1[k]);
+                    apply2<T>(ud, l0[k], l1[k]);
+                }
             } else if (KIND == K_RY) {
                 const T c = ud.m[0].x, s = ud.m[2].x;  // U^dag = [[c, s], [-s, c]]
                 amp_t<T> b0 = mk<T>(c * a0[k].x + ud.m[1].x * a1[k].x, c * a0[k].y + ud.m[1].x * a1[k].y);
@@ -234,6 +269,11 @@ static void adj_gate_t(const void *phi_src, void *phi_dst, void *lam, int n, int
     case K_U3: VQG_ADJ(K_U3); break;
     case K_CNOT: VQG_ADJ(K_CNOT); break;
     case K_CZ: VQG_ADJ(K_CZ); break;
+    case K_CRX: VQG_ADJ(K_CRX); break;
+    case K_CRY: VQG_ADJ(K_CRY); break;
+    case K_CRZ: VQG_ADJ(K_CRZ); break;
+    case K_PHASE: VQG_ADJ(K_PHASE); break;
+    case K_CPHASE: VQG_ADJ(K_CPHASE); break;
     default: break;
     }
 #undef VQG_ADJ

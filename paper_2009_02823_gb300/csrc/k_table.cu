@@ -5,8 +5,9 @@
 
 namespace vqg {
 
-// U_i(theta) for every one-qubit gate, FP64, row-major (re, im) x 4 (App. A gate set):
-//   R_sigma(t) = cos(t/2) I - i sin(t/2) sigma;  U3 per the ABI header.
+// U_i(theta) for every gate with a parameter, FP64, row-major (re, im) x 4 (App. A gate
+// set): R_sigma(t) = cos(t/2) I - i sin(t/2) sigma;  U3 per the ABI header; the phase
+// gate diag(1, e^{it}); controlled kinds store the matrix applied to their target.
 // shift_gate/shift_slot add `shift` to one parameter slot of one occurrence (the
 // per-occurrence parameter-shift baseline).
 __global__ void k_build_mats(const double *__restrict__ theta, const DevGate *__restrict__ gates,
@@ -16,7 +17,7 @@ __global__ void k_build_mats(const double *__restrict__ theta, const DevGate *__
     if (i >= G) return;
     DevGate g = gates[i];
     double a[3] = {0.0, 0.0, 0.0};
-    if (g.kind <= K_U3) {
+    if (has_matrix(g.kind)) {
         a[0] = theta[g.p0];
         if (g.kind == K_U3) {
             a[1] = theta[g.p1];
@@ -28,7 +29,9 @@ __global__ void k_build_mats(const double *__restrict__ theta, const DevGate *__
     sincos(0.5 * a[0], &s, &c);
     double *m = mats + 8 * (size_t)i;
     double r[8] = {1, 0, 0, 0, 0, 0, 1, 0};
-    switch (g.kind) {
+    int kind = g.kind;
+    if (kind >= K_CRX && kind <= K_CRZ) kind -= K_CRX - K_RX;  // target matrix of C[R_sigma]
+    switch (kind) {
     case K_RX:  // [[c, -i s], [-i s, c]]
         r[0] = c; r[1] = 0; r[2] = 0; r[3] = -s; r[4] = 0; r[5] = -s; r[6] = c; r[7] = 0;
         break;
@@ -47,6 +50,13 @@ __global__ void k_build_mats(const double *__restrict__ theta, const DevGate *__
         r[2] = -cl * s; r[3] = -sl * s;
         r[4] = cf * s; r[5] = sf * s;
         r[6] = cfl * c; r[7] = sfl * c;
+        break;
+    }
+    case K_PHASE:
+    case K_CPHASE: {  // diag(1, e^{it})
+        double st, ct;
+        sincos(a[0], &st, &ct);
+        r[0] = 1; r[1] = 0; r[2] = 0; r[3] = 0; r[4] = 0; r[5] = 0; r[6] = ct; r[7] = st;
         break;
     }
     default:

@@ -39,7 +39,12 @@ def _create(n, gates, P, dtype=0):
     (3, [("CZ", 0, 7, (-1, -1, -1))], 0, 0),
     (3, [("RY", 0, -1, (2, -1, -1))], 2, 0),              # parameter index >= P
     (3, [("U3", 0, -1, (0, 1, -1))], 2, 0),               # U3 needs three slots
-    (3, [(9, 0, -1, (0, -1, -1))], 1, 0),                 # unknown kind
+    (3, [(11, 0, -1, (0, -1, -1))], 1, 0),                # unknown kind
+    (3, [(-1, 0, -1, (0, -1, -1))], 1, 0),
+    (3, [("CRX", 2, 2, (0, -1, -1))], 1, 0),              # control == target
+    (3, [("CRY", 0, 3, (0, -1, -1))], 1, 0),              # target >= n
+    (3, [("CPHASE", 0, -1, (0, -1, -1))], 1, 0),          # two-qubit kind without q1
+    (3, [("PHASE", 1, -1, (1, -1, -1))], 1, 0),           # parameter index >= P
     (3, [], 0, 7),                                        # unknown dtype
 ])
 def test_invalid_circuits_rejected(n, gates, P, dtype):

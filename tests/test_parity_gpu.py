@@ -278,3 +278,90 @@ def test_autotune_choice_and_parity(dtype):
     with _circ(w.n, w.gates, w.n_params, dtype, w.terms, tile_qubits=11) as c:
         r3 = c.autotune(w.theta)  # explicit tile: nothing to tune
         assert r3["candidates"] == 0 and c.plan()["tile_qubits"] == 11
+
+
+# ---------------------------------------------------------------- controlled rotations and phase gates (App. A)
+ALL_KINDS = ("RX", "RY", "RZ", "U3", "CNOT", "CZ", "CRX", "CRY", "CRZ", "PHASE", "CPHASE")
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["per_gate", "fused"])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("seed", range(8))
+def test_controlled_random_circuits(seed, dtype, mode):
+    rng = np.random.default_rng(2000 + seed)
+    n = [2, 3, 5, 7, 10, 11, 12, 13][seed]
+    gates, P = W.random_circuit(rng, n, 50 + 5 * n, share_params=(seed % 3 == 0), kinds=ALL_KINDS)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    terms = W.random_paulis(rng, n, 9, min(4, n))
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, dtype, terms, **mode) as c:
+        e, g = c.energy_and_gradient(theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, f"n={n}")
+        assert energy_err(c.energy(theta), e_ref) <= TOL[dtype]  # forward sweep only: psi = U|0>
+        psi = c.get_state()
+        assert np.max(np.abs(psi - oracle.state(n, gates, theta))) <= (1e-12 if dtype == "c128" else 2e-5)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("kind", ["CRX", "CRY", "CRZ", "PHASE", "CPHASE"])
+@pytest.mark.parametrize("n", [6, 11])
+def test_controlled_every_position(kind, dtype, n):
+    """Each new kind on every (control, target) pair (every qubit for PHASE) after a
+    U3 layer, fused (n = 11) and per gate (n = 6): controls on register, thread-level
+    and tile-external bits all occur in the fused case."""
+    rng = np.random.default_rng(17)
+    gates, P = [], 0
+    for q in range(n):
+        gates.append(("U3", q, -1, (P, P + 1, P + 2)))
+        P += 3
+    pairs = [(q, -1) for q in range(n)] if kind == "PHASE" else \
+        [(a, b) for a in range(n) for b in range(n) if a != b]
+    for a, b in pairs:
+        gates.append((kind, a, b, (P, -1, -1)))
+        P += 1
+        if len(gates) % 7 == 0:
+            gates.append(("RY", int(rng.integers(0, n)), -1, (P, -1, -1)))
+            P += 1
+    theta = rng.uniform(0, 2 * np.pi, P)
+    terms = W.random_paulis(rng, n, 12, 4)
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, dtype, terms) as c:
+        e, g = c.energy_and_gradient(theta)
+        assert_parity(dtype, e, g, e_ref, g_ref, f"{kind} n={n}")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("K", [10, 11, 12])
+def test_controlled_fused_tile_sizes(dtype, K):
+    """The controlled-rotation ansatz (Circuit D-like ring) at n = 14 under several tile
+    sizes and both register widths, against the oracle."""
+    n = 14
+    gates, P = W.crx_ring(n, 4)
+    rng = np.random.default_rng(5)
+    theta = rng.uniform(0, 2 * np.pi, P)
+    terms = W.random_paulis(rng, n, 20, 4)
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    regs = ((5, 4), (4, 3)) if dtype == "c64" else ((4, 3), (3, 2))
+    for Rf, Rr in regs:
+        if Rr == 2 and K > 11:
+            continue
+        with _circ(n, gates, P, dtype, terms, tile_qubits=K, fwd_reg_qubits=Rf, rev_reg_qubits=Rr) as c:
+            e, g = c.energy_and_gradient(theta)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"K={K} R={Rf}/{Rr}")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_gpu_parameter_shift_controlled(dtype):
+    """The GPU parameter-shift baseline with the four-term rule of controlled rotations
+    agrees with the oracle's Algorithm-1 gradient (an independent route)."""
+    n = 6
+    gates, P = W.crx_ring(n, 2)
+    gates = gates + [("PHASE", 2, -1, (P, -1, -1)), ("CPHASE", 0, 4, (P + 1, -1, -1)),
+                     ("CRY", 3, 1, (P + 2, -1, -1)), ("CRZ", 5, 0, (P + 3, -1, -1))]
+    P += 4
+    rng = np.random.default_rng(8)
+    theta = rng.uniform(0, 2 * np.pi, P)
+    terms = W.random_paulis(rng, n, 10, 3)
+    _e, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, dtype, terms) as c:
+        assert grad_err(c.gradient_parameter_shift(theta), g_ref) <= TOL[dtype]

@@ -94,3 +94,35 @@ def test_default_tile_table(dtype, kmax):
         info = B.plan_dry_run(n, gates, P, terms, dtype)
         want = 0 if n < 10 else min(kmax, max(10, n - 8))
         assert info["tile_qubits"] == want, n
+
+
+ALL_KINDS = ("RX", "RY", "RZ", "U3", "CNOT", "CZ", "CRX", "CRY", "CRZ", "PHASE", "CPHASE")
+
+
+@pytest.mark.parametrize("K", [10, 11, 12, 13])
+@pytest.mark.parametrize("seed", range(6))
+def test_controlled_gates_plan(seed, K):
+    """Controlled rotations and phase gates (controls anywhere, targets in registers)
+    plan into passes whose every index passes the library's checks, for every register
+    choice the kernels compile."""
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(K, 22))
+    gates, P = W.random_circuit(rng, n, 300, share_params=True, kinds=ALL_KINDS)
+    terms = W.random_paulis(rng, n, 40, 4)
+    for dtype, regs in (("c64", ((5, 4), (4, 3))), ("c128", ((4, 3), (3, 2)))):
+        for Rf, Rr in regs:
+            if (dtype == "c128" and K > 12) or (Rr == 3 and dtype == "c64" and K > 12) or \
+               (Rr == 2 and K > 11):
+                continue
+            info = B.plan_dry_run(n, gates, P, terms, dtype, tile_qubits=K, fwd_reg_qubits=Rf,
+                                  rev_reg_qubits=Rr)
+            assert info["tile_qubits"] == K and info["forward_passes"] >= 1
+
+
+@pytest.mark.parametrize("n", [12, 26, 30])
+def test_crx_ring_plans(n):
+    gates, P = W.crx_ring(n, 6)
+    terms = W.tfim(n, 1.0)
+    for dtype in ("c64", "c128"):
+        info = B.plan_dry_run(n, gates, P, terms, dtype)
+        assert info["forward_passes"] >= 1 and info["forward_passes"] < len(gates)
