@@ -72,6 +72,8 @@ def _load():
             "oracle_gradient_alg1": (None, [i, p, i, p, i, i, p, p, p, p]),
             "oracle_inner_parts": (None, [i, p, p, p]),
             "oracle_openmp_threads": (i, []),
+            "oracle_apply_operator": (None, [i, i, p, p, p, p, p]),
+            "oracle_gradient_alg1_operator": (None, [i, p, i, p, i, i, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -234,3 +236,46 @@ def gradient_alg1(n: int, gates, theta, n_params: int, terms) -> tuple[float, np
     _load().oracle_gradient_alg1(n, _ptr(gt), len(gates), _ptr(th), n_params, len(terms),
                                  _ptr(coef), _ptr(let), _ptr(g), _ptr(e))
     return float(e[0]), g[:n_params]
+
+
+# ---------------------------------------------------------------- non-Hermitian operators (App. B.4)
+def complex_letter_table(terms, n: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Terms with complex coefficients -> (re[T], im[T], letters[T, n])."""
+    re_terms = [(complex(c).real, ops) for c, ops in terms]
+    cr, let = letter_table(re_terms, n)
+    ci = np.zeros_like(cr)
+    for t, (c, _ops) in enumerate(terms):
+        ci[t] = complex(c).imag
+    return cr, ci, let
+
+
+def apply_operator(psi: np.ndarray, terms) -> np.ndarray:
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    n = int(np.log2(psi.size))
+    cr, ci, let = complex_letter_table(terms, n)
+    out = np.zeros_like(psi)
+    _load().oracle_apply_operator(n, len(terms), _ptr(cr), _ptr(ci), _ptr(let), _ptr(psi), _ptr(out))
+    return out
+
+
+def gradient_alg1_operator(n: int, gates, theta, n_params: int, terms) -> tuple[complex, np.ndarray]:
+    """App. B.4: (E, dE/dtheta), both complex, for a non-Hermitian Pauli-sum operator."""
+    gt = gate_table(gates)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.size == 0:
+        th = np.zeros(1)
+    cr, ci, let = complex_letter_table(terms, n)
+    g = np.zeros(2 * max(n_params, 1))
+    e = np.zeros(2)
+    _load().oracle_gradient_alg1_operator(n, _ptr(gt), len(gates), _ptr(th), n_params, len(terms),
+                                          _ptr(cr), _ptr(ci), _ptr(let), _ptr(g), _ptr(e))
+    return complex(e[0], e[1]), (g[0::2] + 1j * g[1::2])[:n_params]
+
+
+def gradient_parameter_shift_operator(n: int, gates, theta, n_params: int, terms) -> np.ndarray:
+    """Faithful route for a non-Hermitian operator A = B + iC (B, C Hermitian: the real
+    and imaginary coefficient parts of a Pauli sum): parameter shift of <B> and <C>."""
+    re_terms = [(complex(c).real, ops) for c, ops in terms]
+    im_terms = [(complex(c).imag, ops) for c, ops in terms]
+    return (gradient_parameter_shift(n, gates, theta, n_params, re_terms)
+            + 1j * gradient_parameter_shift(n, gates, theta, n_params, im_terms))

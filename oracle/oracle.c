@@ -34,7 +34,9 @@
  *   kind 0 RX, 1 RY, 2 RZ, 3 U3, 4 CNOT, 5 CZ, 6 CRX, 7 CRY, 8 CRZ, 9 PHASE, 10 CPHASE;
  *   controlled kinds: q0 = control, q1 = target; unused params are -1.
  * Hamiltonian: n_terms coefficients and an n_terms x n table of letters
- *   (0 = I, 1 = X, 2 = Y, 3 = Z), letters[t * n + q] acting on qubit q.
+ *   (0 = I, 1 = X, 2 = Y, 3 = Z), letters[t * n + q] acting on qubit q.  A non-Hermitian
+ *   operator (App. B.4) has complex coefficients, given as separate real and imaginary
+ *   arrays.
  */
 #include <complex.h>
 #include <math.h>
@@ -437,6 +439,94 @@ void oracle_gradient_alg1(int n, const int32_t *gates, int n_gates, const double
     free(lam);
     free(phi);
     free(mu);
+}
+
+/* ------------------------------------------------- non-Hermitian operators (App. B.4) */
+
+/* out = A psi for A = sum_t (cr_t + i ci_t) (x)_q sigma_{t,q}: each term applied to a copy
+ * of psi letter by letter as plain 2x2 matrices, then accumulated with its complex
+ * coefficient. */
+void oracle_apply_operator(int n, int n_terms, const double *cr, const double *ci,
+                           const uint8_t *letters, const cplx *psi, cplx *out) {
+    const int64_t dim = (int64_t)1 << n;
+    cplx *tmp = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
+    static const cplx PX[4] = {0, 1, 1, 0};
+    static const cplx PZ[4] = {1, 0, 0, -1};
+    cplx PY[4] = {0, -I, I, 0};
+    memset(out, 0, sizeof(cplx) * (size_t)dim);
+    for (int t = 0; t < n_terms; ++t) {
+        memcpy(tmp, psi, sizeof(cplx) * (size_t)dim);
+        for (int q = 0; q < n; ++q) {
+            int l = letters[(int64_t)t * n + q];
+            if (l == 1) oracle_apply_matrix_1q(n, tmp, q, PX);
+            else if (l == 2) oracle_apply_matrix_1q(n, tmp, q, PY);
+            else if (l == 3) oracle_apply_matrix_1q(n, tmp, q, PZ);
+        }
+        const cplx c = cr[t] + I * ci[t];
+        PAR_FOR
+        for (int64_t j = 0; j < dim; ++j) out[j] += c * tmp[j];
+    }
+    free(tmp);
+}
+
+/* Algorithm 1 with App. B.4's change of the step value to <lambda|mu> (complex, no
+ * 2 Re), for the operator with coefficients (cr, ci): g[p] += <lambda_i|mu_i>.
+ * Returns <psi|lambda_G> = <psi|A|psi> through *ex when non-null. */
+static void alg1_complex(int n, const int32_t *gates, int n_gates, const double *theta,
+                         int n_params, int n_terms, const double *cr, const double *ci,
+                         const uint8_t *letters, cplx *g, cplx *ex) {
+    const int64_t dim = (int64_t)1 << n;
+    cplx *lam = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
+    cplx *phi = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
+    cplx *mu = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
+    for (int p = 0; p < n_params; ++p) g[p] = 0;
+    oracle_prepare_state(n, gates, n_gates, theta, lam);
+    memcpy(phi, lam, sizeof(cplx) * (size_t)dim);
+    oracle_apply_operator(n, n_terms, cr, ci, letters, phi, lam);
+    if (ex) *ex = oracle_inner(n, phi, lam);
+    for (int i = n_gates - 1; i >= 0; --i) {
+        const int32_t *gt = gates + 6 * i;
+        oracle_apply_gate(n, phi, gt, theta, 1);
+        for (int j = 0; j < n_params_of(gt[0]); ++j) {
+            memcpy(mu, phi, sizeof(cplx) * (size_t)dim);
+            apply_gate_derivative(n, mu, gt, theta, j);
+            g[gt[3 + j]] += oracle_inner(n, lam, mu);
+        }
+        if (i > 0) oracle_apply_gate(n, lam, gt, theta, 1);
+    }
+    free(lam);
+    free(phi);
+    free(mu);
+}
+
+/* App. B.4: E = <psi|A|psi> and dE/dtheta for a non-Hermitian A (both complex), by two
+ * runs of the modified Algorithm 1: one with A and one with A^dagger (the Pauli strings
+ * are Hermitian, so A^dagger has the conjugate coefficients).  With <lambda|mu>
+ * antilinear in lambda, the run with A yields conj(<d psi|A|psi>) and the run with
+ * A^dagger yields <psi|A|d psi>, so dE = conj(run_A) + run_{A^dagger}.
+ * grad2: 2 n_params doubles (re, im per parameter); expect2: 2 doubles. */
+void oracle_gradient_alg1_operator(int n, const int32_t *gates, int n_gates, const double *theta,
+                                   int n_params, int n_terms, const double *cr, const double *ci,
+                                   const uint8_t *letters, double *grad2, double *expect2) {
+    cplx *ga = (cplx *)malloc(sizeof(cplx) * (size_t)(n_params > 0 ? n_params : 1));
+    cplx *gd = (cplx *)malloc(sizeof(cplx) * (size_t)(n_params > 0 ? n_params : 1));
+    double *cin = (double *)malloc(sizeof(double) * (size_t)(n_terms > 0 ? n_terms : 1));
+    for (int t = 0; t < n_terms; ++t) cin[t] = -ci[t];
+    cplx ex = 0;
+    alg1_complex(n, gates, n_gates, theta, n_params, n_terms, cr, ci, letters, ga, &ex);
+    alg1_complex(n, gates, n_gates, theta, n_params, n_terms, cr, cin, letters, gd, NULL);
+    for (int p = 0; p < n_params; ++p) {
+        const cplx d = conj(ga[p]) + gd[p];
+        grad2[2 * p] = creal(d);
+        grad2[2 * p + 1] = cimag(d);
+    }
+    if (expect2) {
+        expect2[0] = creal(ex);
+        expect2[1] = cimag(ex);
+    }
+    free(ga);
+    free(gd);
+    free(cin);
 }
 
 int oracle_openmp_threads(void) {

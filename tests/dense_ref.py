@@ -145,3 +145,27 @@ def gradient_fd(n: int, gates, theta, n_params: int, terms, delta: float = 1e-5)
         tm = th.copy(); tm[p] -= delta
         g[p] = (energy(n, gates, tp, terms) - energy(n, gates, tm, terms)) / (2 * delta)
     return g
+
+
+def operator(terms, n: int) -> np.ndarray:
+    """Dense operator of a Pauli sum with complex coefficients (non-Hermitian in general)."""
+    a = np.zeros((1 << n, 1 << n), dtype=complex)
+    for c, ops in terms:
+        a += complex(c) * lift({q: PAULI[l] for q, l in ops}, n)
+    return a
+
+
+def expectation_complex(n: int, gates, theta, terms) -> complex:
+    psi = state(n, gates, theta)
+    return complex(psi.conj() @ operator(terms, n) @ psi)
+
+
+def gradient_fd_complex(n: int, gates, theta, n_params: int, terms, delta: float = 1e-5) -> np.ndarray:
+    """Central differences of the complex expectation (real and imaginary parts at once)."""
+    g = np.zeros(n_params, dtype=complex)
+    th = np.array(theta, dtype=float)
+    for p in range(n_params):
+        tp = th.copy(); tp[p] += delta
+        tm = th.copy(); tm[p] -= delta
+        g[p] = (expectation_complex(n, gates, tp, terms) - expectation_complex(n, gates, tm, terms)) / (2 * delta)
+    return g

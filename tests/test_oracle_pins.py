@@ -366,3 +366,56 @@ def test_two_term_shift_fails_for_controlled_rotation():
     two = 0.5 * (D.energy(2, gates, th, terms, (2, 0, np.pi / 2)) - D.energy(2, gates, th, terms, (2, 0, -np.pi / 2)))
     assert abs(two - g_ref[6]) > 1e-3
     assert oracle.gradient_parameter_shift(2, gates, th, 7, terms)[6] == pytest.approx(g_ref[6], abs=1e-9)
+
+
+# ---------------------------------------------------------------- non-Hermitian operators (App. B.4)
+@pytest.mark.parametrize("t", [0.0, 0.5, 2.2, 4.9])
+def test_non_hermitian_closed_form(t):
+    """RY(t)|0> under A = Z + iX: <A> = cos t + i sin t = e^{it}, dA/dt = i e^{it}.
+    RX(t)|0> under A = X + iY: <A> = -i sin t, d/dt = -i cos t."""
+    ry = [("RY", 0, -1, (0, -1, -1))]
+    rx = [("RX", 0, -1, (0, -1, -1))]
+    th = np.array([t])
+    a1 = [(1.0, ((0, "Z"),)), (1j, ((0, "X"),))]
+    a2 = [(1.0, ((0, "X"),)), (1j, ((0, "Y"),))]
+    e, g = oracle.gradient_alg1_operator(1, ry, th, 1, a1)
+    assert e == pytest.approx(np.exp(1j * t), abs=1e-14)
+    assert g[0] == pytest.approx(1j * np.exp(1j * t), abs=1e-14)
+    e, g = oracle.gradient_alg1_operator(1, rx, th, 1, a2)
+    assert e == pytest.approx(-1j * math.sin(t), abs=1e-14)
+    assert g[0] == pytest.approx(-1j * math.cos(t), abs=1e-14)
+    for terms, gates in ((a1, ry), (a2, rx)):
+        ps = oracle.gradient_parameter_shift_operator(1, gates, th, 1, terms)
+        assert ps[0] == pytest.approx(oracle.gradient_alg1_operator(1, gates, th, 1, terms)[1][0], abs=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_non_hermitian_vs_dense(seed):
+    """Random circuits and complex-coefficient Pauli sums: the operator application, the
+    complex expectation and the App. B.4 gradient against the dense route (Kronecker
+    products, central differences of the complex expectation); the parameter-shift
+    route on the real and imaginary parts agrees too."""
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(1, 6))
+    kinds = ("RX", "RY", "RZ", "U3") if n == 1 else ("RX", "RY", "RZ", "U3", "CNOT", "CZ", "CRX", "PHASE")
+    gates, P = W.random_circuit(rng, n, 12, share_params=(seed % 2 == 0), kinds=kinds)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    terms = [(complex(c, float(rng.normal())), ops) for c, ops in W.random_paulis(rng, n, 6, min(4, n))]
+    psi = oracle.state(n, gates, theta)
+    assert np.allclose(oracle.apply_operator(psi, terms), D.operator(terms, n) @ psi, atol=1e-13)
+    e_ref = D.expectation_complex(n, gates, theta, terms)
+    g_ref = D.gradient_fd_complex(n, gates, theta, P, terms)
+    e, g = oracle.gradient_alg1_operator(n, gates, theta, P, terms)
+    assert e == pytest.approx(e_ref, abs=1e-13)
+    assert np.allclose(g, g_ref, atol=1e-8)
+    assert np.allclose(oracle.gradient_parameter_shift_operator(n, gates, theta, P, terms), g, atol=1e-12)
+
+
+def test_non_hermitian_reduces_to_hermitian():
+    """Real coefficients: the App. B.4 route returns the Algorithm-1 energy and gradient
+    with zero imaginary parts."""
+    w = W.config(1, n=6, layers=2)
+    e, g = oracle.gradient_alg1_operator(w.n, w.gates, w.theta, w.n_params, w.terms)
+    e1, g1 = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
+    assert e.real == pytest.approx(e1, abs=1e-13) and abs(e.imag) < 1e-13
+    assert np.allclose(g.real, g1, atol=1e-13) and np.allclose(g.imag, 0.0, atol=1e-13)
