@@ -287,6 +287,7 @@ def run_ours(args, rank, world, dist):
         extra["batched"] = batched_rate(args, rank, world, dist)
     if rank == 0 and not args.no_extra:
         extra["controlled"] = controlled_rate()
+        extra["non_hermitian"] = non_hermitian_rate()
     if rank == 0 and not args.no_ps:
         extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
     if rank == 0 and not args.no_cpu:
@@ -393,6 +394,40 @@ def controlled_rate():
     rng = np.random.default_rng(W.SEED_BASE + 6)
     w = W.Workload("crx_ring_n30_L6_tfim", 30, gates, P, W.draw_theta(rng, P), W.tfim(30, 1.0))
     return workload_rate(w)
+
+
+def non_hermitian_rate(steps=3):
+    """Non-Hermitian operator (App. B.4): the bench circuit (n=30, 745 gates, P=600) with
+    200 random Pauli strings whose coefficients are complex (real and imaginary parts
+    N(0,1)): complex expectation + complex gradient per call."""
+    import torch
+
+    from paper_2009_02823_gb300 import Circuit
+    from paper_2009_02823_gb300 import workloads as W
+    w = W.config(3)
+    rng = np.random.default_rng(W.SEED_BASE + 7)
+    terms = [(complex(c, float(rng.normal())), ops) for c, ops in w.terms]
+    stream = torch.cuda.Stream()
+    circ = Circuit(w.n, w.gates, w.n_params, "c64", stream=stream)
+    circ.set_operator(terms)
+    th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    e = torch.zeros(2, dtype=torch.float64, device="cuda")
+    g = torch.zeros(2 * w.n_params, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    circ.expectation_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        circ.expectation_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    circ.close()
+    return {"workload": "hea_ry_rz_czbrick_n30_L10_rand200, complex coefficients", "dtype": "c64",
+            "ms_per_gradient": round(ms, 3), "gradients_per_s": round(1e3 / ms, 4),
+            "expectation": [float(e[0]), float(e[1])],
+            "method": "A = B + iC: one forward sweep, Hamiltonian + reverse sweep per part"}
 
 
 def param_shift_baseline(args, circ, w, theta_h, adjoint_rate):

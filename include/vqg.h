@@ -191,6 +191,25 @@ int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_par
                      const vqg_options *opt, int n_terms, const uint64_t *x_mask,
                      const uint64_t *z_mask, const double *coef, vqg_plan_info *info);
 
+/* Non-Hermitian cost operators (App. B.4).  vqg_set_operator sets A = sum_k c_k P_k with
+ * complex coefficients c_k = coef_re[k] + i coef_im[k] (masks as vqg_set_hamiltonian);
+ * it replaces any Hamiltonian, and vqg_set_hamiltonian replaces it.  While the
+ * operator has a non-zero imaginary coefficient, vqg_energy* refuse it
+ * (VQG_ERR_STATE) and vqg_expectation_and_gradient* must be used.
+ * vqg_expectation_and_gradient: E = <psi|A|psi> and dE/dtheta_p, both complex:
+ *   expect: 2 doubles (re, im); grad: 2 n_params doubles, (re, im) per parameter; host
+ *   buffers, blocks.  Works for Hermitian operators too (imaginary parts 0).
+ * _device: the same with device pointers on the circuit's stream, no synchronisation.
+ * Method: A = B + iC with B, C Hermitian (the real and imaginary coefficient parts), so
+ * E = <B> + i<C> and dE = d<B> + i d<C>; one forward sweep, then the Hamiltonian
+ * application and reverse sweep of Algorithm 1 once per part (the second from a saved
+ * copy of the final state: one extra state vector of device memory). */
+int vqg_set_operator(vqg_circuit *c, int n_terms, const uint64_t *x_mask, const uint64_t *z_mask,
+                     const double *coef_re, const double *coef_im);
+int vqg_expectation_and_gradient(vqg_circuit *c, const double *theta, double *expect, double *grad);
+int vqg_expectation_and_gradient_device(vqg_circuit *c, const double *theta_dev, double *expect_dev,
+                                        double *grad_dev);
+
 /* Schedule autotuner (no counterpart in the paper, which applies one gate at a time;
  * it tunes the tile fusion of the sweeps).  Times whole energy-and-gradient
  * evaluations of THIS circuit and Hamiltonian under candidate schedules -- tile qubits

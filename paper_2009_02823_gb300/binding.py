@@ -99,6 +99,9 @@ def lib():
             "vqg_kernel_family_name": (ctypes.c_char_p, [i]),
             "vqg_plan": (i, [p, p]),
             "vqg_autotune": (i, [p, p, p]),
+            "vqg_set_operator": (i, [p, i, p, p, p, p]),
+            "vqg_expectation_and_gradient": (i, [p, p, p, p]),
+            "vqg_expectation_and_gradient_device": (i, [p, p, p, p]),
             "vqg_tune_table_clear": (None, []),
             "vqg_last_error": (ctypes.c_char_p, []),
             "vqg_status_string": (ctypes.c_char_p, [i]),
@@ -144,7 +147,7 @@ def pauli_masks(terms, n: int):
     """Neutral Pauli terms -> (x_mask, z_mask, coef): X sets x, Z sets z, Y sets both."""
     x = np.zeros(len(terms), dtype=np.uint64)
     z = np.zeros(len(terms), dtype=np.uint64)
-    c = np.zeros(len(terms), dtype=np.float64)
+    c = np.zeros(len(terms), dtype=np.complex128 if any(isinstance(t[0], complex) for t in terms) else np.float64)
     for t, (coef, ops) in enumerate(terms):
         xm = zm = 0
         for q, l in ops:
@@ -233,10 +236,37 @@ class Circuit:
         self.set_hamiltonian_masks(x, z, c)
 
     def set_hamiltonian_masks(self, x, z, coef):
+        if np.iscomplexobj(coef):
+            if np.any(np.imag(coef) != 0):
+                raise ValueError("complex coefficients: use set_operator (non-Hermitian operator)")
+            coef = np.real(coef)
         x = np.ascontiguousarray(x, dtype=np.uint64)
         z = np.ascontiguousarray(z, dtype=np.uint64)
         c = np.ascontiguousarray(coef, dtype=np.float64)
         _check(lib().vqg_set_hamiltonian(self._h, len(c), _ptr(x), _ptr(z), _ptr(c)))
+
+    def set_operator(self, terms):
+        """Non-Hermitian Pauli sum (complex coefficients), App. B.4."""
+        x, z, c = pauli_masks(terms, self.n)
+        c = np.asarray(c, dtype=np.complex128)
+        cr = np.ascontiguousarray(c.real)
+        ci = np.ascontiguousarray(c.imag)
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        z = np.ascontiguousarray(z, dtype=np.uint64)
+        _check(lib().vqg_set_operator(self._h, len(c), _ptr(x), _ptr(z), _ptr(cr), _ptr(ci)))
+
+    def expectation_and_gradient(self, theta):
+        """(E, dE/dtheta), complex, for the operator set by set_operator."""
+        th = self._theta(theta)
+        e = np.zeros(2)
+        g = np.zeros(2 * max(self.n_params, 1))
+        _check(lib().vqg_expectation_and_gradient(self._h, _ptr(th), _ptr(e), _ptr(g)))
+        return complex(e[0], e[1]), (g[0::2] + 1j * g[1::2])[: self.n_params]
+
+    def expectation_and_gradient_device(self, theta_ptr: int, expect_ptr: int, grad_ptr: int):
+        _check(lib().vqg_expectation_and_gradient_device(self._h, ctypes.c_void_p(theta_ptr),
+                                                         ctypes.c_void_p(expect_ptr),
+                                                         ctypes.c_void_p(grad_ptr)))
 
     # -- evaluation (host buffers)
     def _theta(self, theta) -> np.ndarray:

@@ -114,6 +114,7 @@ void Circuit::prof_harvest() {
 }
 
 Circuit::~Circuit() {
+    free_alt();
     free_plan();
     if (graph_exec_grad) cudaGraphExecDestroy(graph_exec_grad);
     if (graph_exec_energy) cudaGraphExecDestroy(graph_exec_energy);
@@ -355,6 +356,7 @@ extern "C" int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *
     std::vector<PauliTerm> flat;
     int st = group_pauli_terms(cc->n, n_terms, x_mask, z_mask, coef, ham, flat);
     if (st) return st;
+    cc->free_alt();  // a Hermitian operator replaces any non-Hermitian one
     return cc->set_groups(ham, flat);
 }
 
@@ -406,6 +408,11 @@ int Circuit::issue_forward(bool with_ckpt) {
 }
 
 int Circuit::issue_hamiltonian(bool write_lam) {
+    if (ham.empty()) {  // H = 0: lambda = 0, E = 0
+        e_used = 0;
+        if (write_lam) VQG_CUDA(cudaMemsetAsync(lam, 0, state_bytes, stream));
+        return VQG_OK;
+    }
     if (opt.fusion && plan_ok && ham_plan_ok) return issue_hamiltonian_fused();
     e_used = (int)ham.size();
     for (size_t g = 0; g < ham.size(); ++g) {
@@ -464,8 +471,14 @@ int Circuit::issue_gradient(const double *theta_dev, double *energy_dev, double 
 // gate matrices are rebuilt on the device from theta_dev) is captured once per set of
 // argument pointers and replayed afterwards.  Profiling runs eagerly (it needs events
 // between launches); the legacy default stream cannot be captured and also runs eagerly.
+static int hermitian_only(const Circuit &c) {
+    return c.op_complex ? set_error(VQG_ERR_STATE, "the operator is not Hermitian: use vqg_expectation_and_gradient")
+                        : VQG_OK;
+}
+
 int Circuit::run_gradient(const double *theta_dev, double *energy_dev, double *grad_dev) {
     if (!has_ham) return set_error(VQG_ERR_STATE, "no Hamiltonian set");
+    if (int st = hermitian_only(*this)) return st;
     if (opt.autotune && !tuned) {  // first evaluation picks the schedule (blocks once)
         int st = autotune(theta_dev, nullptr);
         if (st) return st;
@@ -505,6 +518,7 @@ int Circuit::run_gradient(const double *theta_dev, double *energy_dev, double *g
 
 int Circuit::run_energy(const double *theta_dev, double *energy_dev, int sg, int ss, double sh) {
     if (!has_ham) return set_error(VQG_ERR_STATE, "no Hamiltonian set");
+    if (int st = hermitian_only(*this)) return st;
     int st;
     if ((st = issue_table(theta_dev, sg, ss, sh))) return st;
     if ((st = issue_forward(false))) return st;

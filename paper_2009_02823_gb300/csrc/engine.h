@@ -13,6 +13,7 @@
 namespace vqg {
 
 struct Plan;
+struct AltHam;
 int set_error(int status, const char *fmt, ...);
 int vqg_validate_circuit(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype);
 
@@ -75,6 +76,20 @@ struct Circuit {
     // fused plan (engine.cu)
     bool plan_ok = false, ham_plan_ok = false;
     struct Plan *plan = nullptr;
+
+    // non-Hermitian operator A = B + iC (operator.cu): the active Hamiltonian is B, `alt`
+    // holds C; psi_saved keeps the forward result for the second part's run
+    AltHam *alt = nullptr;
+    bool op_complex = false;  // C has terms
+    bool op_b_empty = false;  // B has no terms
+    void *psi_saved = nullptr;
+    double *d_op_out = nullptr, *d_op_res = nullptr;
+    void swap_alt();
+    void free_alt();
+    int rebuild_alt_plan();
+    int set_operator(int n_terms, const uint64_t *x, const uint64_t *z, const double *cr, const double *ci);
+    int run_operator(const double *theta_dev, double *expect_dev, double *grad_dev);
+    int ensure_op_scratch(double **out);
 
     // graphs
     cudaGraphExec_t graph_exec_grad = nullptr, graph_exec_energy = nullptr;

@@ -74,6 +74,7 @@ static int apply_schedule(Circuit &c, int K, int Rf, int Rr) {
     int st = c.build_plan();
     if (st) return st;
     if (!c.plan_ok) return set_error(VQG_ERR_UNSUPPORTED, "schedule K=%d Rf=%d Rr=%d has no fused plan", K, Rf, Rr);
+    if ((st = c.rebuild_alt_plan())) return st;  // the stored anti-Hermitian part, if any
     return c.plan_checkpoints();
 }
 

@@ -365,3 +365,87 @@ def test_gpu_parameter_shift_controlled(dtype):
     _e, g_ref = _oracle(n, gates, theta, P, terms)
     with _circ(n, gates, P, dtype, terms) as c:
         assert grad_err(c.gradient_parameter_shift(theta), g_ref) <= TOL[dtype]
+
+
+# ---------------------------------------------------------------- non-Hermitian operators (App. B.4)
+def _assert_complex_parity(dtype, e, g, e_ref, g_ref, what):
+    scale = max(float(np.max(np.abs(g_ref))) if len(g_ref) else 0.0, 1e-300)
+    assert abs(e - e_ref) <= TOL[dtype] * max(1.0, abs(e_ref)), (what, e, e_ref)
+    if len(g_ref):
+        assert float(np.max(np.abs(g - g_ref))) / scale <= TOL[dtype], (what, float(np.max(np.abs(g - g_ref))))
+
+
+def _complex_terms(rng, n, count):
+    return [(complex(c, float(rng.normal())), ops) for c, ops in W.random_paulis(rng, n, count, min(4, n))]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["per_gate", "fused"])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("seed", range(6))
+def test_non_hermitian_random(seed, dtype, mode):
+    rng = np.random.default_rng(3000 + seed)
+    n = [2, 4, 7, 10, 12, 13][seed]
+    gates, P = W.random_circuit(rng, n, 40 + 4 * n, share_params=(seed % 2 == 0), kinds=ALL_KINDS)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    terms = _complex_terms(rng, n, 10)
+    if seed == 3:
+        terms = [(1j * abs(c), ops) for c, ops in terms]  # purely anti-Hermitian
+    e_ref, g_ref = oracle.gradient_alg1_operator(n, gates, theta, P, terms)
+    from paper_2009_02823_gb300 import Circuit
+    with Circuit(n, gates, P, dtype, **mode) as c:
+        c.set_operator(terms)
+        for _ in range(2):  # repeated calls reuse both parts' plans
+            e, g = c.expectation_and_gradient(theta)
+            _assert_complex_parity(dtype, e, g, e_ref, g_ref, f"n={n}")
+
+
+def test_non_hermitian_modes_and_errors():
+    """A Hermitian operator through set_operator (imaginary parts 0), the refusal of the
+    real entry points while the operator is not Hermitian, set_hamiltonian restoring
+    Hermitian mode, the device entry point, and an empty Hamiltonian (gradient 0)."""
+    from paper_2009_02823_gb300 import Circuit
+    from paper_2009_02823_gb300.binding import VqgError
+    import torch
+    rng = np.random.default_rng(31)
+    w = W.config(1, n=11, layers=2)
+    with Circuit(w.n, w.gates, w.n_params, "c128") as c:
+        c.set_operator(w.terms)
+        e, g = c.expectation_and_gradient(w.theta)
+        e_ref, g_ref = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
+        _assert_complex_parity("c128", e, g, complex(e_ref), g_ref.astype(complex), "hermitian via set_operator")
+        terms = _complex_terms(rng, w.n, 8)
+        c.set_operator(terms)
+        with pytest.raises(VqgError) as ei:
+            c.energy_and_gradient(w.theta)
+        assert ei.value.status == -6
+        e_ref, g_ref = oracle.gradient_alg1_operator(w.n, w.gates, w.theta, w.n_params, terms)
+        th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+        ed = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gd = torch.zeros(2 * w.n_params, dtype=torch.float64, device="cuda")
+        c.expectation_and_gradient_device(th.data_ptr(), ed.data_ptr(), gd.data_ptr())
+        torch.cuda.synchronize()
+        e = complex(float(ed[0]), float(ed[1]))
+        g = gd.cpu().numpy()
+        _assert_complex_parity("c128", e, g[0::2] + 1j * g[1::2], e_ref, g_ref, "device entry point")
+        c.set_hamiltonian(w.terms)
+        e, g = c.energy_and_gradient(w.theta)
+        e_ref, g_ref = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
+        assert_parity("c128", e, g, e_ref, g_ref, "set_hamiltonian after set_operator")
+        c.set_hamiltonian([])
+        e, g = c.energy_and_gradient(w.theta)
+        assert e == 0.0 and np.all(g == 0.0)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_non_hermitian_after_autotune(dtype):
+    """The autotuner re-plans both operator parts."""
+    from paper_2009_02823_gb300 import Circuit
+    rng = np.random.default_rng(41)
+    w = W.config(2, n=15, layers=2)
+    terms = _complex_terms(rng, w.n, 12)
+    e_ref, g_ref = oracle.gradient_alg1_operator(w.n, w.gates, w.theta, w.n_params, terms)
+    with Circuit(w.n, w.gates, w.n_params, dtype) as c:
+        c.set_operator(terms)
+        c.autotune(w.theta)
+        e, g = c.expectation_and_gradient(w.theta)
+        _assert_complex_parity(dtype, e, g, e_ref, g_ref, "tuned")
