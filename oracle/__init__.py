@@ -73,6 +73,8 @@ def _load():
             "oracle_inner_parts": (None, [i, p, p, p]),
             "oracle_openmp_threads": (i, []),
             "oracle_apply_operator": (None, [i, i, p, p, p, p, p]),
+            "oracle_apply_product_operator": (None, [i, i, p, p, p, p]),
+            "oracle_gradient_ex": (None, [i, i, p, i, p, i, i, i, p, p, p, p, p, p]),
             "oracle_gradient_alg1_operator": (None, [i, p, i, p, i, i, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
@@ -279,3 +281,55 @@ def gradient_parameter_shift_operator(n: int, gates, theta, n_params: int, terms
     im_terms = [(complex(c).imag, ops) for c, ops in terms]
     return (gradient_parameter_shift(n, gates, theta, n_params, re_terms)
             + 1j * gradient_parameter_shift(n, gates, theta, n_params, im_terms))
+
+
+# ---------------------------------------------------------------- tensor-product operators, input states
+def product_table(products, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """[(coef, [M_0, ..., M_{n-1}])] with 2x2 matrices per qubit -> (coef[K], mats[K, n, 4])."""
+    coef = np.zeros(max(len(products), 1))
+    mats = np.zeros((max(len(products), 1), n, 4), dtype=np.complex128)
+    for k, (c, ms) in enumerate(products):
+        if len(ms) != n:
+            raise ValueError("one 2x2 matrix per qubit")
+        coef[k] = c
+        for q, m in enumerate(ms):
+            mats[k, q] = np.asarray(m, dtype=np.complex128).reshape(4)
+    return coef, np.ascontiguousarray(mats)
+
+
+def apply_product_operator(psi: np.ndarray, products) -> np.ndarray:
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    n = int(np.log2(psi.size))
+    coef, mats = product_table(products, n)
+    out = np.zeros_like(psi)
+    _load().oracle_apply_product_operator(n, len(products), _ptr(coef), _ptr(mats), _ptr(psi), _ptr(out))
+    return out
+
+
+def gradient_general(route: str, n: int, gates, theta, n_params: int, terms=None, products=None,
+                     in_state=None) -> tuple[float, np.ndarray]:
+    """(E, dE/dtheta) for a Pauli sum (terms) or a sum of tensor products (products), from
+    the input state in_state (None: |0...0>).  route: "shift", "alg2" or "alg1"."""
+    gt = gate_table(gates)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.size == 0:
+        th = np.zeros(1)
+    if products is not None:
+        kind, nt = 1, len(products)
+        coef, mats = product_table(products, n)
+        let = np.zeros((1, n), dtype=np.uint8)
+    else:
+        kind, nt = 0, len(terms)
+        coef, let = letter_table(terms, n)
+        mats = np.zeros(4, dtype=np.complex128)
+    ins = None
+    if in_state is not None:
+        ins = np.ascontiguousarray(in_state, dtype=np.complex128)
+        if ins.size != 1 << n:
+            raise ValueError("input state must have 2^n amplitudes")
+    g = np.zeros(max(n_params, 1))
+    e = np.zeros(1)
+    r = {"shift": 0, "alg2": 1, "alg1": 2}[route]
+    _load().oracle_gradient_ex(r, n, _ptr(gt), len(gates), _ptr(th), n_params, kind, nt, _ptr(coef),
+                               _ptr(let), _ptr(mats), None if ins is None else _ptr(ins), _ptr(g), _ptr(e))
+    return float(e[0]), g[:n_params]

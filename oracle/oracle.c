@@ -311,32 +311,76 @@ void oracle_apply_hamiltonian(int n, int n_terms, const double *coef, const uint
     free(tmp);
 }
 
-/* E = <psi|H|psi> for a given state (real part; H is Hermitian for real coef). */
-double oracle_expectation(int n, int n_terms, const double *coef, const uint8_t *letters,
-                          const cplx *psi) {
+/* out = A psi for A = sum_k c_k (x)_q M_{k,q}, a sum of tensor products of 2x2 matrices
+ * (the paper's benchmark operator Hadamard^{(x)N} is one product, Sec. 3): each product
+ * applied to a copy of psi qubit by qubit, then accumulated.  mats holds the 2x2
+ * matrices row-major, product k qubit q at mats + 4 (k n + q). */
+void oracle_apply_product_operator(int n, int n_products, const double *coef, const cplx *mats,
+                                   const cplx *psi, cplx *out) {
+    const int64_t dim = (int64_t)1 << n;
+    cplx *tmp = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
+    memset(out, 0, sizeof(cplx) * (size_t)dim);
+    for (int k = 0; k < n_products; ++k) {
+        memcpy(tmp, psi, sizeof(cplx) * (size_t)dim);
+        for (int q = 0; q < n; ++q) oracle_apply_matrix_1q(n, tmp, q, mats + 4 * ((int64_t)k * n + q));
+        const double c = coef[k];
+        PAR_FOR
+        for (int64_t j = 0; j < dim; ++j) out[j] += c * tmp[j];
+    }
+    free(tmp);
+}
+
+/* The cost operator of the energy and gradient routines: a Pauli sum (letters) or a sum
+ * of tensor products (mats), both with real coefficients; and the input state |in>
+ * (NULL: |0...0>, Sec. 2.2). */
+typedef struct {
+    int kind;  /* 0: Pauli sum, 1: tensor products */
+    int n_terms;
+    const double *coef;
+    const uint8_t *letters;
+    const cplx *mats;
+    const cplx *in;
+} Problem;
+
+static void problem_apply(int n, const Problem *pb, const cplx *psi, cplx *out) {
+    if (pb->kind == 1) oracle_apply_product_operator(n, pb->n_terms, pb->coef, pb->mats, psi, out);
+    else oracle_apply_hamiltonian(n, pb->n_terms, pb->coef, pb->letters, psi, out);
+}
+
+static void problem_input(int n, const Problem *pb, cplx *psi) {
+    if (pb->in) memcpy(psi, pb->in, sizeof(cplx) * ((size_t)1 << n));
+    else oracle_zero_state(n, psi);
+}
+
+static double problem_expectation(int n, const Problem *pb, const cplx *psi) {
     const int64_t dim = (int64_t)1 << n;
     cplx *hp = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
-    oracle_apply_hamiltonian(n, n_terms, coef, letters, psi, hp);
+    problem_apply(n, pb, psi, hp);
     double e = creal(oracle_inner(n, psi, hp));
     free(hp);
     return e;
 }
 
-static double energy_shifted(int n, const int32_t *gates, int n_gates, const double *theta,
-                             int n_terms, const double *coef, const uint8_t *letters,
-                             int shift_gate, int shift_slot, double shift, cplx *psi) {
-    oracle_zero_state(n, psi);
-    for (int i = 0; i < n_gates; ++i)
-        apply_gate_ex(n, psi, gates + 6 * i, theta, 0, i == shift_gate ? shift_slot : -1, shift);
-    return oracle_expectation(n, n_terms, coef, letters, psi);
+/* E = <psi|H|psi> for a given state (real part; H is Hermitian for real coef). */
+double oracle_expectation(int n, int n_terms, const double *coef, const uint8_t *letters,
+                          const cplx *psi) {
+    Problem pb = {0, n_terms, coef, letters, NULL, NULL};
+    return problem_expectation(n, &pb, psi);
 }
 
-/* E(theta) = <0|U^dagger H U|0>  (Sec. 2.2). */
-double oracle_energy(int n, const int32_t *gates, int n_gates, const double *theta, int n_terms,
-                     const double *coef, const uint8_t *letters) {
+static double energy_shifted(int n, const int32_t *gates, int n_gates, const double *theta,
+                             const Problem *pb, int shift_gate, int shift_slot, double shift, cplx *psi) {
+    problem_input(n, pb, psi);
+    for (int i = 0; i < n_gates; ++i)
+        apply_gate_ex(n, psi, gates + 6 * i, theta, 0, i == shift_gate ? shift_slot : -1, shift);
+    return problem_expectation(n, pb, psi);
+}
+
+/* E(theta) = <in|U^dagger H U|in>  (Sec. 2.2). */
+static double energy_pb(int n, const int32_t *gates, int n_gates, const double *theta, const Problem *pb) {
     const int64_t dim = (int64_t)1 << n;
     cplx *psi = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
-    double e = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, -1, -1, 0.0, psi);
+    double e = energy_shifted(n, gates, n_gates, theta, pb, -1, -1, 0.0, psi);
     free(psi);
     return e;
 }
@@ -354,10 +398,8 @@ double oracle_energy(int n, const int32_t *gates, int n_gates, const double *the
  *     a1 + a2 = 1/(2 sqrt 2), a1 - a2 = 1/2, i.e. a1 = (sqrt2 + 1)/(4 sqrt2),
  *     a2 = -(sqrt2 - 1)/(4 sqrt2): a four-term rule, exact.
  * Optional: restrict to gate occurrences [g_first, g_last). */
-void oracle_gradient_parameter_shift(int n, const int32_t *gates, int n_gates,
-                                     const double *theta, int n_params, int n_terms,
-                                     const double *coef, const uint8_t *letters, double *grad,
-                                     int g_first, int g_last) {
+static void ps_pb(int n, const int32_t *gates, int n_gates, const double *theta, int n_params,
+                  const Problem *pb, double *grad, int g_first, int g_last) {
     const int64_t dim = (int64_t)1 << n;
     cplx *psi = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
     const double h = M_PI / 2.0;
@@ -366,13 +408,13 @@ void oracle_gradient_parameter_shift(int n, const int32_t *gates, int n_gates,
     for (int i = g_first; i < g_last; ++i) {
         const int32_t *g = gates + 6 * i;
         for (int j = 0; j < n_params_of(g[0]); ++j) {
-            double ep = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, +h, psi);
-            double em = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, -h, psi);
+            double ep = energy_shifted(n, gates, n_gates, theta, pb, i, j, +h, psi);
+            double em = energy_shifted(n, gates, n_gates, theta, pb, i, j, -h, psi);
             if (g[0] >= OR_CRX && g[0] <= OR_CRZ) {
                 const double r2 = sqrt(2.0);
                 const double a1 = (r2 + 1.0) / (4.0 * r2), a2 = -(r2 - 1.0) / (4.0 * r2);
-                double ep3 = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, +3.0 * h, psi);
-                double em3 = energy_shifted(n, gates, n_gates, theta, n_terms, coef, letters, i, j, -3.0 * h, psi);
+                double ep3 = energy_shifted(n, gates, n_gates, theta, pb, i, j, +3.0 * h, psi);
+                double em3 = energy_shifted(n, gates, n_gates, theta, pb, i, j, -3.0 * h, psi);
                 grad[g[3 + j]] += a1 * (ep - em) + a2 * (ep3 - em3);
             } else {
                 grad[g[3 + j]] += 0.5 * (ep - em);
@@ -386,19 +428,19 @@ void oracle_gradient_parameter_shift(int n, const int32_t *gates, int n_gates,
  *   lambda = H U_{1:G}|in>;  for each occurrence i (and slot j of a multi-parameter gate):
  *   mu = |in>; mu <- U_{1:i-1} mu; mu <- dU_i/dphi_j mu; mu <- U_{i+1:G} mu;
  *   grad[param] += 2 Re <lambda|mu>. */
-void oracle_gradient_alg2(int n, const int32_t *gates, int n_gates, const double *theta,
-                          int n_params, int n_terms, const double *coef, const uint8_t *letters,
-                          double *grad) {
+static void alg2_pb(int n, const int32_t *gates, int n_gates, const double *theta, int n_params,
+                    const Problem *pb, double *grad) {
     const int64_t dim = (int64_t)1 << n;
     cplx *lam = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
     cplx *mu = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
     for (int p = 0; p < n_params; ++p) grad[p] = 0.0;
-    oracle_prepare_state(n, gates, n_gates, theta, mu);
-    oracle_apply_hamiltonian(n, n_terms, coef, letters, mu, lam);
+    problem_input(n, pb, mu);
+    oracle_apply_gates(n, mu, gates, 0, n_gates, theta);
+    problem_apply(n, pb, mu, lam);
     for (int i = 0; i < n_gates; ++i) {
         const int32_t *g = gates + 6 * i;
         for (int j = 0; j < n_params_of(g[0]); ++j) {
-            oracle_zero_state(n, mu);
+            problem_input(n, pb, mu);
             oracle_apply_gates(n, mu, gates, 0, i, theta);
             apply_gate_derivative(n, mu, g, theta, j);
             oracle_apply_gates(n, mu, gates, i + 1, n_gates, theta);
@@ -414,17 +456,17 @@ void oracle_gradient_alg2(int n, const int32_t *gates, int n_gates, const double
  *   for i = G..1: phi <- U_i^dag phi; for each slot j: mu := phi; mu <- dU_i/dphi_j mu;
  *                 grad[param] += 2 Re <lambda|mu>;  if i > 1: lambda <- U_i^dag lambda.
  * Also returns E = Re <phi_{G+1}|lambda_G> (= <psi|H|psi>) through *energy when non-null. */
-void oracle_gradient_alg1(int n, const int32_t *gates, int n_gates, const double *theta,
-                          int n_params, int n_terms, const double *coef, const uint8_t *letters,
-                          double *grad, double *energy) {
+static void alg1_pb(int n, const int32_t *gates, int n_gates, const double *theta, int n_params,
+                    const Problem *pb, double *grad, double *energy) {
     const int64_t dim = (int64_t)1 << n;
     cplx *lam = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
     cplx *phi = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
     cplx *mu = (cplx *)malloc(sizeof(cplx) * (size_t)dim);
     for (int p = 0; p < n_params; ++p) grad[p] = 0.0;
-    oracle_prepare_state(n, gates, n_gates, theta, lam);
+    problem_input(n, pb, lam);
+    oracle_apply_gates(n, lam, gates, 0, n_gates, theta);
     memcpy(phi, lam, sizeof(cplx) * (size_t)dim);
-    oracle_apply_hamiltonian(n, n_terms, coef, letters, phi, lam);
+    problem_apply(n, pb, phi, lam);
     if (energy) *energy = creal(oracle_inner(n, phi, lam));
     for (int i = n_gates - 1; i >= 0; --i) {
         const int32_t *g = gates + 6 * i;
@@ -439,6 +481,49 @@ void oracle_gradient_alg1(int n, const int32_t *gates, int n_gates, const double
     free(lam);
     free(phi);
     free(mu);
+}
+
+/* Pauli-sum operator, |in> = |0...0>. */
+double oracle_energy(int n, const int32_t *gates, int n_gates, const double *theta, int n_terms,
+                     const double *coef, const uint8_t *letters) {
+    Problem pb = {0, n_terms, coef, letters, NULL, NULL};
+    return energy_pb(n, gates, n_gates, theta, &pb);
+}
+
+void oracle_gradient_parameter_shift(int n, const int32_t *gates, int n_gates,
+                                     const double *theta, int n_params, int n_terms,
+                                     const double *coef, const uint8_t *letters, double *grad,
+                                     int g_first, int g_last) {
+    Problem pb = {0, n_terms, coef, letters, NULL, NULL};
+    ps_pb(n, gates, n_gates, theta, n_params, &pb, grad, g_first, g_last);
+}
+
+void oracle_gradient_alg2(int n, const int32_t *gates, int n_gates, const double *theta,
+                          int n_params, int n_terms, const double *coef, const uint8_t *letters,
+                          double *grad) {
+    Problem pb = {0, n_terms, coef, letters, NULL, NULL};
+    alg2_pb(n, gates, n_gates, theta, n_params, &pb, grad);
+}
+
+void oracle_gradient_alg1(int n, const int32_t *gates, int n_gates, const double *theta,
+                          int n_params, int n_terms, const double *coef, const uint8_t *letters,
+                          double *grad, double *energy) {
+    Problem pb = {0, n_terms, coef, letters, NULL, NULL};
+    alg1_pb(n, gates, n_gates, theta, n_params, &pb, grad, energy);
+}
+
+/* General problem: op_kind 0 (Pauli sum: letters) or 1 (tensor products: mats), input
+ * state in_state (NULL: |0...0>).  route 0: parameter shift, 1: Algorithm 2,
+ * 2: Algorithm 1 (energy returned through *energy when non-null). */
+void oracle_gradient_ex(int route, int n, const int32_t *gates, int n_gates, const double *theta,
+                        int n_params, int op_kind, int n_terms, const double *coef,
+                        const uint8_t *letters, const cplx *mats, const cplx *in_state,
+                        double *grad, double *energy) {
+    Problem pb = {op_kind, n_terms, coef, letters, mats, in_state};
+    if (route == 0) ps_pb(n, gates, n_gates, theta, n_params, &pb, grad, 0, -1);
+    else if (route == 1) alg2_pb(n, gates, n_gates, theta, n_params, &pb, grad);
+    else alg1_pb(n, gates, n_gates, theta, n_params, &pb, grad, energy);
+    if (energy && route != 2) *energy = energy_pb(n, gates, n_gates, theta, &pb);
 }
 
 /* ------------------------------------------------- non-Hermitian operators (App. B.4) */

@@ -419,3 +419,76 @@ def test_non_hermitian_reduces_to_hermitian():
     e1, g1 = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
     assert e.real == pytest.approx(e1, abs=1e-13) and abs(e.imag) < 1e-13
     assert np.allclose(g.real, g1, atol=1e-13) and np.allclose(g.imag, 0.0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- tensor-product operators and input states
+HAD = np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_hadamard_product_closed_form(n):
+    """The paper's benchmark operator H^{(x)N} (Sec. 3) on an unentangled RY layer:
+    <H> per qubit is (sin t + cos t)/sqrt2, so E = prod_q f(t_q) and
+    dE/dt_q = f'(t_q) prod_{r != q} f(t_r), for all three routes."""
+    rng = np.random.default_rng(n)
+    t = rng.uniform(0, 2 * np.pi, n)
+    gates = [("RY", q, -1, (q, -1, -1)) for q in range(n)]
+    f = (np.sin(t) + np.cos(t)) / np.sqrt(2)
+    df = (np.cos(t) - np.sin(t)) / np.sqrt(2)
+    e_ref = float(np.prod(f))
+    g_ref = np.array([df[q] * np.prod(np.delete(f, q)) for q in range(n)])
+    for route in ("shift", "alg2", "alg1"):
+        e, g = oracle.gradient_general(route, n, gates, t, n, products=[(1.0, [HAD] * n)])
+        assert e == pytest.approx(e_ref, abs=1e-13)
+        assert np.allclose(g, g_ref, atol=1e-13)
+
+
+def _random_hermitian(rng):
+    a = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    return (a + a.conj().T) / 2
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_products_and_input_state_vs_dense(seed):
+    """Sums of tensor products of random Hermitian 2x2 matrices and a random input state:
+    the operator application, the energy and the three gradient routes against the dense
+    route (Kronecker products, central differences)."""
+    rng = np.random.default_rng(800 + seed)
+    n = int(rng.integers(1, 6))
+    kinds = ("RX", "RY", "RZ", "U3") if n == 1 else ("RX", "RY", "RZ", "U3", "CNOT", "CZ", "CRY", "PHASE")
+    gates, P = W.random_circuit(rng, n, 12, share_params=(seed % 2 == 0), kinds=kinds)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    products = [(float(rng.normal()), [_random_hermitian(rng) for _ in range(n)]) for _ in range(1 + seed % 3)]
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    if seed % 2:
+        psi0 /= np.linalg.norm(psi0)  # normalised or not: E is the plain quadratic form
+    A = np.zeros((1 << n, 1 << n), dtype=complex)
+    for c, ms in products:
+        A += c * D.lift(dict(enumerate(ms)), n)
+    assert np.allclose(oracle.apply_product_operator(psi0, products), A @ psi0, atol=1e-13)
+
+    def dense_e(th):
+        psi = psi0.copy()
+        for g in gates:
+            psi = D.gate_unitary(g, th, n) @ psi
+        return float(np.real(psi.conj() @ A @ psi))
+
+    e_ref = dense_e(theta)
+    g_ref = np.zeros(P)
+    for p in range(P):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += 1e-5
+        tm[p] -= 1e-5
+        g_ref[p] = (dense_e(tp) - dense_e(tm)) / 2e-5
+    for route in ("shift", "alg2", "alg1"):
+        e, g = oracle.gradient_general(route, n, gates, theta, P, products=products, in_state=psi0)
+        assert e == pytest.approx(e_ref, abs=1e-12)
+        assert np.allclose(g, g_ref, atol=1e-7 * max(1.0, np.max(np.abs(g_ref))))
+    # Pauli operator from a custom input state too
+    terms = W.random_paulis(rng, n, 5, min(4, n))
+    Hm = D.hamiltonian(terms, n)
+    psi = psi0.copy()
+    for g in gates:
+        psi = D.gate_unitary(g, theta, n) @ psi
+    e, _g = oracle.gradient_general("alg1", n, gates, theta, P, terms=terms, in_state=psi0)
+    assert e == pytest.approx(float(np.real(psi.conj() @ Hm @ psi)), abs=1e-12)
