@@ -288,6 +288,7 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and not args.no_extra:
         extra["controlled"] = controlled_rate()
         extra["non_hermitian"] = non_hermitian_rate()
+        extra["hadamard_product"] = product_rate()
     if rank == 0 and not args.no_ps:
         extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
     if rank == 0 and not args.no_cpu:
@@ -428,6 +429,42 @@ def non_hermitian_rate(steps=3):
             "ms_per_gradient": round(ms, 3), "gradients_per_s": round(1e3 / ms, 4),
             "expectation": [float(e[0]), float(e[1])],
             "method": "A = B + iC: one forward sweep, Hamiltonian + reverse sweep per part"}
+
+
+def product_rate(steps=3):
+    """The paper's benchmark operator Hadamard^{(x)30} (Sec. 3) on the bench circuit (n=30,
+    745 gates, P=600), from a random normalised input state generated on the device."""
+    import torch
+
+    from paper_2009_02823_gb300 import Circuit
+    from paper_2009_02823_gb300 import workloads as W
+    w = W.config(3)
+    had = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    stream = torch.cuda.Stream()
+    circ = Circuit(w.n, w.gates, w.n_params, "c64", stream=stream)
+    circ.set_product_operator([(1.0, [had] * w.n)])
+    gen = torch.Generator(device="cuda").manual_seed(W.SEED_BASE + 8)
+    psi0 = torch.randn(1 << w.n, dtype=torch.complex64, device="cuda", generator=gen)
+    psi0 /= torch.linalg.vector_norm(psi0)
+    circ.set_input_state(device_ptr=psi0.data_ptr())
+    del psi0
+    th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    circ.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        circ.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    circ.close()
+    return {"workload": "hea_ry_rz_czbrick_n30_L10, operator Hadamard^(x)30, random input state",
+            "dtype": "c64", "ms_per_gradient": round(ms, 3), "gradients_per_s": round(1e3 / ms, 4),
+            "energy": float(e[0])}
 
 
 def param_shift_baseline(args, circ, w, theta_h, adjoint_rate):

@@ -191,6 +191,24 @@ int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_par
                      const vqg_options *opt, int n_terms, const uint64_t *x_mask,
                      const uint64_t *z_mask, const double *coef, vqg_plan_info *info);
 
+/* Tensor-product cost operators (the paper's benchmark operator Hadamard^{(x)N}, Sec. 3;
+ * Sec. 2.1 asks only that the operator can be applied to a state).
+ * vqg_set_product_operator: A = sum_k coef[k] (x)_q M_{k,q}, n_products >= 1 products of
+ *   one 2x2 matrix per qubit; mats: host, n_products * n_qubits * 8 doubles, product k
+ *   qubit q at mats + 8 (k n + q), row-major (re, im) pairs (m00, m01, m10, m11).  Every
+ *   factor must be Hermitian (VQG_ERR_UNSUPPORTED otherwise) so that E is real; the
+ *   energy and gradient entry points then use A.  Replaces any Hamiltonian or operator;
+ *   vqg_set_hamiltonian / vqg_set_operator replace it.  lambda = A psi runs each product
+ *   through the fused forward passes (or one kernel per qubit below 10 qubits) and adds
+ *   the products (one scratch state when n_products > 1). */
+int vqg_set_product_operator(vqg_circuit *c, int n_products, const double *coef, const double *mats);
+
+/* Input state (Sec. 2.2's fixed input state; default |0...0>).  state: 2^n amplitudes of
+ * the circuit's dtype (complex64 or complex128, interleaved), host memory (on_device = 0)
+ * or device memory (on_device = 1); copied into a library-owned buffer (one state), used
+ * as given (not normalised).  NULL restores |0...0>.  Blocks until the copy is done. */
+int vqg_set_input_state(vqg_circuit *c, const void *state, int on_device);
+
 /* Non-Hermitian cost operators (App. B.4).  vqg_set_operator sets A = sum_k c_k P_k with
  * complex coefficients c_k = coef_re[k] + i coef_im[k] (masks as vqg_set_hamiltonian);
  * it replaces any Hamiltonian, and vqg_set_hamiltonian replaces it.  While the

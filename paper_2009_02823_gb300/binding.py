@@ -100,6 +100,8 @@ def lib():
             "vqg_plan": (i, [p, p]),
             "vqg_autotune": (i, [p, p, p]),
             "vqg_set_operator": (i, [p, i, p, p, p, p]),
+            "vqg_set_product_operator": (i, [p, i, p, p]),
+            "vqg_set_input_state": (i, [p, p, i]),
             "vqg_expectation_and_gradient": (i, [p, p, p, p]),
             "vqg_expectation_and_gradient_device": (i, [p, p, p, p]),
             "vqg_tune_table_clear": (None, []),
@@ -254,6 +256,35 @@ class Circuit:
         x = np.ascontiguousarray(x, dtype=np.uint64)
         z = np.ascontiguousarray(z, dtype=np.uint64)
         _check(lib().vqg_set_operator(self._h, len(c), _ptr(x), _ptr(z), _ptr(cr), _ptr(ci)))
+
+    def set_product_operator(self, products):
+        """A = sum_k c_k (x)_q M_{k,q}: products = [(c_k, [M_0, ..., M_{n-1}])], Hermitian 2x2
+        factors (e.g. the Hadamard matrix on every qubit)."""
+        coef = np.ascontiguousarray([float(c) for c, _ms in products], dtype=np.float64)
+        mats = np.zeros((len(products), self.n, 8))
+        for k, (_c, ms) in enumerate(products):
+            if len(ms) != self.n:
+                raise ValueError("one 2x2 matrix per qubit")
+            for q, m in enumerate(ms):
+                m = np.asarray(m, dtype=np.complex128).reshape(4)
+                mats[k, q, 0::2], mats[k, q, 1::2] = m.real, m.imag
+        mats = np.ascontiguousarray(mats)
+        _check(lib().vqg_set_product_operator(self._h, len(products), _ptr(coef), _ptr(mats)))
+
+    def set_input_state(self, state=None, device_ptr: int | None = None):
+        """Input state |in> (host array of 2^n amplitudes, or a device pointer to them);
+        no argument restores |0...0>."""
+        if device_ptr is not None:
+            _check(lib().vqg_set_input_state(self._h, ctypes.c_void_p(device_ptr), 1))
+            return
+        if state is None:
+            _check(lib().vqg_set_input_state(self._h, None, 0))
+            return
+        dt = np.complex64 if DTYPE[self.dtype] == 0 else np.complex128
+        st = np.ascontiguousarray(state, dtype=dt)
+        if st.size != 1 << self.n:
+            raise ValueError("input state must have 2^n amplitudes")
+        _check(lib().vqg_set_input_state(self._h, _ptr(st), 0))
 
     def expectation_and_gradient(self, theta):
         """(E, dE/dtheta), complex, for the operator set by set_operator."""

@@ -115,6 +115,7 @@ void Circuit::prof_harvest() {
 
 Circuit::~Circuit() {
     free_alt();
+    free_products();
     free_plan();
     if (graph_exec_grad) cudaGraphExecDestroy(graph_exec_grad);
     if (graph_exec_energy) cudaGraphExecDestroy(graph_exec_energy);
@@ -356,7 +357,8 @@ extern "C" int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *
     std::vector<PauliTerm> flat;
     int st = group_pauli_terms(cc->n, n_terms, x_mask, z_mask, coef, ham, flat);
     if (st) return st;
-    cc->free_alt();  // a Hermitian operator replaces any non-Hermitian one
+    cc->free_alt();  // a Pauli Hamiltonian replaces a non-Hermitian or tensor-product operator
+    cc->free_products();
     return cc->set_groups(ham, flat);
 }
 
@@ -387,9 +389,10 @@ int Circuit::issue_table(const double *theta_dev, int shift_gate, int shift_slot
 }
 
 int Circuit::issue_forward(bool with_ckpt) {
-    if (opt.fusion && plan_ok) return issue_forward_fused(with_ckpt);  // pass 0 starts from |0...0>
+    if (opt.fusion && plan_ok) return issue_forward_fused(with_ckpt);  // pass 0 starts from |in>
     prof_begin(FAM_INIT);
-    launch_init_zero(psi, n, dbl, nb, stream);
+    if (has_input) VQG_CUDA(cudaMemcpyAsync(psi, d_input, state_bytes, cudaMemcpyDeviceToDevice, stream));
+    else launch_init_zero(psi, n, dbl, nb, stream);
     prof_end();
     size_t k = 0;
     for (int i = 0; i < G; ++i) {
@@ -408,6 +411,7 @@ int Circuit::issue_forward(bool with_ckpt) {
 }
 
 int Circuit::issue_hamiltonian(bool write_lam) {
+    if (prod_active) return issue_hamiltonian_product();
     if (ham.empty()) {  // H = 0: lambda = 0, E = 0
         e_used = 0;
         if (write_lam) VQG_CUDA(cudaMemsetAsync(lam, 0, state_bytes, stream));

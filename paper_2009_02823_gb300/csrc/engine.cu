@@ -584,6 +584,37 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
     return pl;
 }
 
+// Device copies of a plan's pass tables (at least one element each: a valid pointer
+// for empty tables; only what exists is copied).
+int Circuit::upload_plan(Plan *pl) {
+    auto up = [&](void **d, const auto &vec) -> int {
+        const size_t elem = sizeof(vec[0]);
+        int s2 = dalloc(d, elem * std::max<size_t>(vec.size(), 1));
+        if (s2) return s2;
+        if (!vec.empty() && cudaMemcpy(*d, vec.data(), elem * vec.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return set_error(VQG_ERR_CUDA, "plan upload failed");
+        return VQG_OK;
+    };
+    int st;
+    if ((st = up((void **)&pl->d_passes, pl->passes))) return st;
+    if ((st = up((void **)&pl->d_stages, pl->stages))) return st;
+    if ((st = up((void **)&pl->d_ops, pl->ops))) return st;
+    if ((st = up((void **)&pl->d_slot_map, pl->slot_map))) return st;
+    if ((st = up((void **)&pl->d_diags, pl->diags))) return st;
+    if ((st = up((void **)&pl->d_items, pl->items))) return st;
+    return VQG_OK;
+}
+
+// Release a plan with its device tables.
+void Circuit::release_plan(Plan *pl) {
+    if (!pl) return;
+    for (void *p : {(void *)pl->d_passes, (void *)pl->d_stages, (void *)pl->d_ops, (void *)pl->d_diags,
+                    (void *)pl->d_items, (void *)pl->d_slot_map, (void *)pl->d_hp, (void *)pl->d_hg,
+                    (void *)pl->d_ht, (void *)pl->d_mats_f})
+        dfree(p);
+    delete pl;
+}
+
 int Circuit::build_plan() {
     // gate plan once; Hamiltonian plan whenever the Hamiltonian changes
     if (!plan) {
@@ -595,25 +626,13 @@ int Circuit::build_plan() {
             return VQG_OK;  // no fused schedule for this size: one kernel per gate
         }
         pl->grid_fwd = occupancy_grid(num_sms, 2, pl->n_tiles);
-        int st;
-        // allocate at least one element (a valid pointer for empty tables), copy what exists
-        auto up = [&](void **d, const auto &vec) -> int {
-            const size_t elem = sizeof(vec[0]);
-            int s2 = dalloc(d, elem * std::max<size_t>(vec.size(), 1));
-            if (s2) return s2;
-            if (!vec.empty() && cudaMemcpy(*d, vec.data(), elem * vec.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-                return set_error(VQG_ERR_CUDA, "plan upload failed");
-            return VQG_OK;
-        };
+        if (has_input) pl->passes[0].from_zero = 0;  // pass 0 reads the input state
         plan = pl;
-        if ((st = up((void **)&pl->d_passes, pl->passes))) return st;
-        if ((st = up((void **)&pl->d_stages, pl->stages))) return st;
-        if ((st = up((void **)&pl->d_ops, pl->ops))) return st;
-        if ((st = up((void **)&pl->d_slot_map, pl->slot_map))) return st;
-        if ((st = up((void **)&pl->d_diags, pl->diags))) return st;
-        if ((st = up((void **)&pl->d_items, pl->items))) return st;
+        int st;
+        if ((st = upload_plan(pl))) return st;
         if (!dbl && (st = dalloc((void **)&pl->d_mats_f, sizeof(float) * 8 * std::max(G, 1)))) return st;
         plan_ok = true;
+        if (prod_active && (st = build_product_plans())) return st;  // same tile geometry
     }
     if (plan && has_ham) return build_ham_plan();
     return VQG_OK;
@@ -771,15 +790,14 @@ void Circuit::free_plan() {
     plan = nullptr;
 }
 
-// Release the plan with its device tables (the circuit's other buffers stay).
+// Release the plan with its device tables (the circuit's other buffers stay); plans
+// derived from its geometry (tensor-product operators) go too.
 void Circuit::drop_plan() {
     if (!plan) return;
-    for (void *p : {(void *)plan->d_passes, (void *)plan->d_stages, (void *)plan->d_ops, (void *)plan->d_diags,
-                    (void *)plan->d_items, (void *)plan->d_slot_map, (void *)plan->d_hp, (void *)plan->d_hg,
-                    (void *)plan->d_ht, (void *)plan->d_mats_f})
-        dfree(p);
-    free_plan();
+    release_plan(plan);
+    plan = nullptr;
     plan_ok = ham_plan_ok = false;
+    drop_product_plans();
 }
 
 // Checkpoints of the fused schedule sit at pass boundaries: the output of pass j is
@@ -800,7 +818,7 @@ void Circuit::set_fused_checkpoint(int pass, int k) { plan->ckpt_of_pass[pass] =
 int Circuit::issue_forward_fused(bool with_ckpt) {
     Plan *pl = plan;
     const void *mats = dbl ? (const void *)d_mats : (const void *)pl->d_mats_f;
-    const void *in = psi;
+    const void *in = has_input ? d_input : psi;  // pass 0 synthesises |0...0> unless an input is set
     for (size_t j = 0; j < pl->passes.size(); ++j) {
         const int k = with_ckpt ? pl->ckpt_of_pass[j] : -1;
         void *out = k >= 0 ? ckpt_buf[k] : psi;

@@ -91,6 +91,26 @@ struct Circuit {
     int run_operator(const double *theta_dev, double *expect_dev, double *grad_dev);
     int ensure_op_scratch(double **out);
 
+    // input state (product.cu): |in> replaces |0...0> when set
+    bool has_input = false;
+    void *d_input = nullptr;
+    int set_input(const void *state, bool on_device);
+
+    // tensor-product operators (product.cu): A = sum_k c_k (x)_q M_{k,q}, Hermitian factors
+    bool prod_active = false;
+    int n_products = 0;
+    double *d_prod_mats = nullptr;  // 8 doubles per (product, qubit); c_k folded into qubit 0
+    float *d_prod_mats_f = nullptr;
+    void *d_prod_tmp = nullptr;
+    std::vector<Plan *> prod_plans;
+    int set_products(int n_products, const double *coef, const double *mats);
+    int build_product_plans();
+    int issue_hamiltonian_product();
+    void drop_product_plans();
+    void free_products();
+    int upload_plan(Plan *pl);
+    void release_plan(Plan *pl);
+
     // graphs
     cudaGraphExec_t graph_exec_grad = nullptr, graph_exec_energy = nullptr;
     const void *graph_key_grad[3] = {nullptr, nullptr, nullptr};

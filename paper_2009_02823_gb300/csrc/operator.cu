@@ -115,6 +115,7 @@ int Circuit::set_operator(int n_t, const uint64_t *x, const uint64_t *z, const d
     if (!st) st = group_pauli_terms(n, (int)cc.size(), cx.data(), cz.data(), cc.data(), gc, fc);
     if (st) return st;
     free_alt();
+    free_products();
     if (!cc.empty()) {
         alt = new AltHam();
         if ((st = dalloc(&psi_saved, state_bytes))) return st;

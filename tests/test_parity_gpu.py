@@ -449,3 +449,76 @@ def test_non_hermitian_after_autotune(dtype):
         c.autotune(w.theta)
         e, g = c.expectation_and_gradient(w.theta)
         _assert_complex_parity(dtype, e, g, e_ref, g_ref, "tuned")
+
+
+# ---------------------------------------------------------------- tensor-product operators and input states
+HAD = np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2)
+
+
+def _rand_herm(rng):
+    a = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    return (a + a.conj().T) / 2
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["per_gate", "fused"])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("seed", range(6))
+def test_products_and_input_state(seed, dtype, mode):
+    """Sums of tensor products (Hadamard^N and random Hermitian factors), with and
+    without a random input state, against the oracle's general Algorithm-1 route."""
+    from paper_2009_02823_gb300 import Circuit
+    rng = np.random.default_rng(4000 + seed)
+    n = [3, 6, 10, 11, 12, 13][seed]
+    gates, P = W.random_circuit(rng, n, 30 + 3 * n, share_params=(seed % 2 == 1), kinds=ALL_KINDS)
+    theta = rng.uniform(0, 2 * np.pi, max(P, 1))[:P]
+    products = [(1.0, [HAD] * n)] + [(float(rng.normal()), [_rand_herm(rng) for _ in range(n)])
+                                     for _ in range(seed % 3)]
+    psi0 = None
+    if seed % 2 == 0:
+        psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+        psi0 /= np.linalg.norm(psi0)
+    e_ref, g_ref = oracle.gradient_general("alg1", n, gates, theta, P, products=products, in_state=psi0)
+    with Circuit(n, gates, P, dtype, **mode) as c:
+        c.set_product_operator(products)
+        if psi0 is not None:
+            c.set_input_state(psi0)
+        for _ in range(2):
+            e, g = c.energy_and_gradient(theta)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"n={n} products={len(products)}")
+        assert energy_err(c.energy(theta), e_ref) <= TOL[dtype]
+        if psi0 is not None:  # back to |0...0>
+            c.set_input_state(None)
+            e_ref0, g_ref0 = oracle.gradient_general("alg1", n, gates, theta, P, products=products)
+            e, g = c.energy_and_gradient(theta)
+            assert_parity(dtype, e, g, e_ref0, g_ref0, "input cleared")
+        c.set_hamiltonian(W.random_paulis(rng, n, 5, min(4, n)))  # Pauli Hamiltonian again
+        c.energy_and_gradient(theta)
+
+
+def test_product_operator_rejects_non_hermitian():
+    from paper_2009_02823_gb300 import Circuit
+    from paper_2009_02823_gb300.binding import VqgError
+    gates, P = W.hea_ry_rz(4, 1)
+    with Circuit(4, gates, P, "c64") as c:
+        with pytest.raises(VqgError) as ei:
+            c.set_product_operator([(1.0, [np.array([[0, 1], [0, 0]])] * 4)])
+        assert ei.value.status == -5
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hadamard_product_full_size_closed_form(dtype):
+    """Hadamard^{(x)30} on an RY layer over 30 qubits (8 / 16 GiB states): E and every
+    gradient entry against the closed form prod_q f(t_q), f = (sin t + cos t)/sqrt2."""
+    from paper_2009_02823_gb300 import Circuit
+    n = 30
+    rng = np.random.default_rng(30)
+    t = np.pi / 4 + 0.2 * rng.normal(size=n)
+    gates = [("RY", q, -1, (q, -1, -1)) for q in range(n)]
+    f = (np.sin(t) + np.cos(t)) / np.sqrt(2)
+    df = (np.cos(t) - np.sin(t)) / np.sqrt(2)
+    e_ref = float(np.prod(f))
+    g_ref = np.array([df[q] * np.prod(np.delete(f, q)) for q in range(n)])
+    with Circuit(n, gates, n, dtype) as c:
+        c.set_product_operator([(1.0, [HAD] * n)])
+        e, g = c.energy_and_gradient(t)
+        assert_parity(dtype, e, g, e_ref, g_ref, "H^30")
