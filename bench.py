@@ -36,9 +36,9 @@ METRIC = "adjoint gradients/s at n=30,P=600"
 # streams whole states, so traffic scales with 2^n.  Reset an entry to None whenever
 # its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    "adj_fused": (1.073967e9 + 1.016815e9) / 2**26,
-    "fwd_fused": (0.537456384e9 + 0.486807552e9) / 2**26,
-    "ham_fused": (1.073797e9 + 0.487862784e9) / 2**26,
+    "adj_fused": (1.077255e9 + 1.014021e9) / 2**26,
+    "fwd_fused": (0.54030592e9 + 0.48089984e9) / 2**26,
+    "ham_fused": (1.144262e9 + 0.478371072e9) / 2**26,
 }
 UNIT = "gradients/s"
 
@@ -446,6 +446,7 @@ def product_rate(steps=3):
     gen = torch.Generator(device="cuda").manual_seed(W.SEED_BASE + 8)
     psi0 = torch.randn(1 << w.n, dtype=torch.complex64, device="cuda", generator=gen)
     psi0 /= torch.linalg.vector_norm(psi0)
+    torch.cuda.synchronize()  # written on torch's stream; the library copies on its own
     circ.set_input_state(device_ptr=psi0.data_ptr())
     del psi0
     th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")

@@ -206,7 +206,9 @@ int vqg_set_product_operator(vqg_circuit *c, int n_products, const double *coef,
 /* Input state (Sec. 2.2's fixed input state; default |0...0>).  state: 2^n amplitudes of
  * the circuit's dtype (complex64 or complex128, interleaved), host memory (on_device = 0)
  * or device memory (on_device = 1); copied into a library-owned buffer (one state), used
- * as given (not normalised).  NULL restores |0...0>.  Blocks until the copy is done. */
+ * as given (not normalised).  NULL restores |0...0>.  Blocks until the copy is done.
+ * A device source is read on the circuit's stream: the caller makes sure it has been
+ * written (same stream, or synchronised) before the call. */
 int vqg_set_input_state(vqg_circuit *c, const void *state, int on_device);
 
 /* Non-Hermitian cost operators (App. B.4).  vqg_set_operator sets A = sum_k c_k P_k with

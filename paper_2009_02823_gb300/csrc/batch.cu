@@ -147,9 +147,12 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, a.stages, a.ops, a.diags, a.items,
                             a.mats, false, tid, kBNT);
             __syncthreads();
-            for (int ti = t0; ti < t1; ++ti)
+            for (int ti = t0; ti < t1; ++ti) {
+                if (ti + 1 < t1 && !P.from_zero)
+                    TileIO<T, K>::template prefetch<kBNT>(psi, tile_base(ti + 1, P.nontile, P.n_nontile), row_off, tid);
                 fwd_tile<T, K, R, true>(tile, row_off, pg, P.n_stage, tile_base(ti, P.nontile, P.n_nontile),
                                         P.from_zero != 0, psi, psi, tid);
+            }
         } else if (ok && tk.phase < F + H) {  // Hamiltonian pass
             const HPass &P = a.hp[C.hpass0 + tk.phase - F];
             A *tile = reinterpret_cast<A *>(smem);
@@ -162,6 +165,11 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             __syncthreads();
             double eacc = 0.0;
             for (int ti = t0; ti < t1; ++ti) {
+                if (ti + 1 < t1) {
+                    const uint64_t next = tile_base(ti + 1, P.nontile, P.n_nontile);
+                    TileIO<T, K>::template prefetch<kBNT>(psi, next, row_off, tid);
+                    if (!P.first) TileIO<T, K>::template prefetch<kBNT>(lam, next, row_off, tid);
+                }
                 const T run = ham_tile<T, K, true>(tile, row_off, tb, tile_base(ti, P.nontile, P.n_nontile),
                                                    P.first != 0, psi, lam, tid);
                 eacc += (double)warp_tree<T>(run);
@@ -189,9 +197,15 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             load_prog<T, R>(pg, P.rstage0, P.n_rstage, P.rdiag0, P.n_rdiag, a.stages, a.ops, a.diags, a.items,
                             a.mats, true, tid, kBNT);
             __syncthreads();
-            for (int ti = t0; ti < t1; ++ti)
+            for (int ti = t0; ti < t1; ++ti) {
+                if (ti + 1 < t1) {
+                    const uint64_t next = tile_base(ti + 1, P.nontile, P.n_nontile);
+                    TileIO<T, K>::template prefetch<kBNT>(psi, next, row_off, tid);
+                    TileIO<T, K>::template prefetch<kBNT>(lam, next, row_off, tid);
+                }
                 rev_tile<T, K, R, true>(tphi, tlam, row_off, pg, P.n_rstage, tile_base(ti, P.nontile, P.n_nontile),
                                         psi, psi, lam, acc, stash, tid);
+            }
             __syncthreads();
             for (int i = tid; i < n_ls; i += kBNT) part[(size_t)(H + smap[i]) * C.chunks + tk.chunk] = acc[i];
         } else if (ok) {  // finalize: E and the gradient of this circuit (fixed-order sums)
