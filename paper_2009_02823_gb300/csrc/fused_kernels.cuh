@@ -326,41 +326,53 @@ VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64
 }
 
 // ------------------------------------------------------------------ gate ops (reverse)
+// Balanced pairwise sum (short dependency chains; N a power of two).  Consumes x.
+template <int N, typename T>
+VQG_DEV T tree_sum(T (&x)[N]) {
+#pragma unroll
+    for (int s = 1; s < N; s *= 2)
+#pragma unroll
+        for (int i = 0; i + s < N; i += 2 * s) x[i] += x[i + s];
+    return x[0];
+}
+
 // Each returns the thread's partial of the gate's reduction value(s) computed from
 // (phi_{i+1} = a, lambda_i = l) before un-applying U^dagger to both.
 template <int KB, int NA, typename T>
 VQG_DEV T rev_ry(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], T c, T s) {
-    T v = 0;
+    T pv[NA / 2];
+    int q = 0;
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
         if (j & (1 << KB)) continue;
         const int j1 = j | (1 << KB);
         const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
         // Im <lambda| Y |phi> over the pair: Re(conj(l1) a0) - Re(conj(l0) a1)
-        v += (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
+        pv[q++] = (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
         // RY^dagger = [[c, s], [-s, c]]
         a[j] = mk<T>(c * a0.x + s * a1.x, c * a0.y + s * a1.y);
         a[j1] = mk<T>(c * a1.x - s * a0.x, c * a1.y - s * a0.y);
         l[j] = mk<T>(c * l0.x + s * l1.x, c * l0.y + s * l1.y);
         l[j1] = mk<T>(c * l1.x - s * l0.x, c * l1.y - s * l0.y);
     }
-    return v;
+    return tree_sum<NA / 2, T>(pv);
 }
 
 template <int KB, int NA, typename T>
 VQG_DEV T rev_rx(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud) {
-    T v = 0;
+    T pv[NA / 2];
+    int q = 0;
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
         if (j & (1 << KB)) continue;
         const int j1 = j | (1 << KB);
         const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
         // Im <lambda| X |phi>: Im(conj(l0) a1) + Im(conj(l1) a0)
-        v += (l0.x * a1.y - l0.y * a1.x) + (l1.x * a0.y - l1.y * a0.x);
+        pv[q++] = (l0.x * a1.y - l0.y * a1.x) + (l1.x * a0.y - l1.y * a0.x);
         apply2<T>(ud, a[j], a[j1]);
         apply2<T>(ud, l[j], l[j1]);
     }
-    return v;
+    return tree_sum<NA / 2, T>(pv);
 }
 
 template <int KB, int NA, typename T>
@@ -411,17 +423,19 @@ template <int R, int NA, typename T>
 VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg, const FDiag &D,
                       int di, uint64_t gb, T *stash_row, int nt, amp_t<T> &phase) {
     if (D.n_rz > 0) {
-        T S = 0, H[R];
+        T p[NA], H[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) H[k] = 0;
+        for (int j = 0; j < NA; ++j) p[j] = l[j].x * a[j].y - l[j].y * a[j].x;
 #pragma unroll
-        for (int j = 0; j < NA; ++j) {
-            const T pj = l[j].x * a[j].y - l[j].y * a[j].x;
-            S += pj;
+        for (int k = 0; k < R; ++k) {  // sum over register index bit k = 0, as a tree
+            T h[NA / 2];
+            int q = 0;
 #pragma unroll
-            for (int k = 0; k < R; ++k)
-                if (!((j >> k) & 1)) H[k] += pj;
+            for (int j = 0; j < NA; ++j)
+                if (!((j >> k) & 1)) h[q++] = p[j];
+            H[k] = tree_sum<NA / 2, T>(h);
         }
+        const T S = tree_sum<NA, T>(p);
         const int i0 = D.item0 - pg.item_base;
         T v[8];
 #pragma unroll
