@@ -988,7 +988,7 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
     for (int b0 = 0; b0 < CPT; b0 += BCH) {
         uint32_t t0, sw[BA];
         uint64_t gch[BCH];
-        A mine[BA], out[BA];
+        A mine[BA], out[BA], delta[BA];  // delta: this pass's contribution to lambda
 #pragma unroll
         for (int i = 0; i < BCH; ++i) {
             const int c = tid + NT * (b0 + i);
@@ -1009,6 +1009,7 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
                 sw[i * IO::CA + e] = swz<AB>(tc + e);
                 mine[i * IO::CA + e] = tile[sw[i * IO::CA + e]];
                 out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : u.a[e];
+                delta[i * IO::CA + e] = mk<T>((T)0, (T)0);
             }
         }
         for (int g = 0; g < tb.ng; ++g) {
@@ -1049,11 +1050,13 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
                 for (int k = 0; k < BA; ++k) f[k] = U[k];
             }
 #pragma unroll
-            for (int k = 0; k < BA; ++k) {
-                const A d = cmul<T>(f[k], tile[sw[k] ^ xs]);
-                out[k] = cadd<T>(out[k], d);
-                run += mine[k].x * d.x + mine[k].y * d.y;
-            }
+            for (int k = 0; k < BA; ++k) delta[k] = cfma<T>(f[k], tile[sw[k] ^ xs], delta[k]);
+        }
+        // energy part of this pass: Re <psi|delta>, once per amplitude instead of per group
+#pragma unroll
+        for (int k = 0; k < BA; ++k) {
+            run += mine[k].x * delta[k].x + mine[k].y * delta[k].y;
+            out[k] = cadd<T>(out[k], delta[k]);
         }
 #pragma unroll
         for (int i = 0; i < BCH; ++i) {
