@@ -36,9 +36,9 @@ METRIC = "adjoint gradients/s at n=30,P=600"
 # streams whole states, so traffic scales with 2^n.  Reset an entry to None whenever
 # its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    "adj_fused": None,  # changed since its capture
+    "adj_fused": (1.084256e9 + 1.014773e9) / 2**26,
     "fwd_fused": (0.54030592e9 + 0.48089984e9) / 2**26,
-    "ham_fused": None,  # changed since its capture
+    "ham_fused": (1.148753e9 + 0.478210304e9) / 2**26,
 }
 UNIT = "gradients/s"
 
@@ -285,6 +285,8 @@ def run_ours(args, rank, world, dist):
     extra = {}
     if not args.no_batch:
         extra["batched"] = batched_rate(args, rank, world, dist)
+    if rank == 0 and not args.no_extra and args.dtype == "c64":
+        extra["c64_vs_c128"] = precision_check(w, g_d, e_val)
     if rank == 0 and not args.no_extra:
         extra["controlled"] = controlled_rate()
         extra["non_hermitian"] = non_hermitian_rate()
@@ -303,11 +305,36 @@ def run_ours(args, rank, world, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic (seeded; no dataset)", "config": _config(args, w, {"plan": plan}),
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
-            "kernel_families": per_family, "energy": e_val}
+            "kernel_families": per_family, "energy": e_val,
+            "amplitude_updates": amplitude_updates(w, S, value, peak)}
     if cpu:
         line["cpu_baseline"] = cpu
     line.update(extra)
     return line
+
+
+def amplitude_updates(w, S, grads_per_s, hbm_peak):
+    """Amplitude updates per second, (G + 2G) 2^n per gradient (G gate applications forward,
+    two states un-applied per gate in reverse), against the rate the HBM roofline allows a
+    one-gate-per-pass schedule (each update reads and writes one amplitude)."""
+    amp_bytes = S >> w.n
+    ups = 3 * w.n_gates * (1 << w.n) * grads_per_s
+    roof = hbm_peak * 1e9 / (2 * amp_bytes)
+    return {"per_s": ups, "unfused_hbm_roofline_per_s": roof, "ratio_to_unfused_roofline": round(ups / roof, 3)}
+
+
+def precision_check(w, g_c64_dev, e_c64):
+    """The complex64 gradient of the timed run against one complex128 evaluation of the same
+    workload on the GPU (FP64 amplitudes; that path matches the oracle to 1e-10 in the
+    tests): max-abs and norm-wise relative differences."""
+    from paper_2009_02823_gb300 import Circuit
+    g64 = g_c64_dev.cpu().numpy()
+    with Circuit(w.n, w.gates, w.n_params, "c128") as c:
+        c.set_hamiltonian(w.terms)
+        e128, g128 = c.energy_and_gradient(w.theta)
+    diff = np.abs(g64 - g128)
+    return {"max_abs_grad_err": float(diff.max()), "rel_grad_err": float(diff.max() / np.abs(g128).max()),
+            "energy_err": abs(e_c64 - e128), "energy_c128": e128}
 
 
 def batched_rate(args, rank=0, world=1, dist=None):
