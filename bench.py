@@ -646,7 +646,9 @@ def run_reference(args, rank):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / max(args.steps, 1), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic (seeded; no dataset)", "config": _config(args, w),
+            "data": "synthetic (seeded; no dataset)",
+            "config": _config(args, w, {"amplitudes": "c128 (CPU oracle, one gate at a time)",
+                                        "parallelism": "host cores (rank 0 only)"}),
             "cpu_baseline": cpu, "cores": oracle.threads(),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -1,5 +1,6 @@
 // Plan records of the tile-fused sweeps, shared by the host planner (engine.cu) and
-// the kernels (k_fused.cu).
+// the kernels (fused_kernels.cuh, instantiated in k_fused_c64.cu, k_fused_c128.cu,
+// k_fused_ham.cu and batch.cu).
 //
 // A tile is 2^K amplitudes: the L lowest qubits (contiguous 128-byte rows of the
 // state) plus K-L chosen "high" qubits; the other n-K qubits are fixed per tile.  One
