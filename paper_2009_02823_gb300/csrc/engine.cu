@@ -297,33 +297,49 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                 FDiag d;
                 std::memset(&d, 0, sizeof d);
                 d.item0 = (int)pl.items.size();
-                for (int pass_rz = 1; pass_rz >= 0; --pass_rz)  // RZ items first
-                    for (int i : it.gates) {
-                        const vqg_gate &g = gates[i];
-                        if ((g.kind == VQG_RZ) != (pass_rz == 1)) continue;
-                        FDItem x;
-                        std::memset(&x, 0, sizeof x);
-                        x.gate = i;
-                        x.lslot = -1;
-                        if (g.kind == VQG_RZ) {
-                            const int k = regbit(g.q0);
-                            if (k >= 0) x.type = DI_RZ_REG, x.k0 = (int16_t)k;
-                            else x.type = DI_RZ_THR, x.g0 = 1ull << g.q0, st.has_phase = 1;
-                            if (reverse) {
-                                x.lslot = n_lslots++;
-                                pl.slot_map.push_back(slot_base[i]);
-                                st.row_slot[rows++] = (int16_t)x.lslot;
-                            }
-                            d.n_rz++;
-                        } else {
-                            const int ka = regbit(g.q0), kb = regbit(g.q1);
-                            if (ka >= 0 && kb >= 0) x.type = DI_CZ_RR, x.k0 = (int16_t)ka, x.k1 = (int16_t)kb;
-                            else if (ka >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)ka, x.g0 = 1ull << g.q1;
-                            else if (kb >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)kb, x.g0 = 1ull << g.q0;
-                            else x.type = DI_CZ_TT, x.g0 = 1ull << g.q0, x.g1 = 1ull << g.q1, st.has_phase = 1;
-                        }
-                        pl.items.push_back(x);
+                std::vector<FDItem> xs;
+                for (int i : it.gates) {
+                    const vqg_gate &g = gates[i];
+                    FDItem x;
+                    std::memset(&x, 0, sizeof x);
+                    x.gate = i;
+                    x.lslot = -1;
+                    if (g.kind == VQG_RZ) {
+                        const int k = regbit(g.q0);
+                        if (k >= 0) x.type = DI_RZ_REG, x.k0 = (int16_t)k;
+                        else x.type = DI_RZ_THR, x.g0 = 1ull << g.q0, st.has_phase = 1;
+                    } else {
+                        const int ka = regbit(g.q0), kb = regbit(g.q1);
+                        if (ka >= 0 && kb >= 0) x.type = DI_CZ_RR, x.k0 = (int16_t)ka, x.k1 = (int16_t)kb;
+                        else if (ka >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)ka, x.g0 = 1ull << g.q1;
+                        else if (kb >= 0) x.type = DI_CZ_RT, x.k0 = (int16_t)kb, x.g0 = 1ull << g.q0;
+                        else x.type = DI_CZ_TT, x.g0 = 1ull << g.q0, x.g1 = 1ull << g.q1, st.has_phase = 1;
                     }
+                    xs.push_back(x);
+                }
+                // RZ_REG, RZ_THR, CZ_RT / CZ_TT, CZ_RR (stable: gate order within a class)
+                auto cls = [](int t) { return t == DI_RZ_REG ? 0 : t == DI_RZ_THR ? 1 : t == DI_CZ_RR ? 3 : 2; };
+                std::stable_sort(xs.begin(), xs.end(),
+                                 [&](const FDItem &a, const FDItem &b) { return cls(a.type) < cls(b.type); });
+                int thr0 = -1, n_thr = 0;
+                for (size_t q = 0; q < xs.size(); ++q) {
+                    FDItem &x = xs[q];
+                    if (x.type == DI_RZ_REG || x.type == DI_RZ_THR) {
+                        if (reverse) {  // reduction slots and stash rows follow the item order
+                            x.lslot = n_lslots++;
+                            pl.slot_map.push_back(slot_base[x.gate]);
+                            st.row_slot[rows++] = (int16_t)x.lslot;
+                        }
+                        d.n_rz++;
+                    }
+                    if (cls(x.type) == 1 || cls(x.type) == 2) {
+                        if (thr0 < 0) thr0 = (int)q;
+                        ++n_thr;
+                    }
+                    pl.items.push_back(x);
+                }
+                d.thr0 = (int16_t)(thr0 < 0 ? 0 : thr0);
+                d.n_thr = (int16_t)n_thr;
                 d.n_item = (int)pl.items.size() - d.item0;
                 pl.diags.push_back(d);
             }
@@ -437,9 +453,13 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                         const FDiag &D = pl.diags[d0 + op.diag];
                         if (D.n_rz > kMaxDiagRz || D.n_rz > D.n_item) return fail("block RZ count", o, D.n_rz);
                         if (D.item0 < 0 || D.item0 + D.n_item > (int)pl.items.size()) return fail("item range", o, D.item0);
+                        if (D.thr0 < 0 || D.n_thr < 0 || D.thr0 + D.n_thr > D.n_item) return fail("thread items", o, D.thr0);
                         for (int i = D.item0; i < D.item0 + D.n_item; ++i) {
                             const FDItem &x = pl.items[i];
                             const bool rz = x.type == DI_RZ_REG || x.type == DI_RZ_THR;
+                            const bool thr = x.type == DI_RZ_THR || x.type == DI_CZ_RT || x.type == DI_CZ_TT;
+                            const int rel = i - D.item0;
+                            if (thr != (rel >= D.thr0 && rel < D.thr0 + D.n_thr)) return fail("thread item range", i, x.type);
                             if ((i - D.item0 < D.n_rz) != rz) return fail("item order", i, x.type);
                             if (x.type < DI_RZ_REG || x.type > DI_CZ_TT) return fail("item type", i, x.type);
                             const bool k0 = x.type == DI_RZ_REG || x.type == DI_CZ_RR || x.type == DI_CZ_RT;

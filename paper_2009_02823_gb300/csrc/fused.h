@@ -104,10 +104,13 @@ struct FOp {          // 16 bytes: one shared-memory vector load
     int32_t gate;     // gate index (matrix source); OP_DIAG: -1
 };
 
+// Items of a block are ordered RZ on register bits, RZ on thread-level qubits, CZ with
+// a thread-level qubit (CZ_RT, CZ_TT), CZ between register bits: the RZ items lead (they
+// carry reverse reductions) and the per-thread factor only visits [thr0, thr0 + n_thr).
 struct FDiag {
     int32_t item0, n_item;  // items (global index)
     int32_t n_rz;           // leading RZ items
-    int32_t pad;
+    int16_t thr0, n_thr;    // thread-level items, relative to item0
 };
 
 struct FDItem {

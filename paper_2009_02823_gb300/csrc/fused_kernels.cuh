@@ -167,7 +167,8 @@ struct Prog {
         static constexpr size_t o_prm = align8(o_it + sizeof(FDItem) * C::items);
         static constexpr size_t o_iph = align8(o_prm + (size_t)AB * 4 * C::ops);
         static constexpr size_t o_tab = align8(o_iph + (size_t)AB * 2 * C::items);
-        static constexpr size_t bytes = align8(o_tab + (size_t)AB * (1 << R) * C::diags);
+        static constexpr size_t o_ti = align8(o_tab + (size_t)AB * (1 << R) * C::diags);
+        static constexpr size_t bytes = align8(o_ti + sizeof(uint32_t) * C::items);
     };
 
     FStage *st;
@@ -175,6 +176,7 @@ struct Prog {
     FDiag *dg;
     FDItem *it;
     amp_t<T> *prm, *iph, *tab;
+    uint32_t *ti;  // per item, packed for the per-thread factor: type | q0 << 8 | q1 << 16 | k0 << 24
     int op_base, item_base;
 
     template <typename C = FullCaps>
@@ -187,6 +189,7 @@ struct Prog {
         prm = reinterpret_cast<amp_t<T> *>(p + Lo::o_prm);
         iph = reinterpret_cast<amp_t<T> *>(p + Lo::o_iph);
         tab = reinterpret_cast<amp_t<T> *>(p + Lo::o_tab);
+        ti = reinterpret_cast<uint32_t *>(p + Lo::o_ti);
     }
 };
 
@@ -227,6 +230,10 @@ VQG_DEV void load_prog(Prog<T, R> &pg, int s0, int ns, int d0, int nd, const FSt
     }
     for (int i = tid; i < n_it; i += nt) {
         const FDItem x = items[it0 + i];
+        // qubit of a single-bit mask (thread-level qubits of RZ_THR / CZ_RT / CZ_TT)
+        const uint32_t q0 = x.g0 ? (uint32_t)__ffsll((long long)x.g0) - 1u : 0u;
+        const uint32_t q1 = x.g1 ? (uint32_t)__ffsll((long long)x.g1) - 1u : 0u;
+        pg.ti[i] = (uint32_t)x.type | (q0 << 8) | (q1 << 16) | ((uint32_t)(x.k0 & 0xff) << 24);
         if (x.type != DI_RZ_REG && x.type != DI_RZ_THR) continue;
         const T *m = mats + 8 * (size_t)x.gate;
         const T sg = reverse ? (T)-1 : (T)1;
@@ -255,14 +262,16 @@ template <typename T, int R>
 VQG_DEV void diag_thread(const Prog<T, R> &pg, const FDiag &D, uint64_t gb, amp_t<T> &tau, uint32_t &c) {
     tau = mk<T>((T)1, (T)0);
     c = 0;
-    const int i0 = D.item0 - pg.item_base;
-    for (int i = i0; i < i0 + D.n_item; ++i) {
-        const FDItem &x = pg.it[i];
-        if (x.type == DI_RZ_THR) tau = cmul<T>((gb & x.g0) ? pg.iph[2 * i + 1] : pg.iph[2 * i], tau);
-        else if (x.type == DI_CZ_TT) {
-            if ((gb & x.g0) && (gb & x.g1)) tau = neg<T>(tau);
-        } else if (x.type == DI_CZ_RT) {
-            if (gb & x.g0) c ^= 1u << x.k0;
+    const int i0 = D.item0 - pg.item_base + D.thr0;  // thread-level items only
+    for (int i = i0; i < i0 + D.n_thr; ++i) {
+        const uint32_t p = pg.ti[i];
+        const uint32_t type = p & 0xffu, b0 = (uint32_t)(gb >> ((p >> 8) & 0xffu)) & 1u;
+        if (type == DI_RZ_THR) {
+            tau = cmul<T>(b0 ? pg.iph[2 * i + 1] : pg.iph[2 * i], tau);
+        } else if (type == DI_CZ_TT) {
+            if (b0 & (uint32_t)(gb >> ((p >> 16) & 0xffu))) tau = neg<T>(tau);
+        } else {  // DI_CZ_RT
+            if (b0) c ^= 1u << (p >> 24);
         }
     }
 }
