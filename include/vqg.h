@@ -123,7 +123,11 @@ int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *x_mask,
 int vqg_set_stream(vqg_circuit *c, void *stream);
 
 /* E(theta): forward sweep (Algorithm 1's forward sweep) then <psi|H|psi> with FP64 reduction.
- * theta: host array of n_params doubles.  energy: host double.  Blocks until done. */
+ * theta: host array of n_params doubles.  energy: host double.  Blocks until done.
+ * H is the Pauli sum or tensor-product operator set last; a non-Hermitian operator
+ * (vqg_set_operator with imaginary coefficients) is refused with VQG_ERR_STATE; no
+ * operator at all is VQG_ERR_STATE too.  The gradient calls below behave the same way;
+ * with options.autotune the first of them blocks while candidate schedules are timed. */
 int vqg_energy(vqg_circuit *c, const double *theta, double *energy);
 
 /* E(theta) and dE/dtheta (Algorithm 1 with App. B.1/B.2): forward sweep, lambda = H psi
