@@ -89,3 +89,25 @@ def test_cfg5_adam_full_size():
         opt.step()
         energies.append(float(e))
     assert np.all(np.isfinite(energies)) and energies[-1] < energies[0]
+
+
+@pytest.mark.parametrize("n,dtype", [(33, "c64"), (31, "c128")])
+def test_largest_states_closed_form(n, dtype):
+    """The largest states the 280 GB device holds with room to spare (64 GiB per state at
+    33 qubits complex64, 32 GiB at 31 qubits complex128): an RY layer under Hadamard^{(x)n}
+    against the closed form E = prod_q f(t_q), f = (sin t + cos t)/sqrt2, and every gradient
+    entry f'(t_q) prod_{r != q} f(t_r)."""
+    from paper_2009_02823_gb300 import Circuit
+    from tests.tolerances import assert_parity
+    rng = np.random.default_rng(n)
+    t = np.pi / 4 + 0.15 * rng.normal(size=n)
+    gates = [("RY", q, -1, (q, -1, -1)) for q in range(n)]
+    f = (np.sin(t) + np.cos(t)) / np.sqrt(2)
+    df = (np.cos(t) - np.sin(t)) / np.sqrt(2)
+    e_ref = float(np.prod(f))
+    g_ref = np.array([df[q] * np.prod(np.delete(f, q)) for q in range(n)])
+    had = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    with Circuit(n, gates, n, dtype, max_checkpoint_mib=1) as c:
+        c.set_product_operator([(1.0, [had] * n)])
+        e, g = c.energy_and_gradient(t)
+        assert_parity(dtype, e, g, e_ref, g_ref, f"n={n}")
