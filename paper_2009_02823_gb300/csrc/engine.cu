@@ -175,8 +175,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             if (!isreg[p]) isreg[p] = 1, regs.push_back(p);
         std::vector<char> inS(n, 0);
         for (int p : regs) inS[tm.qubit_of[p]] = 1;
-        greedy(gates, uns, inS, n, kMaxPassOps,
-               reverse ? (dbl ? kMaxStageRowsDbl : kMaxStageRows) : kMaxPassSlots, applied, left);
+        greedy(gates, uns, inS, n, kMaxPassOps, reverse ? kMaxStageValues : kMaxPassSlots, applied, left);
         const int NL = dbl ? 3 : 4, MOD = dbl ? 3 : 4;
         std::vector<int> thr;
         std::vector<char> used(K, 0);
@@ -245,8 +244,26 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
             }
         }
         st.op0 = (int)pl.ops.size();
-        int rows = 0;
+        // Reverse: the stash holds rowcap values per thread; when the next op's values do
+        // not fit, a flush op reduces the rows written so far (their local slots are
+        // contiguous from seg_first) and the rows restart at 0.
+        const int rowcap = dbl ? kMaxStageRowsDbl : kMaxStageRows;
+        int rows = 0, seg_first = n_lslots;
         for (const StageItem &it : out) {
+            const int need = it.diag ? it.n_rz : red_values(gates[it.gates[0]].kind);
+            if (reverse && need > 0 && rows + need > rowcap) {
+                FOp f;
+                std::memset(&f, 0, sizeof f);
+                f.type = OP_FLUSH;
+                f.gate = -1;
+                f.cq = -1;
+                f.diag = -1;
+                f.lslot = (int16_t)seg_first;
+                f.row = (int8_t)rows;
+                pl.ops.push_back(f);
+                seg_first = n_lslots;
+                rows = 0;
+            }
             FOp op;
             std::memset(&op, 0, sizeof op);
             op.lslot = -1;
@@ -360,6 +377,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
 std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
     char buf[256];
     const int K = pl.K, L = pl.L;
+    const int rowcap = dbl ? kMaxStageRowsDbl : kMaxStageRows;
     auto fail = [&](const char *what, int a, int b) {
         snprintf(buf, sizeof buf, "plan check failed: %s (%d, %d)", what, a, b);
         return std::string(buf);
@@ -420,10 +438,10 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                 for (int k = 0; k < K - R; ++k)
                     if (st.thr_q[k] < 0 || st.thr_q[k] >= n) return fail("thread qubit", s, st.thr_q[k]);
                 if (dir) {
-                    if (st.n_rows < 0 || st.n_rows > (dbl ? kMaxStageRowsDbl : kMaxStageRows))
-                        return fail("stage rows", s, st.n_rows);
+                    if (st.n_rows < 0 || st.n_rows > rowcap) return fail("stage rows", s, st.n_rows);
                     for (int r = 0; r < st.n_rows; ++r)
-                        if (st.row_slot[r] < 0 || st.row_slot[r] >= p.n_lslots) return fail("row slot", s, st.row_slot[r]);
+                        if (st.row_slot[r] < 0 || st.row_slot[r] >= p.n_lslots || st.row_slot[r] != st.row_slot[0] + r)
+                            return fail("row slot", s, st.row_slot[r]);
                 }
                 for (int o = st.op0; o < st.op0 + st.n_op; ++o) {
                     const FOp &op = pl.ops[o];
@@ -437,15 +455,33 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
                         return fail("control qubit", o, op.cq);
                     if (op.type == OP_PH && !op.rm0 && (op.cq < -1 || op.cq >= n)) return fail("control qubit", o, op.cq);
                     if (!ctl_op && (op.rm0 || op.cq != -1)) return fail("stray control", o, op.cq);
-                    if (op.type != OP_DIAG && (op.gate < 0)) return fail("gate index", o, op.gate);
-                    if (dir && op.lslot >= 0) {
+                    if (op.type != OP_DIAG && op.type != OP_FLUSH && (op.gate < 0)) return fail("gate index", o, op.gate);
+                    if (op.type == OP_FLUSH) {
+                        if (!dir) return fail("flush in a forward stage", o, 0);
+                        if (op.row < 1 || op.row > rowcap) return fail("flush rows", o, op.row);
+                        if (op.lslot < 0 || op.lslot + op.row > p.n_lslots) return fail("flush slots", o, op.lslot);
+                    }
+                    // the stash segment this op writes into ends at the next flush or the stage end
+                    int seg_rows = st.n_rows, seg_first = st.n_rows ? st.row_slot[0] : 0;
+                    if (dir) {
+                        for (int f = o; f < st.op0 + st.n_op; ++f)
+                            if (f > o && pl.ops[f].type == OP_FLUSH) {
+                                seg_rows = pl.ops[f].row;
+                                seg_first = pl.ops[f].lslot;
+                                break;
+                            }
+                    }
+                    if (dir && op.lslot >= 0 && op.type != OP_FLUSH) {
                         const int nv = op.type == OP_U3 ? 8 : 1;
                         if (op.lslot + nv > p.n_lslots) return fail("local slot", o, op.lslot);
-                        if (op.row < 0 || op.row + nv > st.n_rows) return fail("stash row", o, op.row);
+                        if (op.row < 0 || op.row + nv > seg_rows) return fail("stash row", o, op.row);
+                        if (op.lslot != seg_first + op.row) return fail("slot of stash row", o, op.lslot);
                     }
                     if (dir && op.type == OP_DIAG) {
                         const FDiag &D = pl.diags[p.rdiag0 + op.diag];
-                        if (op.row < 0 || op.row + D.n_rz > st.n_rows) return fail("diag stash row", o, op.row);
+                        if (op.row < 0 || op.row + D.n_rz > seg_rows) return fail("diag stash row", o, op.row);
+                        for (int r = 0; r < D.n_rz; ++r)
+                            if (pl.items[D.item0 + r].lslot != seg_first + op.row + r) return fail("slot of diag row", o, r);
                     }
                     if (op.type == OP_DIAG) {
                         const int d0 = dir ? p.rdiag0 : p.diag0, nd = dir ? p.n_rdiag : p.n_diag;

@@ -28,6 +28,7 @@ constexpr int kMaxDiagRz = 8;        // RZ gates per diagonal block
 constexpr int kMaxDiagCz = 16;       // CZ gates per diagonal block
 constexpr int kMaxStageRows = 16;    // reverse reduction values per register stage (complex64)
 constexpr int kMaxStageRowsDbl = 8;  // the same for complex128 (FP64 stash)
+constexpr int kMaxStageValues = 64;  // reverse reduction values per register stage (stash flushed)
 constexpr int kMaxHamGroups = 256;   // groups per Hamiltonian pass
 constexpr int kMaxHamTerms = 1024;   // terms per Hamiltonian pass
 
@@ -58,7 +59,11 @@ enum FOpType : int16_t {
     OP_CRY = 6,
     OP_CRZ = 7,
     OP_PH = 8,    // phase gate (uncontrolled: PHASE; controlled: CPHASE)
-    OP_LAST = OP_PH
+    // reverse only: reduce the stash rows written so far in this stage (row = count) into
+    // local slots lslot .. lslot + row - 1, so that a stage can carry more reduction values
+    // than the stash has rows without a new gather/scatter
+    OP_FLUSH = 9,
+    OP_LAST = OP_FLUSH
 };
 
 // Items of a diagonal block.  RZ items come first (they carry reverse reductions).

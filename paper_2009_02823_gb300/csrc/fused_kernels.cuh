@@ -643,36 +643,37 @@ VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> 
     __syncthreads();
 }
 
-// Reduce a stage's stash rows (per-thread FP32 partials) into the per-slot FP64
-// accumulators: one warp per row, lanes sum NT/32 partials each, then the 32-lane tree;
-// fixed order, so results are reproducible.
+// Reduce stash rows (per-thread partials) into the per-slot FP64 accumulators: row r goes
+// to slot first + r.  One warp per row, lanes sum NT/32 partials each (16-byte loads
+// where NT allows), then the 32-lane tree; fixed order, so results are reproducible.
 template <typename T, int NT>
-VQG_DEV void reduce_stash(const T *stash, const FStage &st, double *acc, int tid) {
+VQG_DEV void reduce_rows(const T *stash, int first, int count, double *acc, int tid) {
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int V = 16 / sizeof(T);  // values per 16-byte load
-    if constexpr (NT % (32 * V) != 0) {
-        for (int r = warp; r < st.n_rows; r += NT / 32) {
-            T v = 0;
-            for (int i = lane; i < NT; i += 32) v += stash[r * NT + i];
-            v = warp_tree<T>(v);
-            if (lane == 0) acc[st.row_slot[r]] += (double)v;
-        }
-        return;
-    }
-    for (int r = warp; r < st.n_rows; r += NT / 32) {
+    for (int r = warp; r < count; r += NT / 32) {
         T v = 0;
+        if constexpr (NT % (32 * V) != 0) {
+            for (int i = lane; i < NT; i += 32) v += stash[r * NT + i];
+        } else {
 #pragma unroll
-        for (int i = lane * V; i < NT; i += 32 * V) {
-            const float4 q = *reinterpret_cast<const float4 *>(stash + r * NT + i);
-            if constexpr (sizeof(T) == 4) v += (q.x + q.y) + (q.z + q.w);
-            else {
-                const double2 d = *reinterpret_cast<const double2 *>(&q);
-                v += d.x + d.y;
+            for (int i = lane * V; i < NT; i += 32 * V) {
+                const float4 q = *reinterpret_cast<const float4 *>(stash + r * NT + i);
+                if constexpr (sizeof(T) == 4) v += (q.x + q.y) + (q.z + q.w);
+                else {
+                    const double2 d = *reinterpret_cast<const double2 *>(&q);
+                    v += d.x + d.y;
+                }
             }
         }
         v = warp_tree<T>(v);
-        if (lane == 0) acc[st.row_slot[r]] += (double)v;
+        if (lane == 0) acc[first + r] += (double)v;
     }
+}
+
+// The rows of a stage's last stash segment (their local slots are contiguous).
+template <typename T, int NT>
+VQG_DEV void reduce_stash(const T *stash, const FStage &st, double *acc, int tid) {
+    reduce_rows<T, NT>(stash, st.row_slot[0], st.n_rows, acc, tid);
 }
 
 template <typename T> constexpr int stash_rows() { return sizeof(T) == 4 ? kMaxStageRows : kMaxStageRowsDbl; }
@@ -760,6 +761,11 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             }
             case OP_DIAG:
                 rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, stash + op.row * NT + tid, NT, phase);
+                break;
+            case OP_FLUSH:  // uniform: every thread runs the same op list
+                __syncthreads();
+                reduce_rows<T, NT>(stash, op.lslot, op.row, acc, tid);
+                __syncthreads();
                 break;
             default:
                 break;
