@@ -83,9 +83,12 @@ typedef struct vqg_gate {
 typedef struct vqg_options {
     int32_t fusion;              /* 1: apply runs of gates per tile pass (default);
                                     0: one kernel per gate                                  */
-    int32_t checkpoint_interval; /* forward states stored every this many gates and used to
-                                    restart phi in the reverse sweep; 0 = automatic (64 for
-                                    complex64, none for complex128), -1 = none              */
+    int32_t checkpoint_interval; /* forward states stored every this many gates (fused: at
+                                    the first pass boundary after that many gates) and used
+                                    to restart phi in the reverse sweep; 0 = automatic
+                                    (complex64: every fused pass boundary, or every 64 gates
+                                    unfused; complex128: none), -1 = none; as many as fit
+                                    in free device memory (see max_checkpoint_mib)         */
     int32_t tile_qubits;         /* qubits per fused tile; 0 = built-in table: n - 8 clamped
                                     to [10, 13] (complex64) or [10, 12] (complex128)        */
     int32_t use_graph;           /* 1: replay the launch sequence from a CUDA graph          */
@@ -151,8 +154,10 @@ int vqg_energy_and_gradient_device(vqg_circuit *c, const double *theta_dev, doub
 int vqg_gradient_parameter_shift(vqg_circuit *c, const double *theta, int first_gate,
                                  int last_gate, double *grad);
 
-/* Copy |psi> of the last forward sweep (complex64 or complex128 per dtype) into host
- * memory `out` of `bytes` >= 2^n * amplitude size.  Blocks until done. */
+/* Copy the state buffer (complex64 or complex128 per dtype) into host memory `out` of
+ * `bytes` >= 2^n * amplitude size.  Blocks until done.  After vqg_energy it holds
+ * |psi> = U(theta)|in>; after a gradient call it holds reverse-sweep scratch (the reverse
+ * sweep un-applies the gates in place), so call vqg_energy first to read |psi>. */
 int vqg_get_state(vqg_circuit *c, void *out, size_t bytes);
 
 /* Timing of the kernels of the last call, for measurement: fills up to max_entries

@@ -275,10 +275,13 @@ int Circuit::init(int n_, const vqg_gate *gates_, int G_, int P_, int dtype_, co
 // already held (from an earlier schedule of the same circuit) are reused; surplus ones
 // are released.
 int Circuit::plan_checkpoints() {
-    int interval = opt.checkpoint_interval;
-    if (interval == 0) interval = dbl ? -1 : 64;
-    ckpt_pos.clear();
     const bool fused = opt.fusion && plan_ok;
+    int interval = opt.checkpoint_interval;
+    // automatic: complex64 stores the output of every fused pass (each reverse pass then
+    // restarts phi from exact forward data, and no reverse pass has to store phi) or every
+    // 64 gates unfused; complex128 stores none
+    if (interval == 0) interval = dbl ? -1 : (fused ? 1 : 64);
+    ckpt_pos.clear();
     std::vector<int> want;
     if (interval >= 0 && G >= 2) {
         if (fused) want = fused_checkpoint_passes(interval);

@@ -30,7 +30,7 @@ namespace vqg {
 #define VQG_REV_ARGS                                                                             \
     int K, int R, const void *phi_src, void *phi_dst, void *lam, const FPass *passes, int pi,     \
         const FStage *st, const FOp *ops, const FDiag *dg, const FDItem *it, const int *slot_map, \
-        const void *mats, uint64_t n_tiles, double *partials, int nb, cudaStream_t s
+        const void *mats, uint64_t n_tiles, double *partials, int nb, int wmask, cudaStream_t s
 bool launch_fused_fwd_c64(VQG_FWD_ARGS);
 bool launch_fused_fwd_c128(VQG_FWD_ARGS);
 bool launch_fused_rev_c64(VQG_REV_ARGS);
@@ -911,10 +911,14 @@ int Circuit::issue_reverse_fused() {
     for (int j = (int)pl->passes.size() - 1; j >= 0; --j) {
         const int k = pl->ckpt_of_pass[j];
         const void *src = k >= 0 ? ckpt_buf[k] : psi;  // restart phi from the stored state
+        // phi_j is read only if the next reverse pass does not restart from a checkpoint;
+        // nothing reads phi or lambda after the last reverse pass
+        const bool write_phi = j > 0 && pl->ckpt_of_pass[j - 1] < 0, write_lam = j > 0;
         prof_begin(FAM_ADJ_FUSED);
         (dbl ? launch_fused_rev_c128 : launch_fused_rev_c64)(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j,
                                                              pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
-                                                             pl->d_slot_map, mats, pl->n_tiles, gpart, nb, stream);
+                                                             pl->d_slot_map, mats, pl->n_tiles, gpart, nb,
+                                                             (write_phi ? 1 : 0) | (write_lam ? 2 : 0), stream);
         prof_end();
     }
     cudaError_t e = cudaGetLastError();

@@ -685,7 +685,7 @@ template <typename T, int K, int R, bool L2ONLY>
 VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, const Prog<T, R> &pg,
                       int n_stage, uint64_t base, const amp_t<T> *__restrict__ phi_src,
                       amp_t<T> *__restrict__ phi_dst, amp_t<T> *__restrict__ lam, double *acc,
-                      T *stash, int tid) {
+                      T *stash, int tid, bool write_phi = true, bool write_lam = true) {
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
     constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
@@ -794,8 +794,8 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             __syncthreads();
         }
     }
-    IO::template store<NT>(tphi, phi_dst, base, row_off, tid);
-    IO::template store<NT>(tlam, lam, base, row_off, tid);
+    if (write_phi) IO::template store<NT>(tphi, phi_dst, base, row_off, tid);
+    if (write_lam) IO::template store<NT>(tlam, lam, base, row_off, tid);
     __syncthreads();
 }
 
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(1 << (K - R))
                 const FStage *__restrict__ stages, const FOp *__restrict__ ops,
                 const FDiag *__restrict__ diags, const FDItem *__restrict__ items,
                 const int *__restrict__ slot_map, const T *__restrict__ mats, uint64_t n_tiles,
-                double *__restrict__ partials, int nb) {
+                double *__restrict__ partials, int nb, int wmask) {
     using A = amp_t<T>;
     using C = RevCfg<T, K, R>;
     constexpr int NT = C::NT, NW = C::NW;
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(1 << (K - R))
             TileIO<T, K>::template prefetch<NT>(lam, next, row_off, tid);
         }
         rev_tile<T, K, R, false>(tphi, tlam, row_off, pg, P.n_rstage, tile_base(ti, P.nontile, P.n_nontile),
-                                 phi_src, phi_dst, lam, acc, stash, tid);
+                                 phi_src, phi_dst, lam, acc, stash, tid, (wmask & 1) != 0, (wmask & 2) != 0);
     }
     __syncthreads();
     for (int i = tid; i < n_ls; i += NT) partials[(size_t)smap[i] * nb + blockIdx.x] = acc[i];

@@ -23,13 +23,13 @@ template <typename T, int K, int R>
 static void rev_t(const void *phi_src, void *phi_dst, void *lam, const FPass *passes, int pi,
                   const FStage *st, const FOp *ops, const FDiag *dg, const FDItem *it,
                   const int *slot_map, const void *mats, uint64_t n_tiles, double *partials, int nb,
-                  cudaStream_t s) {
+                  int wmask, cudaStream_t s) {
     constexpr size_t sm = RevCfg<T, K, R>::smem();
     static bool once = false;
     if (!once) set_smem(k_fused_rev<T, K, R>, sm), once = true;
     k_fused_rev<T, K, R><<<nb, RevCfg<T, K, R>::NT, sm, s>>>(
         (const amp_t<T> *)phi_src, (amp_t<T> *)phi_dst, (amp_t<T> *)lam, passes, pi, st, ops, dg, it,
-        slot_map, (const T *)mats, n_tiles, partials, nb);
+        slot_map, (const T *)mats, n_tiles, partials, nb, wmask);
 }
 
 // Returns false if (K, R) has no instantiation.
@@ -53,10 +53,10 @@ bool launch_fused_fwd_c64(int K, int R, const void *src, void *dst, const FPass 
 bool launch_fused_rev_c64(int K, int R, const void *phi_src, void *phi_dst, void *lam,
                       const FPass *passes, int pi, const FStage *st, const FOp *ops, const FDiag *dg,
                       const FDItem *it, const int *slot_map, const void *mats, uint64_t n_tiles,
-                      double *partials, int nb, cudaStream_t s) {
+                      double *partials, int nb, int wmask, cudaStream_t s) {
 #define VQG_REV(KK, RR) \
     if (K == KK && R == RR) { \
-        rev_t<float, KK, RR>(phi_src, phi_dst, lam, passes, pi, st, ops, dg, it, slot_map, mats, n_tiles, partials, nb, s); \
+        rev_t<float, KK, RR>(phi_src, phi_dst, lam, passes, pi, st, ops, dg, it, slot_map, mats, n_tiles, partials, nb, wmask, s); \
         return true; \
     }
     VQG_REV(10, 3)
