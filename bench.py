@@ -36,9 +36,9 @@ METRIC = "adjoint gradients/s at n=30,P=600"
 # streams whole states, so traffic scales with 2^n.  Reset an entry to None whenever
 # its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    "adj_fused": None,  # changed since its capture
-    "fwd_fused": None,  # changed since its capture
-    "ham_fused": (1.148753e9 + 0.478210304e9) / 2**26,
+    "adj_fused": (1.075564e9 + 0.477504e9) / 2**26,  # a pass that stores lambda only (3 S)
+    "fwd_fused": (0.543695872e9 + 0.480878336e9) / 2**26,
+    "ham_fused": (1.143671e9 + 0.478273536e9) / 2**26,
 }
 UNIT = "gradients/s"
 
@@ -158,8 +158,11 @@ def family_bytes(fam: str, w, S: int, plan: dict) -> float | None:
         return 4.0 * S
     if fam == "fwd_gate":    # read + write psi (CNOT/CZ touch part of it; counted whole)
         return 2.0 * S
-    if fam == "adj_fused":   # per reverse tile pass: read + write phi and lambda
-        return 4.0 * S
+    if fam == "adj_fused":
+        # per reverse tile pass: read phi and lambda; write lambda except after the last
+        # pass; write phi only when the next pass does not restart from a checkpoint
+        P, C = plan.get("reverse_passes", 1), plan.get("checkpoints", 0)
+        return (2.0 * P + (P - 1) + max(P - 1 - C, 0)) * S / max(P, 1)
     if fam == "fwd_fused":   # per forward tile pass: read + write psi
         return 2.0 * S
     if fam == "ham_group":   # read psi, read + write lambda
