@@ -111,3 +111,46 @@ def test_largest_states_closed_form(n, dtype):
         c.set_product_operator([(1.0, [had] * n)])
         e, g = c.energy_and_gradient(t)
         assert_parity(dtype, e, g, e_ref, g_ref, f"n={n}")
+
+
+def _c64_vs_c128(make, tol=1e-4):
+    """Run a full-size evaluation in both precisions (the complex128 path matches the
+    oracle to 1e-10 at sizes the oracle finishes) and compare norm-wise."""
+    out = {}
+    for dtype in ("c64", "c128"):
+        out[dtype] = make(dtype)
+    (e64, g64), (e128, g128) = out["c64"], out["c128"]
+    scale = max(float(np.max(np.abs(g128))), 1e-300)
+    assert abs(e64 - e128) <= tol * max(1.0, abs(e128))
+    assert float(np.max(np.abs(g64 - g128))) / scale <= tol
+
+
+def test_controlled_ring_n26_precisions_agree():
+    """The controlled-rotation ring (CRX on every neighbouring pair, 4 layers) at 26
+    qubits: complex64 against complex128."""
+    from paper_2009_02823_gb300 import Circuit
+    gates, P = W.crx_ring(26, 4)
+    rng = np.random.default_rng(26)
+    theta = rng.uniform(0, 2 * np.pi, P)
+    terms = W.random_paulis(rng, 26, 40, 4)
+
+    def make(dtype):
+        with Circuit(26, gates, P, dtype) as c:
+            c.set_hamiltonian(terms)
+            return c.energy_and_gradient(theta)
+    _c64_vs_c128(make)
+
+
+def test_non_hermitian_n26_precisions_agree():
+    """A complex-coefficient operator on the 26-qubit brickwork circuit: complex64 against
+    complex128 (complex expectation and gradient)."""
+    from paper_2009_02823_gb300 import Circuit
+    w = W.config(3, n=26, layers=4)
+    rng = np.random.default_rng(27)
+    terms = [(complex(c, float(rng.normal())), ops) for c, ops in w.terms]
+
+    def make(dtype):
+        with Circuit(w.n, w.gates, w.n_params, dtype) as c:
+            c.set_operator(terms)
+            return c.expectation_and_gradient(w.theta)
+    _c64_vs_c128(make)
