@@ -60,7 +60,8 @@ def _workload(args):
 
 def _config(args, w, extra=None):
     cfg = {"workload": w.name, "n_qubits": w.n, "n_params": w.n_params, "n_gates": w.n_gates,
-           "hamiltonian_terms": len(w.terms), "amplitudes": f"{args.dtype} (FP64 reductions)",
+           "hamiltonian_terms": len(w.terms), "amplitudes": f"{args.dtype} (FP64 reductions)" if args.dtype == "c64" or args.c128_arith == "fp64"
+           else "c128 storage, float-float tile arithmetic, FP64 reductions",
            "state_bytes": (8 if args.dtype == "c64" else 16) << w.n,
            "l2": "inputs larger than L2 (state vectors >> 129 MB)",
            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
@@ -185,7 +186,7 @@ def run_ours(args, rank, world, dist):
     w = _workload(args)
     S = (8 if args.dtype == "c64" else 16) << w.n
     stream = torch.cuda.Stream()  # every kernel of the step and both timing events go here
-    circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream)
+    circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream, c128_arith=args.c128_arith)
     circ.set_hamiltonian(w.terms)
     theta_h = replica_theta(w.theta, rank)
     theta_d = torch.tensor(theta_h, dtype=torch.float64, device="cuda")
@@ -305,7 +306,8 @@ def run_ours(args, rank, world, dist):
         return None
     line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128-float-float" if args.dtype == "c128" and args.c128_arith == "float-float" else args.dtype,
             "data": "synthetic (seeded; no dataset)", "config": _config(args, w, {"plan": plan}),
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
             "kernel_families": per_family, "energy": e_val,
@@ -663,6 +665,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--c128-arith", default="fp64", choices=["fp64", "float-float"],
+                    help="arithmetic of the complex128 tile passes")
     ap.add_argument("--cfg", type=int, default=3)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--layers", type=int, default=None)

@@ -80,6 +80,16 @@ typedef struct vqg_gate {
 } vqg_gate;
 
 /* Execution options (vqg_default_options fills the defaults). */
+/* Arithmetic of the complex128 tile passes.  Amplitudes are FP64 in memory either way;
+ * reductions (energy, gradient partials) are FP64 either way.
+ *   VQG_C128_FP64:        gate arithmetic in FP64 (bounded by the GPU's FP64 rate).
+ *   VQG_C128_FLOAT_FLOAT: gate arithmetic on pairs of FP32 numbers (hi + lo, about 48
+ *                         significant bits; error-free TwoSum / FMA TwoProduct), rounded
+ *                         to FP64 at every state store.  Relative error per operation
+ *                         below ~2^-44; tile passes only (3 register qubits per stage);
+ *                         the one-kernel-per-gate route (fusion = 0, n < 10) stays FP64. */
+typedef enum { VQG_C128_FP64 = 0, VQG_C128_FLOAT_FLOAT = 1 } vqg_c128_arith;
+
 typedef struct vqg_options {
     int32_t fusion;              /* 1: apply runs of gates per tile pass (default);
                                     0: one kernel per gate                                  */
@@ -97,7 +107,9 @@ typedef struct vqg_options {
     int32_t rev_reg_qubits;      /* qubits held in registers per reverse stage; 0 = default  */
     int32_t autotune;            /* 1: time candidate schedules on the first evaluation and
                                     keep the fastest (see vqg_autotune)                     */
-    int32_t reserved[8];
+    int32_t c128_arith;          /* complex128 tile-pass arithmetic (vqg_c128_arith):
+                                    VQG_C128_FP64 (default) or VQG_C128_FLOAT_FLOAT      */
+    int32_t reserved[7];
 } vqg_options;
 
 typedef struct vqg_circuit vqg_circuit;

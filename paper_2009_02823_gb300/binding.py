@@ -44,7 +44,10 @@ class vqg_options(ctypes.Structure):
                 ("tile_qubits", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("max_checkpoint_mib", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
                 ("rev_reg_qubits", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("c128_arith", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+# vqg_c128_arith: arithmetic of the complex128 tile passes
+C128_ARITH = {"fp64": 0, "float-float": 1}
 
 
 class vqg_plan_info(ctypes.Structure):
@@ -186,7 +189,7 @@ class Circuit:
     def __init__(self, n: int, gates, n_params: int, dtype: str = "c64", *, fusion: bool = True,
                  checkpoint_interval: int = 0, tile_qubits: int = 0, use_graph: bool = False,
                  max_checkpoint_mib: int = 0, fwd_reg_qubits: int = 0, rev_reg_qubits: int = 0,
-                 autotune: bool = False, stream=None):
+                 autotune: bool = False, c128_arith: str = "fp64", stream=None):
         L = lib()
         self.n, self.n_params, self.n_gates = n, n_params, len(gates)
         self.dtype = dtype
@@ -200,6 +203,7 @@ class Circuit:
         opt.fwd_reg_qubits = fwd_reg_qubits
         opt.rev_reg_qubits = rev_reg_qubits
         opt.autotune = int(autotune)
+        opt.c128_arith = C128_ARITH[c128_arith]
         self._gates = gate_array(gates)
         h = ctypes.c_void_p()
         _check(L.vqg_circuit_create(n, self._gates, len(gates), n_params, DTYPE[dtype],
@@ -386,7 +390,7 @@ def reverse_noalloc(n: int, dtype: str, gates, theta, n_params: int, phi_ptr: in
 
 def plan_dry_run(n: int, gates, n_params: int, terms, dtype: str = "c64", *, fusion: bool = True,
                  tile_qubits: int = 0, checkpoint_interval: int = 0, fwd_reg_qubits: int = 0,
-                 rev_reg_qubits: int = 0) -> dict:
+                 rev_reg_qubits: int = 0, c128_arith: str = "fp64") -> dict:
     """Host-only schedule of a circuit + Hamiltonian (vqg_plan_dry_run); no GPU needed."""
     L = lib()
     opt = vqg_options()
@@ -396,6 +400,7 @@ def plan_dry_run(n: int, gates, n_params: int, terms, dtype: str = "c64", *, fus
     opt.checkpoint_interval = checkpoint_interval
     opt.fwd_reg_qubits = fwd_reg_qubits
     opt.rev_reg_qubits = rev_reg_qubits
+    opt.c128_arith = C128_ARITH[c128_arith]
     x, z, c = pauli_masks(terms, n)
     info = vqg_plan_info()
     arr = gate_array(gates)

@@ -192,6 +192,8 @@ extern "C" int vqg_circuit_create(int n_qubits, const vqg_gate *gates, int n_gat
     *out = nullptr;
     int vst = vqg_validate_circuit(n_qubits, gates, n_gates, n_params, dtype);
     if (vst) return vst;
+    if (opt && opt->c128_arith != VQG_C128_FP64 && opt->c128_arith != VQG_C128_FLOAT_FLOAT)
+        return set_error(VQG_ERR_INVALID, "c128_arith %d is not a vqg_c128_arith", opt->c128_arith);
     Circuit *c = new (std::nothrow) Circuit();
     if (!c) return set_error(VQG_ERR_OOM, "host allocation failed");
     int st = c->init(n_qubits, gates, n_gates, n_params, dtype, opt);

@@ -35,15 +35,29 @@ bool launch_fused_fwd_c64(VQG_FWD_ARGS);
 bool launch_fused_fwd_c128(VQG_FWD_ARGS);
 bool launch_fused_rev_c64(VQG_REV_ARGS);
 bool launch_fused_rev_c128(VQG_REV_ARGS);
+bool launch_fused_fwd_df(VQG_FWD_ARGS);
+bool launch_fused_rev_df(VQG_REV_ARGS);
 
 // Compiled (tile qubits, register qubits) variants; every one fits shared memory.
-bool fused_supported(bool dbl, int K, int Rf, int Rr) {
+// ff: complex128 in float-float arithmetic.
+bool fused_supported(bool dbl, int K, int Rf, int Rr, bool ff) {
     if (!dbl) return K >= 10 && K <= 13 && (Rf == 4 || Rf == 5) && (Rr == 4 || (Rr == 3 && K <= 12));
+    if (ff) return K >= 10 && K <= 12 && Rf == 3 && Rr == 3;
     return K >= 10 && K <= 12 && (Rf == 3 || Rf == 4) && (Rr == 3 || (Rr == 2 && K <= 11));
 }
 void launch_fused_ham(bool dbl, int K, const void *psi, void *lam, const HPass *hp, int pi,
                       const HGroup *groups, const HTerm *terms, uint64_t n_tiles, double *partials,
                       int nb, cudaStream_t s);
+void launch_fused_ham_df(int K, const void *psi, void *lam, const HPass *hp, int pi, const HGroup *groups,
+                         const HTerm *terms, uint64_t n_tiles, double *partials, int nb, cudaStream_t s);
+
+bool float_float(bool dbl, const vqg_options &opt) { return dbl && opt.c128_arith == VQG_C128_FLOAT_FLOAT; }
+
+// Forward tile pass in the circuit's arithmetic (complex64, complex128 FP64 or float-float).
+bool launch_fused_fwd(bool dbl, bool ff, VQG_FWD_ARGS) {
+    auto f = !dbl ? launch_fused_fwd_c64 : ff ? launch_fused_fwd_df : launch_fused_fwd_c128;
+    return f(K, R, src, dst, passes, pi, st, ops, dg, it, mats, n_tiles, grid, s);
+}
 
 struct QUse {
     int q;
@@ -566,12 +580,13 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
                         bool single_kernels) {
     err.clear();
     const int G = (int)gates.size();
+    const bool ff = float_float(dbl, opt);
     int K = std::min(n, default_tile_qubits(n, dbl));
     if (opt.tile_qubits > 0) K = std::min(opt.tile_qubits, n);
-    const int Rf = opt.fwd_reg_qubits > 0 ? opt.fwd_reg_qubits : (dbl ? 4 : 5);
+    const int Rf = opt.fwd_reg_qubits > 0 ? opt.fwd_reg_qubits : (ff ? 3 : dbl ? 4 : 5);
     const int Rr = opt.rev_reg_qubits > 0 ? opt.rev_reg_qubits : (dbl ? 3 : 4);
     if (!opt.fusion || G == 0 || K < 10) return nullptr;
-    if (single_kernels ? !fused_supported(dbl, K, Rf, Rr)
+    if (single_kernels ? !fused_supported(dbl, K, Rf, Rr, ff)
                        : (Rf < 1 || Rr < 1 || Rf > kMaxRegBits || Rr > kMaxRegBits || K > 13 ||
                           K - Rf > kMaxThreadBits || K - Rr > kMaxThreadBits)) {
         err = "no compiled fused kernel for this tile / register-qubit choice";
@@ -879,9 +894,8 @@ int Circuit::issue_forward_fused(bool with_ckpt) {
         const int k = with_ckpt ? pl->ckpt_of_pass[j] : -1;
         void *out = k >= 0 ? ckpt_buf[k] : psi;
         prof_begin(FAM_FWD_FUSED);
-        (dbl ? launch_fused_fwd_c128 : launch_fused_fwd_c64)(pl->K, pl->Rf, in, out, pl->d_passes, (int)j,
-                                                             pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
-                                                             mats, pl->n_tiles, pl->grid_fwd, stream);
+        launch_fused_fwd(dbl, float_float(dbl, opt), pl->K, pl->Rf, in, out, pl->d_passes, (int)j, pl->d_stages,
+                         pl->d_ops, pl->d_diags, pl->d_items, mats, pl->n_tiles, pl->grid_fwd, stream);
         prof_end();
         in = out;
     }
@@ -894,8 +908,12 @@ int Circuit::issue_hamiltonian_fused() {
     Plan *pl = plan;
     for (size_t h = 0; h < pl->hp.size(); ++h) {
         prof_begin(FAM_HAM_FUSED);
-        launch_fused_ham(dbl, pl->K, psi, lam, pl->d_hp, (int)h, pl->d_hg, pl->d_ht, pl->n_tiles,
-                         d_partials, nb, stream);
+        if (float_float(dbl, opt))
+            launch_fused_ham_df(pl->K, psi, lam, pl->d_hp, (int)h, pl->d_hg, pl->d_ht, pl->n_tiles, d_partials, nb,
+                                stream);
+        else
+            launch_fused_ham(dbl, pl->K, psi, lam, pl->d_hp, (int)h, pl->d_hg, pl->d_ht, pl->n_tiles,
+                             d_partials, nb, stream);
         prof_end();
     }
     e_used = (int)pl->hp.size();
@@ -915,10 +933,9 @@ int Circuit::issue_reverse_fused() {
         // nothing reads phi or lambda after the last reverse pass
         const bool write_phi = j > 0 && pl->ckpt_of_pass[j - 1] < 0, write_lam = j > 0;
         prof_begin(FAM_ADJ_FUSED);
-        (dbl ? launch_fused_rev_c128 : launch_fused_rev_c64)(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j,
-                                                             pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
-                                                             pl->d_slot_map, mats, pl->n_tiles, gpart, nb,
-                                                             (write_phi ? 1 : 0) | (write_lam ? 2 : 0), stream);
+        auto rev = !dbl ? launch_fused_rev_c64 : float_float(dbl, opt) ? launch_fused_rev_df : launch_fused_rev_c128;
+        rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
+            pl->d_slot_map, mats, pl->n_tiles, gpart, nb, (write_phi ? 1 : 0) | (write_lam ? 2 : 0), stream);
         prof_end();
     }
     cudaError_t e = cudaGetLastError();
@@ -997,6 +1014,8 @@ extern "C" int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates
     vqg_options opt;
     vqg_default_options(&opt);
     if (opt_in) opt = *opt_in;
+    if (opt.c128_arith != VQG_C128_FP64 && opt.c128_arith != VQG_C128_FLOAT_FLOAT)
+        return set_error(VQG_ERR_INVALID, "c128_arith %d is not a vqg_c128_arith", opt.c128_arith);
     const bool dbl = dtype == VQG_C128;
     std::vector<vqg_gate> gv(gates, gates + n_gates);
     std::vector<int> slot_base(std::max(n_gates, 1), 0);

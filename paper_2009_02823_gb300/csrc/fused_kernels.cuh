@@ -20,16 +20,24 @@
 #pragma once
 #include <type_traits>
 
+#include "df.cuh"
 #include "fused.h"
 #include "kernels.h"
 
 namespace vqg {
 
+// Per arithmetic type: row qubits L (one 128-byte row), bytes per amplitude in shared
+// memory, the gate-table element type, and whether global amplitudes are converted on
+// the way in and out (float-float tiles of complex128 states).
 template <typename T> struct FT;
-template <> struct FT<float> { static constexpr int L = 4, AB = 8; };
-template <> struct FT<double> { static constexpr int L = 3, AB = 16; };
+template <> struct FT<float> { static constexpr int L = 4, AB = 8; using mat_t = float; static constexpr bool conv = false; };
+template <> struct FT<double> { static constexpr int L = 3, AB = 16; using mat_t = double; static constexpr bool conv = false; };
+template <> struct FT<df> { static constexpr int L = 3, AB = 16; using mat_t = double; static constexpr bool conv = true; };
 
 template <typename T> VQG_DEV T shfl(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <> VQG_DEV df shfl<df>(df v, int m) {
+    return df(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
 
 template <typename T> VQG_DEV T warp_tree(T v) {
 #pragma unroll
@@ -204,7 +212,7 @@ VQG_DEV void copy_words(W *dst, const W *__restrict__ src, int count, int tid, i
 template <typename T, int R>
 VQG_DEV void load_prog(Prog<T, R> &pg, int s0, int ns, int d0, int nd, const FStage *__restrict__ stages,
                        const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
-                       const FDItem *__restrict__ items, const T *__restrict__ mats, bool reverse,
+                       const FDItem *__restrict__ items, const typename FT<T>::mat_t *__restrict__ mats, bool reverse,
                        int tid, int nt) {
     const int op0 = ns ? stages[s0].op0 : 0;
     const int n_op = ns ? stages[s0 + ns - 1].op0 + stages[s0 + ns - 1].n_op - op0 : 0;
@@ -220,13 +228,13 @@ VQG_DEV void load_prog(Prog<T, R> &pg, int s0, int ns, int d0, int nd, const FSt
         const FOp op = ops[op0 + o];
         const int g = op.gate;
         if (g < 0) continue;
-        const T *m = mats + 8 * (size_t)g;
+        const typename FT<T>::mat_t *m = mats + 8 * (size_t)g;
         if (op.type == OP_RY) {  // (cos, sin) of the real rotation in one slot
-            pg.prm[4 * o] = mk<T>(m[0], m[4]);
+            pg.prm[4 * o] = mk<T>((T)m[0], (T)m[4]);
             continue;
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) pg.prm[4 * o + e] = mk<T>(m[2 * e], m[2 * e + 1]);
+        for (int e = 0; e < 4; ++e) pg.prm[4 * o + e] = mk<T>((T)m[2 * e], (T)m[2 * e + 1]);
     }
     for (int i = tid; i < n_it; i += nt) {
         const FDItem x = items[it0 + i];
@@ -235,10 +243,10 @@ VQG_DEV void load_prog(Prog<T, R> &pg, int s0, int ns, int d0, int nd, const FSt
         const uint32_t q1 = x.g1 ? (uint32_t)__ffsll((long long)x.g1) - 1u : 0u;
         pg.ti[i] = (uint32_t)x.type | (q0 << 8) | (q1 << 16) | ((uint32_t)(x.k0 & 0xff) << 24);
         if (x.type != DI_RZ_REG && x.type != DI_RZ_THR) continue;
-        const T *m = mats + 8 * (size_t)x.gate;
+        const typename FT<T>::mat_t *m = mats + 8 * (size_t)x.gate;
         const T sg = reverse ? (T)-1 : (T)1;
-        pg.iph[2 * i] = mk<T>(m[0], sg * m[1]);
-        pg.iph[2 * i + 1] = mk<T>(m[6], sg * m[7]);
+        pg.iph[2 * i] = mk<T>((T)m[0], sg * (T)m[1]);
+        pg.iph[2 * i + 1] = mk<T>((T)m[6], sg * (T)m[7]);
     }
     __syncthreads();
     constexpr int NA = 1 << R;
@@ -536,20 +544,58 @@ struct TileIO {
         for (int i = 0; i < G::CPT; ++i) put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), make_float4(0.f, 0.f, 0.f, 0.f));
         if (base == 0 && tid == 0) tile[swz<AB>(0)] = mk<T>((T)1, (T)0);
     }
+    // A 16-byte global chunk <-> its CA amplitudes in the tile arithmetic (float-float
+    // amplitudes are FP64 in memory).
+    static VQG_DEV void unpack(float4 v, amp_t<T> *a) {
+        if constexpr (AB == 8) {
+            a[0] = mk<T>(v.x, v.y);
+            a[1] = mk<T>(v.z, v.w);
+        } else if constexpr (FT<T>::conv) {
+            union {
+                float4 f;
+                double2 d;
+            } u;
+            u.f = v;
+            a[0] = mk<T>(T(u.d.x), T(u.d.y));
+        } else {
+            union {
+                float4 f;
+                amp_t<T> a;
+            } u;
+            u.f = v;
+            a[0] = u.a;
+        }
+    }
+    static VQG_DEV float4 pack(const amp_t<T> *a) {
+        if constexpr (AB == 8) {
+            return make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
+        } else {
+            union {
+                float4 f;
+                double2 d;
+            } u;
+            u.d = make_double2((double)a[0].x, (double)a[0].y);
+            return u.f;
+        }
+    }
     // A 16-byte chunk (two complex64 or one complex128 amplitudes) at swizzled slot s of its
     // first amplitude.  For complex64 the second amplitude sits at s ^ swz(1) = s ^ 1.
     static VQG_DEV void put_chunk(amp_t<T> *tile, uint32_t s, float4 v) {
-        if constexpr (AB == 8) {
-            tile[s] = mk<T>(v.x, v.y);
-            tile[s ^ 1u] = mk<T>(v.z, v.w);
+        if constexpr (AB == 8 || FT<T>::conv) {
+            amp_t<T> a[CA];
+            unpack(v, a);
+            tile[s] = a[0];
+            if constexpr (CA == 2) tile[s ^ 1u] = a[1];
         } else {
             *reinterpret_cast<float4 *>(tile + s) = v;
         }
     }
     static VQG_DEV float4 get_chunk(const amp_t<T> *tile, uint32_t s) {
         if constexpr (AB == 8) {
-            const amp_t<T> a = tile[s], b = tile[s ^ 1u];
-            return make_float4(a.x, a.y, b.x, b.y);
+            const amp_t<T> a[2] = {tile[s], tile[s ^ 1u]};
+            return pack(a);
+        } else if constexpr (FT<T>::conv) {
+            return pack(tile + s);
         } else {
             return *reinterpret_cast<const float4 *>(tile + s);
         }
@@ -652,7 +698,7 @@ VQG_DEV void reduce_rows(const T *stash, int first, int count, double *acc, int 
     constexpr int V = 16 / sizeof(T);  // values per 16-byte load
     for (int r = warp; r < count; r += NT / 32) {
         T v = 0;
-        if constexpr (NT % (32 * V) != 0) {
+        if constexpr (NT % (32 * V) != 0 || FT<T>::conv) {
             for (int i = lane; i < NT; i += 32) v += stash[r * NT + i];
         } else {
 #pragma unroll
@@ -816,7 +862,7 @@ __global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
     k_fused_fwd(const amp_t<T> *__restrict__ src, amp_t<T> *__restrict__ dst,
                 const FPass *__restrict__ passes, int pi, const FStage *__restrict__ stages,
                 const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
-                const FDItem *__restrict__ items, const T *__restrict__ mats, uint64_t n_tiles) {
+                const FDItem *__restrict__ items, const typename FT<T>::mat_t *__restrict__ mats, uint64_t n_tiles) {
     using A = amp_t<T>;
     using C = FwdCfg<T, K, R>;
     constexpr int NT = C::NT;
@@ -859,7 +905,7 @@ __global__ void __launch_bounds__(1 << (K - R))
                 amp_t<T> *__restrict__ lam, const FPass *__restrict__ passes, int pi,
                 const FStage *__restrict__ stages, const FOp *__restrict__ ops,
                 const FDiag *__restrict__ diags, const FDItem *__restrict__ items,
-                const int *__restrict__ slot_map, const T *__restrict__ mats, uint64_t n_tiles,
+                const int *__restrict__ slot_map, const typename FT<T>::mat_t *__restrict__ mats, uint64_t n_tiles,
                 double *__restrict__ partials, int nb, int wmask) {
     using A = amp_t<T>;
     using C = RevCfg<T, K, R>;
@@ -1011,19 +1057,16 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
             const uint32_t tc = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
             if (i == 0) t0 = tc;
             gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
-            union {
-                float4 f;
-                A a[IO::CA];
-            } u;
+            A prev[IO::CA];
             if (!first) {
                 const float4 *g = reinterpret_cast<const float4 *>(lam + gch[i]);
-                u.f = L2ONLY ? __ldcg(g) : __ldcs(g);
+                IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), prev);
             }
 #pragma unroll
             for (int e = 0; e < IO::CA; ++e) {
                 sw[i * IO::CA + e] = swz<AB>(tc + e);
                 mine[i * IO::CA + e] = tile[sw[i * IO::CA + e]];
-                out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : u.a[e];
+                out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : prev[e];
                 delta[i * IO::CA + e] = mk<T>((T)0, (T)0);
             }
         }
@@ -1074,15 +1117,7 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
             out[k] = cadd<T>(out[k], delta[k]);
         }
 #pragma unroll
-        for (int i = 0; i < BCH; ++i) {
-            union {
-                float4 f;
-                A a[IO::CA];
-            } u;
-#pragma unroll
-            for (int e = 0; e < IO::CA; ++e) u.a[e] = out[i * IO::CA + e];
-            __stcs(reinterpret_cast<float4 *>(lam + gch[i]), u.f);
-        }
+        for (int i = 0; i < BCH; ++i) __stcs(reinterpret_cast<float4 *>(lam + gch[i]), IO::pack(out + i * IO::CA));
     }
     __syncthreads();
     return run;

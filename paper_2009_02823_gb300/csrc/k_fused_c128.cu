@@ -16,7 +16,7 @@ static void fwd_t(const void *src, void *dst, const FPass *passes, int pi, const
     static bool once = false;
     if (!once) set_smem(k_fused_fwd<T, K, R>, sm), once = true;
     k_fused_fwd<T, K, R><<<grid, FwdCfg<T, K, R>::NT, sm, s>>>(
-        (const amp_t<T> *)src, (amp_t<T> *)dst, passes, pi, st, ops, dg, it, (const T *)mats, n_tiles);
+        (const amp_t<T> *)src, (amp_t<T> *)dst, passes, pi, st, ops, dg, it, (const typename FT<T>::mat_t *)mats, n_tiles);
 }
 
 template <typename T, int K, int R>
@@ -29,7 +29,7 @@ static void rev_t(const void *phi_src, void *phi_dst, void *lam, const FPass *pa
     if (!once) set_smem(k_fused_rev<T, K, R>, sm), once = true;
     k_fused_rev<T, K, R><<<nb, RevCfg<T, K, R>::NT, sm, s>>>(
         (const amp_t<T> *)phi_src, (amp_t<T> *)phi_dst, (amp_t<T> *)lam, passes, pi, st, ops, dg, it,
-        slot_map, (const T *)mats, n_tiles, partials, nb, wmask);
+        slot_map, (const typename FT<T>::mat_t *)mats, n_tiles, partials, nb, wmask);
 }
 
 // Returns false if (K, R) has no instantiation.

@@ -48,7 +48,14 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
 // Hamiltonian tile passes of a plan; false if some group cannot live in one tile.
 bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham, const std::vector<PauliTerm> &host_terms);
 std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl);
-bool fused_supported(bool dbl, int K, int Rf, int Rr);
+bool fused_supported(bool dbl, int K, int Rf, int Rr, bool ff);
+// complex128 computed in float-float arithmetic (options.c128_arith)
+bool float_float(bool dbl, const vqg_options &opt);
+#define VQG_FWD_LAUNCH_ARGS                                                                      \
+    int K, int R, const void *src, void *dst, const FPass *passes, int pi, const FStage *st,      \
+        const FOp *ops, const FDiag *dg, const FDItem *it, const void *mats, uint64_t n_tiles,    \
+        int grid, cudaStream_t s
+bool launch_fused_fwd(bool dbl, bool ff, VQG_FWD_LAUNCH_ARGS);
 int default_tile_qubits(int n, bool dbl);
 
 }  // namespace vqg

@@ -27,13 +27,6 @@
 
 namespace vqg {
 
-bool launch_fused_fwd_c64(int K, int R, const void *src, void *dst, const FPass *passes, int pi, const FStage *st,
-                          const FOp *ops, const FDiag *dg, const FDItem *it, const void *mats, uint64_t n_tiles,
-                          int grid, cudaStream_t s);
-bool launch_fused_fwd_c128(int K, int R, const void *src, void *dst, const FPass *passes, int pi, const FStage *st,
-                           const FOp *ops, const FDiag *dg, const FDItem *it, const void *mats, uint64_t n_tiles,
-                           int grid, cudaStream_t s);
-
 // Re <psi|lambda> per block into partials[blockIdx.x] (FP64 per thread, deterministic tree).
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot_re(const amp_t<T> *__restrict__ psi, const amp_t<T> *__restrict__ lam,
@@ -148,10 +141,9 @@ int Circuit::issue_hamiltonian_product() {
             const void *m = dbl ? (const void *)(d_prod_mats + 8 * (size_t)k * n)
                                 : (const void *)(d_prod_mats_f + 8 * (size_t)k * n);
             for (size_t j = 0; j < pp->passes.size(); ++j)
-                (dbl ? launch_fused_fwd_c128 : launch_fused_fwd_c64)(pp->K, pp->Rf, j == 0 ? psi : dst, dst,
-                                                                     pp->d_passes, (int)j, pp->d_stages, pp->d_ops,
-                                                                     pp->d_diags, pp->d_items, m, pp->n_tiles,
-                                                                     pp->grid_fwd, stream);
+                launch_fused_fwd(dbl, float_float(dbl, opt), pp->K, pp->Rf, j == 0 ? psi : dst, dst, pp->d_passes,
+                                 (int)j, pp->d_stages, pp->d_ops, pp->d_diags, pp->d_items, m, pp->n_tiles,
+                                 pp->grid_fwd, stream);
         } else {
             cudaError_t e = cudaMemcpyAsync(dst, psi, state_bytes, cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "state copy: %s", cudaGetErrorString(e));

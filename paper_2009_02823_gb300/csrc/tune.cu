@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/vqg.h"
@@ -52,7 +53,7 @@ TuneKey key_of(const Circuit &c) {
         fh.add(&g.count, sizeof g.count);
     }
     for (const PauliTerm &t : c.host_terms) fh.add(&t.z, sizeof t.z);
-    return {c.n, c.dbl ? 1 : 0, c.G, c.P, fg.h, fh.h};
+    return {c.n, c.dbl ? (float_float(c.dbl, c.opt) ? 2 : 1) : 0, c.G, c.P, fg.h, fh.h};
 }
 
 struct FamTimes {
@@ -129,7 +130,11 @@ int Circuit::autotune(const double *theta_dev, vqg_tune_result *out) {
         return VQG_OK;
     }
     const int Kmax = std::min(n, dbl ? 12 : 13);
-    const int reg_pairs[2][2] = {{dbl ? 4 : 5, dbl ? 3 : 4}, {dbl ? 3 : 4, dbl ? 2 : 3}};
+    const bool ff = float_float(dbl, opt);
+    // (forward, reverse) register qubits; float-float has one compiled geometry
+    const std::vector<std::pair<int, int>> reg_pairs =
+        ff ? std::vector<std::pair<int, int>>{{3, 3}}
+           : std::vector<std::pair<int, int>>{{dbl ? 4 : 5, dbl ? 3 : 4}, {dbl ? 3 : 4, dbl ? 2 : 3}};
     const int K0 = plan->K, Rf0 = plan->Rf, Rr0 = plan->Rr;
     double best = 1e300;
     int bK = K0, bRf = Rf0, bRr = Rr0;
@@ -139,8 +144,8 @@ int Circuit::autotune(const double *theta_dev, vqg_tune_result *out) {
         double best_f = 1e300, best_r = 1e300, ham_t = 0, best_pair = 1e300;
         int kRf = 0, kRr = 0, pRf = 0, pRr = 0;
         for (const auto &rp : reg_pairs) {
-            int Rf = rp[0], Rr = rp[1];
-            if (!fused_supported(dbl, K, Rf, Rr)) continue;
+            const int Rf = rp.first, Rr = rp.second;
+            if (!fused_supported(dbl, K, Rf, Rr, ff)) continue;
             if ((st = apply_schedule(*this, K, Rf, Rr))) return st;
             FamTimes t;
             if (!warm) {  // first launch of the kernels: module load and attributes
@@ -157,7 +162,7 @@ int Circuit::autotune(const double *theta_dev, vqg_tune_result *out) {
         }
         if (!kRf) continue;
         double est = best_f + ham_t + best_r;
-        if (!fused_supported(dbl, K, kRf, kRr)) est = best_pair, kRf = pRf, kRr = pRr;  // mix not compiled
+        if (!fused_supported(dbl, K, kRf, kRr, ff)) est = best_pair, kRf = pRf, kRr = pRr;  // mix not compiled
         if (est < best) best = est, bK = K, bRf = kRf, bRr = kRr;
     }
     if (plan->K != bK || plan->Rf != bRf || plan->Rr != bRr)

@@ -2,6 +2,8 @@
 every workload at full size and random circuits plan into passes whose every index
 (tile geometry, register/thread bits, op fields, reduction slots, Hamiltonian masks)
 passes the library's own bounds checks."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -81,6 +83,38 @@ def test_register_variants(dtype, K, Rf, Rr, ok):
         with pytest.raises(B.VqgError):
             B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype, tile_qubits=K,
                            fwd_reg_qubits=Rf, rev_reg_qubits=Rr)
+
+
+@pytest.mark.parametrize("K,Rf,Rr,ok", [(10, 3, 3, True), (11, 3, 3, True), (12, 3, 3, True),
+                                        (12, 4, 3, False), (11, 3, 2, False), (13, 3, 3, False)])
+def test_float_float_register_variants(K, Rf, Rr, ok):
+    """complex128 in float-float arithmetic has one register geometry (3 + 3) for K=10..12."""
+    w = W.config(3)
+    kw = dict(tile_qubits=K, fwd_reg_qubits=Rf, rev_reg_qubits=Rr, c128_arith="float-float")
+    if ok:
+        info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c128", **kw)
+        assert (info["tile_qubits"], info["fwd_reg_qubits"], info["rev_reg_qubits"]) == (K, Rf, Rr)
+    else:
+        with pytest.raises(B.VqgError):
+            B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c128", **kw)
+
+
+def test_float_float_defaults_and_bad_mode():
+    w = W.config(3)
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c128", c128_arith="float-float")
+    assert (info["tile_qubits"], info["fwd_reg_qubits"], info["rev_reg_qubits"]) == (12, 3, 3)
+    fp = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c128")
+    assert (fp["fwd_reg_qubits"], fp["rev_reg_qubits"]) == (4, 3)
+    L = B.lib()
+    opt = B.vqg_options()
+    L.vqg_default_options(ctypes.byref(opt))
+    assert opt.c128_arith == 0
+    opt.c128_arith = 2
+    arr = B.gate_array(w.gates)
+    info_s = B.vqg_plan_info()
+    st = L.vqg_plan_dry_run(w.n, arr, len(w.gates), w.n_params, B.DTYPE["c128"], ctypes.byref(opt), 0,
+                            None, None, None, ctypes.byref(info_s))
+    assert st == -1 and b"c128_arith" in L.vqg_last_error()
 
 
 @pytest.mark.parametrize("dtype,kmax", [("c64", 13), ("c128", 12)])
