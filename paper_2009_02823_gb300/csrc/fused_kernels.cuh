@@ -78,13 +78,25 @@ template <typename T> VQG_DEV amp_t<T> neg(amp_t<T> a) { return mk<T>(-a.x, -a.y
 // ------------------------------------------------------------------ gate ops (forward)
 template <int KB, int NA, typename T>
 VQG_DEV void op_ry(amp_t<T> (&a)[NA], T c, T s) {
+    if constexpr (std::is_same<T, float>::value) {  // real factors: packed FP32 pairs
+        const float2 cc = make_float2(c, c), ss = make_float2(s, s), ns = make_float2(-s, -s);
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        if (j & (1 << KB)) continue;
-        const int j1 = j | (1 << KB);
-        const amp_t<T> x = a[j], y = a[j1];
-        a[j] = mk<T>(c * x.x - s * y.x, c * x.y - s * y.y);
-        a[j1] = mk<T>(s * x.x + c * y.x, s * x.y + c * y.y);
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const float2 x = a[j], y = a[j1];
+            a[j] = __ffma2_rn(cc, x, __fmul2_rn(ns, y));
+            a[j1] = __ffma2_rn(ss, x, __fmul2_rn(cc, y));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const amp_t<T> x = a[j], y = a[j1];
+            a[j] = mk<T>(c * x.x - s * y.x, c * x.y - s * y.y);
+            a[j1] = mk<T>(s * x.x + c * y.x, s * x.y + c * y.y);
+        }
     }
 }
 
@@ -357,6 +369,29 @@ VQG_DEV T tree_sum(T (&x)[N]) {
 // (phi_{i+1} = a, lambda_i = l) before un-applying U^dagger to both.
 template <int KB, int NA, typename T>
 VQG_DEV T rev_ry(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], T c, T s) {
+    if constexpr (std::is_same<T, float>::value) {
+        // Packed FP32 pairs: the RY^dagger updates have real factors, and the reduction
+        // keeps sum(l1 * a0) and sum(l0 * a1) component-wise (two chains each), combined
+        // as (P.x + P.y) - (Q.x + Q.y) at the end.
+        const float2 cc = make_float2(c, c), ss = make_float2(s, s), ns = make_float2(-s, -s);
+        float2 P[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, Q[2] = {P[0], P[1]};
+        int q = 0;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const float2 a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+            P[q & 1] = __ffma2_rn(l1, a0, P[q & 1]);
+            Q[q & 1] = __ffma2_rn(l0, a1, Q[q & 1]);
+            ++q;
+            a[j] = __ffma2_rn(cc, a0, __fmul2_rn(ss, a1));
+            a[j1] = __ffma2_rn(cc, a1, __fmul2_rn(ns, a0));
+            l[j] = __ffma2_rn(cc, l0, __fmul2_rn(ss, l1));
+            l[j1] = __ffma2_rn(cc, l1, __fmul2_rn(ns, l0));
+        }
+        const float2 p = __fadd2_rn(P[0], P[1]), r = __fadd2_rn(Q[0], Q[1]);
+        return (p.x + p.y) - (r.x + r.y);
+    }
     T pv[NA / 2];
     int q = 0;
 #pragma unroll
