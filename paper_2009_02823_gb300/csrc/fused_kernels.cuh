@@ -1092,17 +1092,18 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
             const uint32_t tc = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
             if (i == 0) t0 = tc;
             gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
-            A prev[IO::CA];
-            if (!first) {
-                const float4 *g = reinterpret_cast<const float4 *>(lam + gch[i]);
-                IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), prev);
-            }
 #pragma unroll
             for (int e = 0; e < IO::CA; ++e) {
                 sw[i * IO::CA + e] = swz<AB>(tc + e);
                 mine[i * IO::CA + e] = tile[sw[i * IO::CA + e]];
-                out[i * IO::CA + e] = first ? mk<T>((T)0, (T)0) : prev[e];
+                out[i * IO::CA + e] = mk<T>((T)0, (T)0);
                 delta[i * IO::CA + e] = mk<T>((T)0, (T)0);
+            }
+            // lambda so far goes straight into the output registers: its first use is the
+            // final add, so the load's latency hides behind the group loop
+            if (!first) {
+                const float4 *g = reinterpret_cast<const float4 *>(lam + gch[i]);
+                IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), out + i * IO::CA);
             }
         }
         for (int g = 0; g < tb.ng; ++g) {
