@@ -357,11 +357,12 @@ VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64
 // ------------------------------------------------------------------ gate ops (reverse)
 // Balanced pairwise sum (short dependency chains; N a power of two).  Consumes x.
 template <int N, typename T>
-VQG_DEV T tree_sum(T (&x)[N]) {
+VQG_DEV T tree_sum(T (&x)[N], int n = N) {  // the first n entries (n a power of two, <= N)
 #pragma unroll
     for (int s = 1; s < N; s *= 2)
 #pragma unroll
-        for (int i = 0; i + s < N; i += 2 * s) x[i] += x[i + s];
+        for (int i = 0; i + s < N; i += 2 * s)
+            if (i + s < n) x[i] += x[i + s];
     return x[0];
 }
 
@@ -478,16 +479,20 @@ VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg
         T p[NA], H[R];
 #pragma unroll
         for (int j = 0; j < NA; ++j) p[j] = l[j].x * a[j].y - l[j].y * a[j].x;
+        // H[k] = sum over register index bit k = 0, S = sum of all, from one pairwise tree:
+        // level k folds bit k, and H[k] sums the bit-k = 0 entries of the level's input
+        // (2^R - 1 + sum_k (2^(R-1-k) - 1) adds instead of R (2^(R-1) - 1) + 2^R - 1)
 #pragma unroll
-        for (int k = 0; k < R; ++k) {  // sum over register index bit k = 0, as a tree
+        for (int k = 0; k < R; ++k) {
+            const int len = NA >> k;
             T h[NA / 2];
-            int q = 0;
 #pragma unroll
-            for (int j = 0; j < NA; ++j)
-                if (!((j >> k) & 1)) h[q++] = p[j];
-            H[k] = tree_sum<NA / 2, T>(h);
+            for (int m = 0; m < len / 2; ++m) h[m] = p[2 * m];
+            H[k] = tree_sum<NA / 2, T>(h, len / 2);
+#pragma unroll
+            for (int m = 0; m < len / 2; ++m) p[m] = p[2 * m] + p[2 * m + 1];
         }
-        const T S = tree_sum<NA, T>(p);
+        const T S = p[0];
         const int i0 = D.item0 - pg.item_base;
         T v[8];
 #pragma unroll
