@@ -363,6 +363,7 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
                         }
                         d.n_rz++;
                     }
+                    if (x.type == DI_CZ_RT) d.has_rt = 1;
                     if (cls(x.type) == 1 || cls(x.type) == 2) {
                         if (thr0 < 0) thr0 = (int)q;
                         ++n_thr;

@@ -114,7 +114,8 @@ struct FOp {          // 16 bytes: one shared-memory vector load
 // carry reverse reductions) and the per-thread factor only visits [thr0, thr0 + n_thr).
 struct FDiag {
     int32_t item0, n_item;  // items (global index)
-    int32_t n_rz;           // leading RZ items
+    int16_t n_rz;           // leading RZ items
+    int16_t has_rt;         // any CZ between a register bit and a thread-level qubit
     int16_t thr0, n_thr;    // thread-level items, relative to item0
 };
 

@@ -301,13 +301,18 @@ VQG_DEV void diag_thread(const Prog<T, R> &pg, const FDiag &D, uint64_t gb, amp_
 // factor on all of a thread's amplitudes commutes with every later op of the stage
 // (they act within the thread's amplitudes) and is applied once before the scatter.
 template <int NA, typename T>
-VQG_DEV void diag_apply(amp_t<T> (&a)[NA], const amp_t<T> *__restrict__ tab, uint32_t c) {
-    const uint32_t w = walsh_bits(c);
+VQG_DEV void diag_apply(amp_t<T> (&a)[NA], const amp_t<T> *__restrict__ tab, uint32_t c, bool has_rt) {
+    if (has_rt) {  // block-uniform: sign pattern only where a register-thread CZ exists
+        const uint32_t w = walsh_bits(c);
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        amp_t<T> d = tab[j];
-        if ((w >> j) & 1u) d = neg<T>(d);
-        a[j] = cmul<T>(d, a[j]);
+        for (int j = 0; j < NA; ++j) {
+            amp_t<T> d = tab[j];
+            if ((w >> j) & 1u) d = neg<T>(d);
+            a[j] = cmul<T>(d, a[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) a[j] = cmul<T>(tab[j], a[j]);
     }
 }
 
@@ -346,7 +351,7 @@ VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64
         uint32_t c;
         diag_thread<T, R>(pg, pg.dg[op.diag], gb, tau, c);
         phase = cmul<T>(tau, phase);
-        diag_apply<NA, T>(a, pg.tab + op.diag * NA, c);
+        diag_apply<NA, T>(a, pg.tab + op.diag * NA, c, pg.dg[op.diag].has_rt != 0);
         break;
     }
     default:
