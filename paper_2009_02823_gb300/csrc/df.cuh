@@ -83,6 +83,45 @@ struct df2 {
     df x, y;
 };
 
+// Packed float-float pairs for real-factor updates of a complex amplitude (RY): the real
+// and imaginary parts run the same sequence, so each FP32 step is one packed instruction
+// (sm_100 and later) on (re, im) lanes.  hi = (x.hi, y.hi), lo = (x.lo, y.lo).
+struct dfp {
+    float2 hi, lo;
+};
+VQG_DEV dfp to_dfp(const df2 &a) { return {make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo)}; }
+VQG_DEV df2 from_dfp(const dfp &v) { return {df(v.hi.x, v.lo.x), df(v.hi.y, v.lo.y)}; }
+VQG_DEV float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+VQG_DEV void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(s, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+}
+VQG_DEV void fast_two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    e = __fadd2_rn(b, neg2(__fadd2_rn(s, neg2(a))));
+}
+// lane-wise a * b + c with a.hi/a.lo given as (possibly broadcast) pairs; same error
+// model as fma(df, df, df)
+VQG_DEV dfp fma2(float2 ah, float2 al, const dfp &b, const dfp &c) {
+    const float2 p = __fmul2_rn(ah, b.hi);
+    float2 e = __ffma2_rn(ah, b.hi, neg2(p));
+    e = __ffma2_rn(ah, b.lo, __ffma2_rn(al, b.hi, e));
+    float2 s, t;
+    two_sum2(p, c.hi, s, t);
+    t = __fadd2_rn(t, __fadd2_rn(e, c.lo));
+    fast_two_sum2(s, t, s, t);
+    return {s, t};
+}
+VQG_DEV dfp mul2(float2 ah, float2 al, const dfp &b) {
+    const float2 p = __fmul2_rn(ah, b.hi);
+    float2 e = __ffma2_rn(ah, b.hi, neg2(p));
+    e = __ffma2_rn(ah, b.lo, __ffma2_rn(al, b.hi, e));
+    float2 s;
+    fast_two_sum2(p, e, s, e);
+    return {s, e};
+}
+
 }  // namespace vqg
 
 template <> struct Amp<vqg::df> { using type = vqg::df2; };

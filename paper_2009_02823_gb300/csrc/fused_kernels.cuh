@@ -88,6 +88,18 @@ VQG_DEV void op_ry(amp_t<T> (&a)[NA], T c, T s) {
             a[j] = __ffma2_rn(cc, x, __fmul2_rn(ns, y));
             a[j1] = __ffma2_rn(ss, x, __fmul2_rn(cc, y));
         }
+    } else if constexpr (std::is_same<T, df>::value) {  // packed float-float (re, im) lanes
+        const float2 ch = make_float2(c.hi, c.hi), cl = make_float2(c.lo, c.lo);
+        const float2 sh = make_float2(s.hi, s.hi), sl = make_float2(s.lo, s.lo);
+        const float2 nsh = make_float2(-s.hi, -s.hi), nsl = make_float2(-s.lo, -s.lo);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const dfp x = to_dfp(a[j]), y = to_dfp(a[j1]);
+            a[j] = from_dfp(fma2(ch, cl, x, mul2(nsh, nsl, y)));
+            a[j1] = from_dfp(fma2(sh, sl, x, mul2(ch, cl, y)));
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
@@ -397,23 +409,24 @@ VQG_DEV T rev_ry(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], T c, T s) {
         }
         const float2 p = __fadd2_rn(P[0], P[1]), r = __fadd2_rn(Q[0], Q[1]);
         return (p.x + p.y) - (r.x + r.y);
-    }
-    T pv[NA / 2];
-    int q = 0;
+    } else {
+        T pv[NA / 2];
+        int q = 0;
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        if (j & (1 << KB)) continue;
-        const int j1 = j | (1 << KB);
-        const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
-        // Im <lambda| Y |phi> over the pair: Re(conj(l1) a0) - Re(conj(l0) a1)
-        pv[q++] = (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
-        // RY^dagger = [[c, s], [-s, c]]
-        a[j] = mk<T>(c * a0.x + s * a1.x, c * a0.y + s * a1.y);
-        a[j1] = mk<T>(c * a1.x - s * a0.x, c * a1.y - s * a0.y);
-        l[j] = mk<T>(c * l0.x + s * l1.x, c * l0.y + s * l1.y);
-        l[j1] = mk<T>(c * l1.x - s * l0.x, c * l1.y - s * l0.y);
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const amp_t<T> a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+            // Im <lambda| Y |phi> over the pair: Re(conj(l1) a0) - Re(conj(l0) a1)
+            pv[q++] = (l1.x * a0.x + l1.y * a0.y) - (l0.x * a1.x + l0.y * a1.y);
+            // RY^dagger = [[c, s], [-s, c]]
+            a[j] = mk<T>(c * a0.x + s * a1.x, c * a0.y + s * a1.y);
+            a[j1] = mk<T>(c * a1.x - s * a0.x, c * a1.y - s * a0.y);
+            l[j] = mk<T>(c * l0.x + s * l1.x, c * l0.y + s * l1.y);
+            l[j1] = mk<T>(c * l1.x - s * l0.x, c * l1.y - s * l0.y);
+        }
+        return tree_sum<NA / 2, T>(pv);
     }
-    return tree_sum<NA / 2, T>(pv);
 }
 
 template <int KB, int NA, typename T>
