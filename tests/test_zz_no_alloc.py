@@ -55,10 +55,18 @@ def test_noalloc_matches_energy_and_gradient(dtype):
         phi_d = torch.tensor(psi, dtype=cdt, device="cuda")
         lam_d = torch.tensor(lam, dtype=cdt, device="cuda")
         grad_d = torch.zeros(P, dtype=torch.float64, device="cuda")
+        tol = 1e-12 if dtype == "c128" else 2e-5
+        nl = float(np.linalg.norm(lam))
         for seg in reversed(segments):  # last segment first, one call per segment
             B.reverse_noalloc(n, dtype, seg, theta, P, phi_d.data_ptr(), lam_d.data_ptr(),
                               grad_d.data_ptr(), stream)
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            # invariants of the recurrence (Sec. 2.2): both vectors are un-applied by the same
+            # unitaries, so <lambda_i|phi_{i+1}> stays E and the norms stay put
+            f, l_ = phi_d.cpu().numpy(), lam_d.cpu().numpy()
+            assert abs(np.vdot(l_, f) - e_ref) <= tol * max(1.0, abs(e_ref))
+            assert abs(np.linalg.norm(f) - 1.0) <= tol
+            assert abs(np.linalg.norm(l_) - nl) <= tol * max(1.0, nl)
         g = grad_d.cpu().numpy()
         assert grad_err(g, g_ref) <= TOL[dtype], grad_err(g, g_ref)
         # phi has been swept back to the input state |0...0>
