@@ -584,6 +584,30 @@ struct TileIO {
             put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), v);
         }
     }
+    // Two tiles at the same positions (the reverse pass's phi and lambda): every global
+    // load of both is issued before the first shared-memory store.
+    template <int NT, bool L2ONLY = false>
+    static VQG_DEV void load2(amp_t<T> *ta, const amp_t<T> *__restrict__ sa, amp_t<T> *tb,
+                              const amp_t<T> *__restrict__ sb, uint64_t base, const uint64_t *row_off, int tid) {
+        using G = Geo<NT>;
+        const int row0 = tid / CPR, col = tid % CPR;
+        const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
+        const uint64_t o0 = (base | row_off[row0]) + col * CA;
+        float4 va[G::CPT], vb[G::CPT];
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i) {
+            const uint64_t o = o0 + row_off[G::RSTEP * i];
+            const float4 *ga = reinterpret_cast<const float4 *>(sa + o);
+            const float4 *gb = reinterpret_cast<const float4 *>(sb + o);
+            va[i] = L2ONLY ? __ldcg(ga) : __ldcs(ga);
+            vb[i] = L2ONLY ? __ldcg(gb) : __ldcs(gb);
+        }
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i) {
+            put_chunk(ta, s0 ^ swz<AB>((uint32_t)i << G::SHI), va[i]);
+            put_chunk(tb, s0 ^ swz<AB>((uint32_t)i << G::SHI), vb[i]);
+        }
+    }
     // Ask L2 for the rows of a tile (one 128-byte row = one L2 line per request) one tile
     // ahead of its load: the load then hits L2 instead of waiting on HBM.
     template <int NT>
@@ -793,8 +817,7 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
     constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
-    IO::template load<NT, L2ONLY>(tphi, phi_src, base, row_off, tid);
-    IO::template load<NT, L2ONLY>(tlam, lam, base, row_off, tid);
+    IO::template load2<NT, L2ONLY>(tphi, phi_src, tlam, lam, base, row_off, tid);
     __syncthreads();
     for (int s = 0; s < n_stage; ++s) {
         const FStage &st = pg.st[s];
