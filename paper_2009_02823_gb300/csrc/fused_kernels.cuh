@@ -577,12 +577,14 @@ struct TileIO {
         const int row0 = tid / CPR, col = tid % CPR;
         const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
         const amp_t<T> *g0 = src + ((base | row_off[row0]) + col * CA);
+        float4 v[G::CPT];  // every global load in flight before the first shared store
 #pragma unroll
         for (int i = 0; i < G::CPT; ++i) {
             const float4 *g = reinterpret_cast<const float4 *>(g0 + row_off[G::RSTEP * i]);
-            const float4 v = L2ONLY ? __ldcg(g) : __ldcs(g);
-            put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), v);
+            v[i] = L2ONLY ? __ldcg(g) : __ldcs(g);
         }
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i) put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), v[i]);
     }
     // Two tiles at the same positions (the reverse pass's phi and lambda): every global
     // load of both is issued before the first shared-memory store.
@@ -689,9 +691,11 @@ struct TileIO {
         const int row0 = tid / CPR, col = tid % CPR;
         const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
         amp_t<T> *g0 = dst + ((base | row_off[row0]) + col * CA);
+        float4 v[G::CPT];  // every shared load before the first global store
 #pragma unroll
-        for (int i = 0; i < G::CPT; ++i)
-            __stcs(reinterpret_cast<float4 *>(g0 + row_off[G::RSTEP * i]), get_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI)));
+        for (int i = 0; i < G::CPT; ++i) v[i] = get_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI));
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i) __stcs(reinterpret_cast<float4 *>(g0 + row_off[G::RSTEP * i]), v[i]);
     }
 };
 
