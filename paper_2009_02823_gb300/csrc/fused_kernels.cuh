@@ -1037,7 +1037,7 @@ struct HamCfg {
     static constexpr int NT = 256;
     static constexpr size_t o_row = (size_t)(1 << K) * FT<T>::AB;
     static constexpr size_t o_tab = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
-    static constexpr size_t tab_bytes = (sizeof(uint32_t) * 3) * kMaxHamGroups +
+    static constexpr size_t tab_bytes = (sizeof(uint32_t) * 5 + 2 * sizeof(T)) * kMaxHamGroups +
                                         (2 * sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
     static constexpr size_t smem() { return o_tab + tab_bytes; }
 };
@@ -1052,6 +1052,10 @@ struct HamTab {
     uint64_t *t_znt;
     amp_t<T> *t_w, *t_weff;
     uint32_t *t_zl, *t_cls, *g_xs, *g_t0, *g_nt;
+    // a single-term group's term, indexed by the group (no dependent second lookup);
+    // g_w is its weight with the tile's sign, refreshed per tile
+    uint32_t *g_zl, *g_cls;
+    amp_t<T> *g_w;
     int ng, n_terms;
     VQG_DEV void bind(unsigned char *p) {
         t_znt = reinterpret_cast<uint64_t *>(p);
@@ -1062,6 +1066,20 @@ struct HamTab {
         g_xs = t_cls + kMaxHamTerms;
         g_t0 = g_xs + kMaxHamGroups;
         g_nt = g_t0 + kMaxHamGroups;
+        g_zl = g_nt + kMaxHamGroups;
+        g_cls = g_zl + kMaxHamGroups;
+        g_w = reinterpret_cast<amp_t<T> *>(g_cls + kMaxHamGroups);  // 16-byte aligned: see tab_bytes
+    }
+    // class bit d = bit of z_l at the d-th varying position of a batch
+    template <int D, int SH, int E0>
+    static VQG_DEV uint32_t class_of(uint32_t zl) {
+        uint32_t cls = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int pos = (E0 && d == 0) ? 0 : SH + d - E0;
+            cls |= ((zl >> pos) & 1u) << d;
+        }
+        return cls;
     }
     template <int D, int SH, int E0>
     VQG_DEV void load(const HPass &P, const HGroup *__restrict__ groups, const HTerm *__restrict__ terms,
@@ -1074,19 +1092,17 @@ struct HamTab {
             g_xs[g] = swz<AB>(G.xl);  // swz is linear: swz(t ^ x) = swz(t) ^ swz(x)
             g_t0[g] = (uint32_t)(G.term0 - term_base);
             g_nt[g] = (uint32_t)G.n_term;
+            if (G.n_term == 1) {
+                const uint32_t zl = terms[G.term0].zl;
+                g_zl[g] = zl;
+                g_cls[g] = class_of<D, SH, E0>(zl);
+            }
         }
         for (int k = tid; k < n_terms; k += nt) {
             const HTerm tm = terms[term_base + k];
             t_znt[k] = tm.znt;
             t_zl[k] = tm.zl;
-            // class bit d = bit of z_l at the d-th varying position of a batch
-            uint32_t cls = 0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int pos = (E0 && d == 0) ? 0 : SH + d - E0;
-                cls |= ((tm.zl >> pos) & 1u) << d;
-            }
-            t_cls[k] = cls;
+            t_cls[k] = class_of<D, SH, E0>(tm.zl);
             if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
             else t_w[k] = mk<T>(tm.wr, tm.wi);
         }
@@ -1128,6 +1144,12 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
         const A w = tb.t_w[k];
         tb.t_weff[k] = (__popcll(base & tb.t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;
     }
+    for (int g = tid; g < tb.ng; g += NT)
+        if (tb.g_nt[g] == 1) {
+            const int j = (int)tb.g_t0[g];
+            const A w = tb.t_w[j];
+            tb.g_w[g] = (__popcll(base & tb.t_znt[j]) & 1) ? mk<T>(-w.x, -w.y) : w;
+        }
     __syncthreads();
     T run = 0;
 #pragma unroll 1
@@ -1161,8 +1183,8 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
             const int j0 = tb.g_t0[g], nt_g = tb.g_nt[g];
             A f[BA];
             if (nt_g == 1) {  // one term: f = +-w with the sign pattern of its class
-                const uint32_t zl = tb.t_zl[j0], cls = tb.t_cls[j0];
-                const A w = tb.t_weff[j0];
+                const uint32_t zl = tb.g_zl[g], cls = tb.g_cls[g];
+                const A w = tb.g_w[g];
                 uint32_t m = (__popc(t0 & zl) & 1) ? 0xFFu : 0u;
                 if (cls & 1u) m ^= 0xAAu;
                 if (cls & 2u) m ^= 0xCCu;
