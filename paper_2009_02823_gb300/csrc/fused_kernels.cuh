@@ -543,8 +543,16 @@ VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg
     for (int j = 0; j < NA; ++j) {
         amp_t<T> d = tab[j];
         if ((w >> j) & 1u) d = neg<T>(d);
-        a[j] = cmul<T>(d, a[j]);
-        l[j] = cmul<T>(d, l[j]);
+        if constexpr (std::is_same<T, float>::value) {
+            // packed FP32 pairs; the factor's broadcasts serve phi and lambda:
+            // d z = (d.x, d.x) * z + (-d.y, d.y) * (z.y, z.x)
+            const float2 dr = make_float2(d.x, d.x), di2 = make_float2(-d.y, d.y);
+            a[j] = __ffma2_rn(dr, a[j], __fmul2_rn(di2, make_float2(a[j].y, a[j].x)));
+            l[j] = __ffma2_rn(dr, l[j], __fmul2_rn(di2, make_float2(l[j].y, l[j].x)));
+        } else {
+            a[j] = cmul<T>(d, a[j]);
+            l[j] = cmul<T>(d, l[j]);
+        }
     }
 }
 
