@@ -913,11 +913,21 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
         }
         asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
         if (st.has_phase) {
+            if constexpr (std::is_same<T, float>::value) {  // packed, broadcasts shared by both states
+                const float2 pr = make_float2(phase.x, phase.x), pi2 = make_float2(-phase.y, phase.y);
 #pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                const uint32_t ad = reg_addr<R, NA>(sb, w, j);
-                tphi[ad] = cmul<T>(phase, a[j]);
-                tlam[ad] = cmul<T>(phase, l[j]);
+                for (int j = 0; j < NA; ++j) {
+                    const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                    tphi[ad] = __ffma2_rn(pr, a[j], __fmul2_rn(pi2, make_float2(a[j].y, a[j].x)));
+                    tlam[ad] = __ffma2_rn(pr, l[j], __fmul2_rn(pi2, make_float2(l[j].y, l[j].x)));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NA; ++j) {
+                    const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                    tphi[ad] = cmul<T>(phase, a[j]);
+                    tlam[ad] = cmul<T>(phase, l[j]);
+                }
             }
         } else {
 #pragma unroll
