@@ -494,23 +494,47 @@ template <int R, int NA, typename T>
 VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg, const FDiag &D,
                       int di, uint64_t gb, T *stash_row, int nt, amp_t<T> &phase) {
     if (D.n_rz > 0) {
-        T p[NA], H[R];
+        T H[R], S;
+        if constexpr (std::is_same<T, float>::value) {
+            // p_j = Im(conj(l_j) a_j) held as pairs q_m = (p_2m, p_2m+1): every fold of the
+            // tree below is one packed add for two index-bit-0 lanes; the lanes meet only
+            // in the final scalar adds.
+            float2 q[NA / 2];
 #pragma unroll
-        for (int j = 0; j < NA; ++j) p[j] = l[j].x * a[j].y - l[j].y * a[j].x;
-        // H[k] = sum over register index bit k = 0, S = sum of all, from one pairwise tree:
-        // level k folds bit k, and H[k] sums the bit-k = 0 entries of the level's input
-        // (2^R - 1 + sum_k (2^(R-1-k) - 1) adds instead of R (2^(R-1) - 1) + 2^R - 1)
+            for (int m = 0; m < NA / 2; ++m)
+                q[m] = make_float2(l[2 * m].x * a[2 * m].y - l[2 * m].y * a[2 * m].x,
+                                   l[2 * m + 1].x * a[2 * m + 1].y - l[2 * m + 1].y * a[2 * m + 1].x);
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int len = NA >> k;
-            T h[NA / 2];
+            for (int k = 1; k < R; ++k) {  // fold index bit k (bit k - 1 of m)
+                const int len = (NA / 2) >> (k - 1);
+                float2 h = q[0];
 #pragma unroll
-            for (int m = 0; m < len / 2; ++m) h[m] = p[2 * m];
-            H[k] = tree_sum<NA / 2, T>(h, len / 2);
+                for (int m = 1; m < len / 2; ++m) h = __fadd2_rn(h, q[2 * m]);
+                H[k] = h.x + h.y;
 #pragma unroll
-            for (int m = 0; m < len / 2; ++m) p[m] = p[2 * m] + p[2 * m + 1];
+                for (int m = 0; m < len / 2; ++m) q[m] = __fadd2_rn(q[2 * m], q[2 * m + 1]);
+            }
+            H[0] = q[0].x;
+            S = q[0].x + q[0].y;
+        } else {
+            T p[NA];
+#pragma unroll
+            for (int j = 0; j < NA; ++j) p[j] = l[j].x * a[j].y - l[j].y * a[j].x;
+            // H[k] = sum over register index bit k = 0, S = sum of all, from one pairwise
+            // tree: level k folds bit k, and H[k] sums the bit-k = 0 entries of the level's
+            // input (2^R - 1 + sum_k (2^(R-1-k) - 1) adds instead of R (2^(R-1) - 1) + 2^R - 1)
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int len = NA >> k;
+                T h[NA / 2];
+#pragma unroll
+                for (int m = 0; m < len / 2; ++m) h[m] = p[2 * m];
+                H[k] = tree_sum<NA / 2, T>(h, len / 2);
+#pragma unroll
+                for (int m = 0; m < len / 2; ++m) p[m] = p[2 * m] + p[2 * m + 1];
+            }
+            S = p[0];
         }
-        const T S = p[0];
         const int i0 = D.item0 - pg.item_base;
         T v[8];
 #pragma unroll
