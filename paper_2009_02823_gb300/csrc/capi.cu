@@ -1,6 +1,7 @@
 // C ABI of the library (include/vqg.h): circuit objects, Hamiltonian grouping, and
 // the launch sequence of Algorithm 1 on one GPU.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -393,7 +394,18 @@ int Circuit::issue_table(const double *theta_dev, int shift_gate, int shift_slot
     return check_launch("build_mats");
 }
 
+// NVTX range over the host-side issue of one phase (forward sweep, Hamiltonian, reverse
+// sweep): a profiler that records NVTX (Nsight Systems, ncu --nvtx) attributes the phase's
+// kernels to it; without one attached the calls do nothing.
+namespace {
+struct PhaseRange {
+    explicit PhaseRange(const char *name) { nvtxRangePushA(name); }
+    ~PhaseRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 int Circuit::issue_forward(bool with_ckpt) {
+    PhaseRange range("vqg forward sweep");
     if (opt.fusion && plan_ok) return issue_forward_fused(with_ckpt);  // pass 0 starts from |in>
     prof_begin(FAM_INIT);
     if (has_input) VQG_CUDA(cudaMemcpyAsync(psi, d_input, state_bytes, cudaMemcpyDeviceToDevice, stream));
@@ -416,6 +428,7 @@ int Circuit::issue_forward(bool with_ckpt) {
 }
 
 int Circuit::issue_hamiltonian(bool write_lam) {
+    PhaseRange range("vqg lambda = H psi");
     if (prod_active) return issue_hamiltonian_product();
     if (ham.empty()) {  // H = 0: lambda = 0, E = 0
         e_used = 0;
@@ -440,6 +453,7 @@ int Circuit::issue_hamiltonian(bool write_lam) {
 }
 
 int Circuit::issue_reverse() {
+    PhaseRange range("vqg reverse sweep");
     if (opt.fusion && plan_ok) return issue_reverse_fused();
     double *gpart = d_partials + (size_t)n_eslots * nb;
     int k = (int)ckpt_pos.size() - 1;
