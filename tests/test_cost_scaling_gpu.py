@@ -48,6 +48,7 @@ def test_adjoint_linear_parameter_shift_quadratic():
     # asymptotic slopes 1 and 2: the adjoint must not grow faster than linearly, the
     # parameter-shift gradient must grow clearly faster, by about one power of P.
     s_adj, s_ps = _slopes(20, (4, 8, 16, 32))
+    print(f"log-log slopes in P: adjoint {s_adj:.3f}, parameter shift {s_ps:.3f}")
     assert s_adj <= 1.2, f"adjoint time grows faster than linearly in P (slope {s_adj:.2f})"
     assert 1.4 <= s_ps <= 2.3, f"parameter-shift slope {s_ps:.2f}"
     assert s_ps - s_adj >= 0.6, f"slopes {s_adj:.2f} / {s_ps:.2f}"
