@@ -112,6 +112,40 @@ VQG_DEV void op_ry(amp_t<T> (&a)[NA], T c, T s) {
     }
 }
 
+// Whether a stage's amplitudes carry a scale to undo at the scatter (complex64 only).
+template <typename T> VQG_DEV bool scaled_stage(T kacc) {
+    if constexpr (std::is_same<T, float>::value) return kacc != 1.f;
+    else return false;
+}
+
+// complex64 RY without its scale factor k (see load_prog): each output is one packed
+// multiply-add and equals the true output divided by k; the caller multiplies the stage's
+// amplitudes by the product of the k at the scatter.  C-form: (a0 - r a1, a1 + r a0);
+// S-form: (r a0 - a1, a0 + r a1).
+template <int KB, int NA>
+VQG_DEV void op_ry_scaled(float2 (&a)[NA], float r, bool sform) {
+    const float2 rr = make_float2(r, r), nr = make_float2(-r, -r);
+    if (!sform) {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const float2 x = a[j], y = a[j1];
+            a[j] = __ffma2_rn(nr, y, x);
+            a[j1] = __ffma2_rn(rr, x, y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (j & (1 << KB)) continue;
+            const int j1 = j | (1 << KB);
+            const float2 x = a[j], y = a[j1];
+            a[j] = __ffma2_rn(rr, x, make_float2(-y.x, -y.y));
+            a[j1] = __ffma2_rn(rr, y, x);
+        }
+    }
+}
+
 template <int KB, int NA, typename T>
 VQG_DEV void op_gen(amp_t<T> (&a)[NA], const Mat2<T> &u) {
 #pragma unroll
@@ -255,6 +289,16 @@ VQG_DEV void load_prog(Prog<T, R> &pg, int s0, int ns, int d0, int nd, const FSt
         const typename FT<T>::mat_t *m = mats + 8 * (size_t)g;
         if (op.type == OP_RY) {  // (cos, sin) of the real rotation in one slot
             pg.prm[4 * o] = mk<T>((T)m[0], (T)m[4]);
+            if constexpr (std::is_same<T, float>::value) {
+                // scaled form: RY = k [[1, -r], [r, 1]] (k = c, r = s / c) when |c| >= |s|,
+                // else k [[r, -1], [1, r]] (k = s, r = c / s); |r| <= 1.  Slot 1: (r, form),
+                // slot 2: (k, k^2), computed in FP64 from the table entries, rounded once.
+                const double c = m[0], sn = m[4];
+                const bool sform = std::fabs(sn) > std::fabs(c);
+                const double k = sform ? sn : c, r = sform ? c / sn : sn / c;
+                pg.prm[4 * o + 1] = mk<T>((T)r, sform ? (T)1 : (T)0);
+                pg.prm[4 * o + 2] = mk<T>((T)k, (T)(k * k));
+            }
             continue;
         }
 #pragma unroll
@@ -329,13 +373,20 @@ VQG_DEV void diag_apply(amp_t<T> (&a)[NA], const amp_t<T> *__restrict__ tab, uin
 }
 
 template <int R, int NA, typename T>
-VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64_t gb, amp_t<T> &phase) {
+VQG_DEV void apply_fwd_op(amp_t<T> (&a)[NA], const Prog<T, R> &pg, int o, uint64_t gb, amp_t<T> &phase,
+                          T &kacc) {
     const FOp op = pg.op[o];
     const amp_t<T> *m = pg.prm + 4 * o;
     switch (op.type) {
     case OP_RY: {
-        const amp_t<T> cs = m[0];
-        with_k<R>(op.k, [&](auto kb) { op_ry<decltype(kb)::value, NA, T>(a, cs.x, cs.y); });
+        if constexpr (std::is_same<T, float>::value) {  // scaled form; k joins the stage's factor
+            const float2 p1 = m[1];
+            with_k<R>(op.k, [&](auto kb) { op_ry_scaled<decltype(kb)::value, NA>(a, p1.x, p1.y != 0.f); });
+            kacc *= m[2].x;
+        } else {
+            const amp_t<T> cs = m[0];
+            with_k<R>(op.k, [&](auto kb) { op_ry<decltype(kb)::value, NA, T>(a, cs.x, cs.y); });
+        }
         break;
     }
     case OP_RX:
@@ -381,6 +432,43 @@ VQG_DEV T tree_sum(T (&x)[N], int n = N) {  // the first n entries (n a power of
         for (int i = 0; i + s < N; i += 2 * s)
             if (i + s < n) x[i] += x[i + s];
     return x[0];
+}
+
+// complex64 RY^dagger without its scale factor k, on phi and lambda: C-form
+// (a0 + r a1, a1 - r a0), S-form (r a0 + a1, r a1 - a0).  Returns the raw partial of
+// Im <lambda|Y|phi> from the inputs, which hold the true values divided by the stage's
+// product K of the k so far (the caller multiplies the partial by K^2).
+template <int KB, int NA, bool SFORM>
+VQG_DEV float rev_ry_scaled_form(float2 (&a)[NA], float2 (&l)[NA], float r) {
+    const float2 rr = make_float2(r, r), nr = make_float2(-r, -r);
+    float2 P[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, Q[2] = {P[0], P[1]};
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (j & (1 << KB)) continue;
+        const int j1 = j | (1 << KB);
+        const float2 a0 = a[j], a1 = a[j1], l0 = l[j], l1 = l[j1];
+        P[q & 1] = __ffma2_rn(l1, a0, P[q & 1]);
+        Q[q & 1] = __ffma2_rn(l0, a1, Q[q & 1]);
+        ++q;
+        if constexpr (!SFORM) {
+            a[j] = __ffma2_rn(rr, a1, a0);
+            a[j1] = __ffma2_rn(nr, a0, a1);
+            l[j] = __ffma2_rn(rr, l1, l0);
+            l[j1] = __ffma2_rn(nr, l0, l1);
+        } else {
+            a[j] = __ffma2_rn(rr, a0, a1);
+            a[j1] = __ffma2_rn(rr, a1, make_float2(-a0.x, -a0.y));
+            l[j] = __ffma2_rn(rr, l0, l1);
+            l[j1] = __ffma2_rn(rr, l1, make_float2(-l0.x, -l0.y));
+        }
+    }
+    const float2 p = __fadd2_rn(P[0], P[1]), t = __fadd2_rn(Q[0], Q[1]);
+    return (p.x + p.y) - (t.x + t.y);
+}
+template <int KB, int NA>
+VQG_DEV float rev_ry_scaled(float2 (&a)[NA], float2 (&l)[NA], float r, bool sform) {
+    return sform ? rev_ry_scaled_form<KB, NA, true>(a, l, r) : rev_ry_scaled_form<KB, NA, false>(a, l, r);
 }
 
 // Each returns the thread's partial of the gate's reduction value(s) computed from
@@ -492,7 +580,7 @@ VQG_DEV T rev_cgen(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Mat2<T> &ud, uint
 // bit k needs sum_j (-1)^{j_k} p_j and an RZ on a thread-level qubit +-sum_j p_j.
 template <int R, int NA, typename T>
 VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg, const FDiag &D,
-                      int di, uint64_t gb, T *stash_row, int nt, amp_t<T> &phase) {
+                      int di, uint64_t gb, T *stash_row, int nt, amp_t<T> &phase, T k2acc) {
     if (D.n_rz > 0) {
         T H[R], S;
         if constexpr (std::is_same<T, float>::value) {
@@ -555,7 +643,10 @@ VQG_DEV void rev_diag(amp_t<T> (&a)[NA], amp_t<T> (&l)[NA], const Prog<T, R> &pg
         }
 #pragma unroll
         for (int r = 0; r < 8; ++r)
-            if (r < D.n_rz) stash_row[r * nt] = v[r];
+            if (r < D.n_rz) {
+                if constexpr (std::is_same<T, float>::value) v[r] *= k2acc;  // the stage's scale so far
+                stash_row[r * nt] = v[r];
+            }
     }
     amp_t<T> tau;
     uint32_t c;
@@ -791,12 +882,20 @@ VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> 
 #pragma unroll
         for (int j = 0; j < NA; ++j) a[j] = tile[reg_addr<R, NA>(sb, w, j)];
         A phase = mk<T>((T)1, (T)0);
+        T kacc = (T)1;  // product K of the k of the stage's scaled RY ops (complex64)
         const int o0 = st.op0 - pg.op_base;
-        for (int o = o0; o < o0 + st.n_op; ++o) apply_fwd_op<R, NA, T>(a, pg, o, gb, phase);
+        for (int o = o0; o < o0 + st.n_op; ++o) apply_fwd_op<R, NA, T>(a, pg, o, gb, phase, kacc);
         asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
         if (st.has_phase) {
+            if constexpr (std::is_same<T, float>::value) phase = mk<T>(phase.x * kacc, phase.y * kacc);
 #pragma unroll
             for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = cmul<T>(phase, a[j]);
+        } else if (scaled_stage<T>(kacc)) {
+            if constexpr (std::is_same<T, float>::value) {
+                const float2 sv = make_float2(kacc, kacc);
+#pragma unroll
+                for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = __fmul2_rn(sv, a[j]);
+            }
         } else {
 #pragma unroll
             for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(sb, w, j)] = a[j];
@@ -871,6 +970,10 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             l[j] = tlam[ad];
         }
         A phase = mk<T>((T)1, (T)0);
+        // complex64: the scaled RY ops leave phi and lambda holding their true values
+        // divided by K, the product of the ops' k: kacc = K (multiplied back at the scatter),
+        // k2acc = K^2 (multiplies every reduction partial formed from the held values)
+        T kacc = (T)1, k2acc = (T)1;
         const int o0 = st.op0 - pg.op_base;
         for (int o = o0; o < o0 + st.n_op; ++o) {
             const FOp op = pg.op[o];
@@ -879,14 +982,25 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
             bool red1 = false;
             switch (op.type) {
             case OP_RY: {
-                const A cs = m[0];
-                with_k<R>(op.k, [&](auto kb) { v1 = rev_ry<decltype(kb)::value, NA, T>(a, l, cs.x, cs.y); });
+                if constexpr (std::is_same<T, float>::value) {  // scaled form (see load_prog)
+                    const float2 p1 = m[1], p2 = m[2];
+                    with_k<R>(op.k, [&](auto kb) {
+                        v1 = rev_ry_scaled<decltype(kb)::value, NA>(a, l, p1.x, p1.y != 0.f);
+                    });
+                    v1 *= k2acc;  // the inputs held the true values divided by K so far
+                    kacc *= p2.x;
+                    k2acc *= p2.y;
+                } else {
+                    const A cs = m[0];
+                    with_k<R>(op.k, [&](auto kb) { v1 = rev_ry<decltype(kb)::value, NA, T>(a, l, cs.x, cs.y); });
+                }
                 red1 = true;
                 break;
             }
             case OP_RX: {
                 const Mat2<T> ud = dagger<T>(mat_of<T>(m));
                 with_k<R>(op.k, [&](auto kb) { v1 = rev_rx<decltype(kb)::value, NA, T>(a, l, ud); });
+                if constexpr (std::is_same<T, float>::value) v1 *= k2acc;
                 red1 = true;
                 break;
             }
@@ -895,7 +1009,10 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
                 T v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 with_k<R>(op.k, [&](auto kb) { rev_u3<decltype(kb)::value, NA, T>(a, l, ud, v8); });
 #pragma unroll
-                for (int x = 0; x < 8; ++x) stash[(op.row + x) * NT + tid] = v8[x];
+                for (int x = 0; x < 8; ++x) {
+                    if constexpr (std::is_same<T, float>::value) v8[x] *= k2acc;
+                    stash[(op.row + x) * NT + tid] = v8[x];
+                }
                 break;
             }
             case OP_CNOT: {
@@ -919,11 +1036,13 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
                     else if (op.type == OP_CRZ) v1 = rev_cgen<2, KB, NA, T>(a, l, ud, op.rm0, c);
                     else v1 = rev_cgen<3, KB, NA, T>(a, l, ud, op.rm0, c);
                 });
+                if constexpr (std::is_same<T, float>::value) v1 *= k2acc;
                 red1 = true;
                 break;
             }
             case OP_DIAG:
-                rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, stash + op.row * NT + tid, NT, phase);
+                rev_diag<R, NA, T>(a, l, pg, pg.dg[op.diag], op.diag, gb, stash + op.row * NT + tid, NT, phase,
+                                   k2acc);
                 break;
             case OP_FLUSH:  // uniform: every thread runs the same op list
                 __syncthreads();
@@ -938,6 +1057,7 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
         asm volatile("" : "+r"(sb));  // recompute the addresses instead of keeping them live
         if (st.has_phase) {
             if constexpr (std::is_same<T, float>::value) {  // packed, broadcasts shared by both states
+                phase = mk<T>(phase.x * kacc, phase.y * kacc);
                 const float2 pr = make_float2(phase.x, phase.x), pi2 = make_float2(-phase.y, phase.y);
 #pragma unroll
                 for (int j = 0; j < NA; ++j) {
@@ -951,6 +1071,16 @@ VQG_DEV void rev_tile(amp_t<T> *tphi, amp_t<T> *tlam, const uint64_t *row_off, c
                     const uint32_t ad = reg_addr<R, NA>(sb, w, j);
                     tphi[ad] = cmul<T>(phase, a[j]);
                     tlam[ad] = cmul<T>(phase, l[j]);
+                }
+            }
+        } else if (scaled_stage<T>(kacc)) {
+            if constexpr (std::is_same<T, float>::value) {
+                const float2 sv = make_float2(kacc, kacc);
+#pragma unroll
+                for (int j = 0; j < NA; ++j) {
+                    const uint32_t ad = reg_addr<R, NA>(sb, w, j);
+                    tphi[ad] = __fmul2_rn(sv, a[j]);
+                    tlam[ad] = __fmul2_rn(sv, l[j]);
                 }
             }
         } else {
