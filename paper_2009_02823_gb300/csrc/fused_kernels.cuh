@@ -17,6 +17,12 @@
 // most 16 terms in FP32; in the reverse pass the block's per-thread partials of one tile
 // are summed in FP32 (lane runs of NT/32 values, then the 32-lane tree) and added to an
 // FP64 accumulator per tile; block and grid levels are FP64.
+//
+// complex64 arithmetic uses packed FP32 pairs (sm_100 and later) where one instruction can
+// update the real and imaginary parts together: RY ops in a scaled form with one packed
+// multiply-add per output (the stage carries the dropped factor, see load_prog), and the
+// reverse pass's diagonal multiplies whose factor is shared by phi and lambda.  complex128
+// tiles compute in FP64 or, by option, in float-float (df.cuh).
 #pragma once
 #include <type_traits>
 
