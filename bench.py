@@ -139,9 +139,9 @@ def family_alu_ops(fam: str, w) -> float | None:
     one gradient): per-amplitude counts x 2^n."""
     amps = float(1 << w.n)
     if fam in ("fwd_fused", "fwd_gate"):
-        return amps * sum(FWD_OPS[g[0]] for g in w.gates)
+        return amps * sum(FWD_OPS.get(g[0], 0) for g in w.gates)  # kinds not listed count 0
     if fam in ("adj_fused", "adj_gate"):
-        return amps * sum(REV_OPS[g[0]] for g in w.gates)
+        return amps * sum(REV_OPS.get(g[0], 0) for g in w.gates)
     if fam in ("ham_fused", "ham_group", "ham_diag"):
         groups = len({tuple(sorted(q for q, l in ops if l in "XY")) for _c, ops in w.terms})
         return amps * (2 * len(w.terms) + 8 * groups)  # sign-weighted sums; complex MAC + energy
