@@ -11,13 +11,15 @@ from paper_2009_02823_gb300 import binding as B
 from paper_2009_02823_gb300 import workloads as W
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "c128-ff"])
 @pytest.mark.parametrize("cfg", [1, 2, 3, 5])
 def test_workloads_plan(cfg, dtype):
     w = W.config(cfg)
-    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype)
+    arith = "float-float" if dtype == "c128-ff" else "fp64"
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, dtype[:4], c128_arith=arith)
     assert info["tile_qubits"] == min(13 if dtype == "c64" else 12, max(10, w.n - 8))
-    assert (info["fwd_reg_qubits"], info["rev_reg_qubits"]) == ((5, 4) if dtype == "c64" else (4, 3))
+    regs = {"c64": (5, 4), "c128": (4, 3), "c128-ff": (3, 3)}[dtype]
+    assert (info["fwd_reg_qubits"], info["rev_reg_qubits"]) == regs
     assert 1 <= info["forward_passes"] <= w.n_gates
     assert info["hamiltonian_passes"] >= 1
     assert info["forward_stages"] >= info["forward_passes"]
@@ -40,10 +42,10 @@ def test_random_circuits_plan(seed, K):
     n = int(rng.integers(K, 22))
     gates, P = W.random_circuit(rng, n, 300, share_params=True)
     terms = W.random_paulis(rng, n, 60, 4)
-    for dtype in ("c64", "c128"):
+    for dtype, arith in (("c64", "fp64"), ("c128", "fp64"), ("c128", "float-float")):
         if dtype == "c128" and K > 12:
             continue
-        info = B.plan_dry_run(n, gates, P, terms, dtype, tile_qubits=K)
+        info = B.plan_dry_run(n, gates, P, terms, dtype, tile_qubits=K, c128_arith=arith)
         assert info["tile_qubits"] == K
 
 
