@@ -32,15 +32,15 @@ from paper_2009_02823_gb300.replicas import (circuit_cost, max_over_ranks, parti
 METRIC = "adjoint gradients/s at n=30,P=600"
 
 # DRAM bytes (read + write) per launch per amplitude of the state, from one ncu capture
-# of each fused complex64 kernel at n=26 (profiles/k_fused_*_n26_c64.md).  Every launch
-# streams whole states, so traffic scales with 2^n.  Reset an entry to None whenever
-# its kernel changes until it is captured again.
+# (dram__bytes_read.sum + dram__bytes_write.sum) of each fused complex64 kernel on the
+# bench recipe at n=26 (0.5 GB per state, far larger than L2), taken on the kernels as
+# they are now: reverse 1.0792 + 0.4791 GB, forward 0.5405 + 0.4823 GB, Hamiltonian
+# 1.1276 + 0.4777 GB per launch.  Every launch streams whole states, so traffic scales
+# with 2^n.  Reset an entry to None whenever its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    # the reverse kernel changed (scaled RY) after its last capture: no traffic figure until
-    # it is captured again (that capture moved 1.558 GB per n=26 launch, 0.97x of 3 S)
-    "adj_fused": None,
-    "fwd_fused": (0.539988736e9 + 0.482312192e9) / 2**26,
-    "ham_fused": (1.134581e9 + 0.476873472e9) / 2**26,
+    "adj_fused": (1.079234e9 + 0.479091456e9) / 2**26,
+    "fwd_fused": (0.540485376e9 + 0.482346752e9) / 2**26,
+    "ham_fused": (1.127569e9 + 0.477710592e9) / 2**26,
 }
 UNIT = "gradients/s"
 
@@ -148,10 +148,11 @@ def family_alu_ops(fam: str, w) -> float | None:
     return None
 
 
-def alu_peak(sm_mhz: float | None) -> tuple[float, str]:
-    """FP32 lane-op peak: 152 SMs x 128 FP32 lanes x SM clock (sampled during the run)."""
+def alu_peak(sm_mhz: float | None, n_sm: int = 152) -> tuple[float, str]:
+    """FP32 lane-op peak: SMs (read from the device) x 128 FP32 lanes x SM clock (sampled
+    during the run)."""
     mhz = sm_mhz or 2070.0
-    return 152 * 128 * mhz * 1e6 / 1e9, f"152 SM x 128 FP32 lanes x {mhz:.0f} MHz (sampled)"
+    return n_sm * 128 * mhz * 1e6 / 1e9, f"{n_sm} SM x 128 FP32 lanes x {mhz:.0f} MHz (sampled)"
 
 
 def family_bytes(fam: str, w, S: int, plan: dict) -> float | None:
@@ -185,6 +186,7 @@ def run_ours(args, rank, world, dist):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     w = _workload(args)
     S = (8 if args.dtype == "c64" else 16) << w.n
     stream = torch.cuda.Stream()  # every kernel of the step and both timing events go here
@@ -257,7 +259,7 @@ def run_ours(args, rank, world, dist):
         if ops is not None:
             gops = ops * args.steps / (ms / 1e3) / 1e9
             ent["alu_gops"] = round(gops, 1)
-            ent["alu_frac"] = round(gops / alu_peak(clk.get("sm_mhz"))[0], 4)
+            ent["alu_frac"] = round(gops / alu_peak(clk.get("sm_mhz"), n_sm)[0], 4)
         per_family[f] = ent
     if launches:
         avg_s = tot_ms / launches / 1e3
@@ -266,7 +268,7 @@ def run_ours(args, rank, world, dist):
         fused = fam.endswith("_fused")
         ops = family_alu_ops(fam, w)
         if fused and ops:
-            apk, apk_src = alu_peak(clk.get("sm_mhz"))
+            apk, apk_src = alu_peak(clk.get("sm_mhz"), n_sm)
             ach = ops * args.steps / (tot_ms / 1e3) / 1e9
             roof = {"bound": "alu", "kernel": fam, "achieved": round(ach, 1), "peak": round(apk, 1),
                     "unit": "GFLOP32-lane-op/s", "frac": round(ach / apk, 4), "peak_source": apk_src,
@@ -292,7 +294,7 @@ def run_ours(args, rank, world, dist):
     if not args.no_batch:
         extra["batched"] = batched_rate(args, rank, world, dist)
     if rank == 0 and not args.no_extra and args.dtype == "c64":
-        extra["c64_vs_c128"] = precision_check(w, g_d, e_val)
+        extra["c128_n%d" % w.n] = c128_rates(w, g_d, e_val, dev)
     if rank == 0 and not args.no_extra:
         extra["controlled"] = controlled_rate()
         extra["non_hermitian"] = non_hermitian_rate()
@@ -301,7 +303,9 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and not args.no_ps:
         extra["param_shift"] = param_shift_baseline(args, circ, w, theta_h, value / world)
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline_sample(args, w, budget_s=args.cpu_budget)
+        cpu = cpu_baseline_sample(args, w, budget_s=args.cpu_budget, reps=3)
+        if args.cpu_full_n > 0:
+            cpu["full_gradient"] = cpu_full_gradient(args.cpu_full_n)
     else:
         cpu = None
     circ.close()
@@ -331,18 +335,55 @@ def amplitude_updates(w, S, grads_per_s, hbm_peak):
     return {"per_s": ups, "unfused_hbm_roofline_per_s": roof, "ratio_to_unfused_roofline": round(ups / roof, 3)}
 
 
-def precision_check(w, g_c64_dev, e_c64):
-    """The complex64 gradient of the timed run against one complex128 evaluation of the same
-    workload on the GPU (FP64 amplitudes; that path matches the oracle to 1e-10 in the
-    tests): max-abs and norm-wise relative differences."""
+def c128_rates(w, g_c64_dev, e_c64, dev):
+    """The same workload with complex128 amplitudes (the paper's double-precision state
+    vector), timed on the GPU in both tile-pass arithmetics (FP64 and float-float): one
+    untimed warm-up gradient, then one gradient timed with CUDA events on the circuit's
+    stream, nvidia-smi clocks sampled meanwhile.  The FP64 gradient (the path that matches
+    the oracle to 1e-10 in the parity tests) is also the reference for the complex64
+    gradient of the timed run and for the float-float one: max-abs and norm-wise relative
+    differences."""
+    import torch
+
     from paper_2009_02823_gb300 import Circuit
     g64 = g_c64_dev.cpu().numpy()
-    with Circuit(w.n, w.gates, w.n_params, "c128") as c:
-        c.set_hamiltonian(w.terms)
-        e128, g128 = c.energy_and_gradient(w.theta)
-    diff = np.abs(g64 - g128)
-    return {"max_abs_grad_err": float(diff.max()), "rel_grad_err": float(diff.max() / np.abs(g128).max()),
-            "energy_err": abs(e_c64 - e128), "energy_c128": e128}
+    out, grads = {}, {}
+    for arith in ("float-float", "fp64"):
+        stream = torch.cuda.Stream()
+        with Circuit(w.n, w.gates, w.n_params, "c128", stream=stream, c128_arith=arith) as c:
+            c.set_hamiltonian(w.terms)
+            th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+            e = torch.zeros(1, dtype=torch.float64, device="cuda")
+            g = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            c.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+            torch.cuda.synchronize()
+            clocks = Clocks(dev)
+            c.set_profiling(True)
+            clocks.start()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            c.energy_and_gradient_device(th.data_ptr(), e.data_ptr(), g.data_ptr())
+            t1.record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            stats = c.kernel_stats()
+            ms = t0.elapsed_time(t1)
+            grads[arith] = (float(e.item()), g.cpu().numpy())
+        out[arith] = {"ms_per_gradient": round(ms, 1), "gradients_per_s": round(1e3 / ms, 4),
+                      "family_ms": {f: round(v[1], 1) for f, v in stats.items() if v[1] > 0.5},
+                      "clocks": {"sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons")}}
+    e128, g128 = grads["fp64"]
+    scale = float(np.abs(g128).max())
+    eff, gff = grads["float-float"]
+    out["float-float"]["vs_fp64"] = {"max_abs_grad_err": float(np.abs(gff - g128).max()),
+                                     "rel_grad_err": float(np.abs(gff - g128).max() / scale),
+                                     "energy_err": abs(eff - e128)}
+    out["c64_vs_fp64"] = {"max_abs_grad_err": float(np.abs(g64 - g128).max()),
+                          "rel_grad_err": float(np.abs(g64 - g128).max() / scale),
+                          "energy_err": abs(e_c64 - e128), "energy_c128": e128}
+    out["timing"] = "one gradient each after one warm-up, CUDA events on the circuit's stream"
+    return out
 
 
 def batched_rate(args, rank=0, world=1, dist=None):
@@ -600,36 +641,17 @@ def p_scaling(n=20, layers=(4, 8, 16, 32)):
 
 
 # ---------------------------------------------------------------- CPU oracle baseline
-def cpu_baseline_sample(args, w, budget_s=20.0):
-    """The oracle as it stands, on the host cores, on a bounded sample of the same
-    workload: its Algorithm-1 primitives (apply gate, apply adjoint gate, derivative
-    matrix + clone + inner product, one Hamiltonian term) are timed at the workload's
-    n on the workload's own gates/terms, and the full Algorithm-1 gradient time is
-    extrapolated from the per-primitive times and the workload's gate and term counts."""
+def _primitive_total(L, oracle, w, psi, lam, gt, th, coef, let, budget_s, t_start):
+    """One sample of the oracle's Algorithm-1 primitives at the workload's n, extrapolated
+    to a whole gradient; returns (seconds per gradient, kinds timed, parameter slots)."""
     import ctypes
-
-    import oracle
-    L = oracle._load()
     n = w.n
-    dim = 1 << n
-    t_start = time.perf_counter()
-    try:
-        psi = np.zeros(dim, dtype=np.complex128)
-        lam = np.zeros(dim, dtype=np.complex128)
-    except MemoryError:
-        return {"value": None, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                "sample": "host memory too small for the workload's state vectors"}
-    psi[0] = 1.0
-    lam[:] = psi
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-    gt = oracle.gate_table(w.gates)
-    th = np.ascontiguousarray(w.theta)
-    coef, let = oracle.letter_table(w.terms, n)
     kinds = {}
     for i, g in enumerate(w.gates):
         kinds.setdefault(g[0], i)
     per = {}
-    # forward + adjoint application per kind (one launch each; the work is data-independent)
+    # forward + adjoint application per kind (one call each; the work is data-independent)
     for kind, i in kinds.items():
         t0 = time.perf_counter()
         L.oracle_apply_gate(n, ptr(psi), ptr(gt[i]), ptr(th), 0)
@@ -661,14 +683,66 @@ def cpu_baseline_sample(args, w, budget_s=20.0):
         total += f + 2 * a
         n_slots += {"RX": 1, "RY": 1, "RZ": 1, "U3": 3}.get(g[0], 0)
     total += n_slots * t_deriv
+    return total, sorted(per), n_slots, k_terms
+
+
+def cpu_full_gradient(n=22):
+    """One complete Algorithm-1 gradient of the oracle, timed in full, on the bench recipe
+    at n qubits (same circuit structure and Hamiltonian recipe, smaller state)."""
+    import oracle
+    from paper_2009_02823_gb300 import workloads as W
+    w = W.config(3, n=n)
+    t0 = time.perf_counter()
+    oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
+    dt = time.perf_counter() - t0
+    return {"workload": w.name, "n_qubits": n, "n_params": w.n_params, "n_gates": w.n_gates,
+            "s_per_gradient": round(dt, 2), "gradients_per_s": 1.0 / dt, "cores": oracle.threads(),
+            "routine": "oracle.gradient_alg1 (complex128, Algorithm 1), timed in full"}
+
+
+def cpu_baseline_sample(args, w, budget_s=20.0, reps=1):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same
+    workload: its Algorithm-1 primitives (apply gate, apply adjoint gate, derivative
+    matrix + clone + inner product, one Hamiltonian term) are timed at the workload's
+    n on the workload's own gates/terms, and the full Algorithm-1 gradient time is
+    extrapolated from the per-primitive times and the workload's gate and term counts.
+    With reps > 1 the sample is repeated and the median extrapolation is reported with
+    the spread of the samples."""
+    import oracle
+    L = oracle._load()
+    n = w.n
+    dim = 1 << n
+    t_start = time.perf_counter()
+    try:
+        psi = np.zeros(dim, dtype=np.complex128)
+        lam = np.zeros(dim, dtype=np.complex128)
+    except MemoryError:
+        return {"value": None, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                "sample": "host memory too small for the workload's state vectors"}
+    psi[0] = 1.0
+    lam[:] = psi
+    gt = oracle.gate_table(w.gates)
+    th = np.ascontiguousarray(w.theta)
+    coef, let = oracle.letter_table(w.terms, n)
+    totals = []
+    for _ in range(max(1, reps)):
+        total, kinds, n_slots, k_terms = _primitive_total(L, oracle, w, psi, lam, gt, th, coef, let,
+                                                          budget_s * max(1, reps), t_start)
+        totals.append(total)
+    total = statistics.median(totals)
     sample_s = time.perf_counter() - t_start
-    return {"value": 1.0 / total, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": (f"oracle primitives at n={n} (complex128): one forward and one adjoint "
-                       f"application per gate kind {sorted(per)}, one derivative+clone+inner "
-                       f"product, {k_terms} of {len(w.terms)} Hamiltonian terms; Algorithm 1 "
-                       f"time extrapolated over {w.n_gates} gates / {n_slots} parameter slots "
-                       f"= {total:.1f} s per gradient; sample took {sample_s:.1f} s"),
-            "extrapolated_s_per_gradient": round(total, 2)}
+    res = {"value": 1.0 / total, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+           "sample": (f"oracle primitives at n={n} (complex128): one forward and one adjoint "
+                      f"application per gate kind {kinds}, one derivative+clone+inner "
+                      f"product, {k_terms} of {len(w.terms)} Hamiltonian terms; Algorithm 1 "
+                      f"time extrapolated over {w.n_gates} gates / {n_slots} parameter slots "
+                      f"= {total:.1f} s per gradient (median of {len(totals)} samples); "
+                      f"sample took {sample_s:.1f} s"),
+           "extrapolated_s_per_gradient": round(total, 2)}
+    if len(totals) > 1:
+        res["samples_s_per_gradient"] = [round(t, 1) for t in totals]
+        res["spread"] = round((max(totals) - min(totals)) / total, 4)
+    return res
 
 
 def run_reference(args, rank):
@@ -717,6 +791,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the extra-workload figures")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-full-n", type=int, default=22,
+                    help="qubits of the complete CPU oracle gradient timed beside the sample (0: skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -85,8 +85,9 @@ typedef struct vqg_gate {
  *   VQG_C128_FP64:        gate arithmetic in FP64 (bounded by the GPU's FP64 rate).
  *   VQG_C128_FLOAT_FLOAT: gate arithmetic on pairs of FP32 numbers (hi + lo, about 48
  *                         significant bits; error-free TwoSum / FMA TwoProduct), rounded
- *                         to FP64 at every state store.  Relative error per operation
- *                         below ~2^-44; tile passes only (3 register qubits per stage);
+ *                         to FP64 at every state store.  Absolute error per operation
+ *                         below ~2^-46 (|a| + |b|) for a sum or a product-sum a*b + c
+ *                         of amplitudes bounded by the state norm; tile passes only (3 register qubits per stage);
  *                         the one-kernel-per-gate route (fusion = 0, n < 10) stays FP64. */
 typedef enum { VQG_C128_FP64 = 0, VQG_C128_FLOAT_FLOAT = 1 } vqg_c128_arith;
 
@@ -116,13 +117,20 @@ typedef struct vqg_circuit vqg_circuit;
 
 void vqg_default_options(vqg_options *opt);
 
-/* Create a circuit of n_qubits (1..34) over gates[0..n_gates) with n_params parameters.
- * dtype is a vqg_dtype.  opt may be NULL (defaults).  Device buffers for two state
- * vectors (and checkpoints) are allocated here on the current CUDA device.
- * Errors: VQG_ERR_INVALID for malformed gates, VQG_ERR_OOM when buffers do not fit. */
+/* Create the circuit U(theta) = U_G ... U_1 of Sec. 2.2 (gates[0] acts first; each
+ * gate slot names the parameter it takes, App. B.1/B.2) on n_qubits (1..34) over
+ * gates[0..n_gates) with n_params parameters.  gates: host array, copied.  dtype is a
+ * vqg_dtype.  opt may be NULL (defaults).  Device buffers for two state vectors (and
+ * checkpoints) are allocated here on the current CUDA device and owned by the circuit.
+ * *out receives the handle.  Errors: VQG_ERR_INVALID for malformed gates (qubit out of
+ * range, q0 == q1, parameter index outside 0..n_params-1, unknown kind), VQG_ERR_OOM
+ * when buffers do not fit; *out is untouched on error. */
 int vqg_circuit_create(int n_qubits, const vqg_gate *gates, int n_gates, int n_params,
                        int dtype, const vqg_options *opt, vqg_circuit **out);
 
+/* Release a circuit of vqg_circuit_create and every device buffer it owns (the state
+ * vectors of Sec. 2.2's |psi>, Algorithm 1's lambda and the checkpoints).  Waits for the
+ * circuit's outstanding work first.  NULL is a no-op returning VQG_OK. */
 int vqg_circuit_destroy(vqg_circuit *c);
 
 /* Set (replace) the Hamiltonian: sum_t coef[t] * i^{popcount(x&z)} X^{x_mask[t]} Z^{z_mask[t]}.
@@ -131,6 +139,22 @@ int vqg_circuit_destroy(vqg_circuit *c);
  * term of a group.  coef real (Hermitian H).  May be called between evaluations. */
 int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *x_mask,
                         const uint64_t *z_mask, const double *coef);
+
+/* The same Hamiltonian written as Pauli strings (Sec. 2.1 leaves the representation
+ * open; Sec. 3's operators are tensor products of one-qubit Paulis):
+ * strings[t] is a NUL-terminated string of exactly n_qubits characters, character q
+ * the letter acting on qubit q, one of 'I', 'X', 'Y', 'Z' (so "XIZY" is X_0 Z_2 Y_3);
+ * coef[t] its real coefficient.  Both arrays are host memory, read during the call.
+ * Any other character, a NULL string, or a string of another length returns
+ * VQG_ERR_INVALID and leaves the circuit's Hamiltonian unchanged.  Otherwise the call
+ * behaves exactly as vqg_set_hamiltonian on the converted masks.
+ * vqg_pauli_strings_to_masks does the conversion alone, on the host (no GPU, no
+ * circuit): x_mask[t], z_mask[t] (host, n_terms each) receive term t's masks, with the
+ * same checks and errors; n_qubits may be 1..64 there. */
+int vqg_set_hamiltonian_strings(vqg_circuit *c, int n_terms, const char *const *strings,
+                                const double *coef);
+int vqg_pauli_strings_to_masks(int n_qubits, int n_terms, const char *const *strings,
+                               uint64_t *x_mask, uint64_t *z_mask);
 
 /* All work of this circuit is issued on `stream` (a cudaStream_t; NULL = the library's
  * own non-blocking stream; pass cudaStreamLegacy, (void *)0x1, for the legacy default
@@ -338,21 +362,24 @@ int vqg_batch_destroy(vqg_batch *b);
  *
  * vqg_reverse_noalloc runs the reverse-sweep body (un-apply U^dagger to phi and lambda,
  * accumulate the gate's gradient contributions) for gates[n_gates-1] down to gates[0]:
+ *   gates    : host array; kinds RX, RY, RZ, U3, CNOT and CZ (the controlled rotations
+ *              and phase gates are refused with VQG_ERR_INVALID; use a vqg_circuit).
  *   phi, lam : device state vectors of 2^n_qubits amplitudes (dtype), both updated in
  *              place; on entry phi = U_{1:G}|in> restricted to the segment's end and lam
  *              the matching lambda, exactly as in Algorithm 1's loop.
  *   theta    : host array of n_params doubles; grad: device array of n_params doubles
  *              to which the contributions are ADDED (the caller zeroes it first).
  *   stream   : cudaStream_t (NULL = legacy default stream); work is asynchronous.
- * It calls no cudaMalloc, cudaFree or other allocating routine.  Its reduction scratch
- * is a file-scope static device array (1 MiB of per-block partial sums plus 8 KiB of
- * gate matrices) that every GPU the process uses holds until the process exits.  At
- * most VQG_NOALLOC_MAX_GATES gates per call; more returns VQG_ERR_INVALID (split a
- * longer sweep into segments and call them last segment first).  The first call on
- * each device resolves the scratch arrays' device addresses (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the scratch: calls
- * whose work overlaps on the GPU (different streams or host threads) race and must be
- * serialised by the caller.  Returns VQG_OK or a negative vqg_status. */
+ * It calls no cudaMalloc, cudaFree or other allocating routine, and copies nothing from
+ * host memory: the gate matrices travel as kernel parameters.  Its reduction scratch is
+ * a file-scope static device array (1 MiB of per-block partial sums) that every GPU the
+ * process uses holds until the process exits.  At most VQG_NOALLOC_MAX_GATES gates per
+ * call; more returns VQG_ERR_INVALID (split a longer sweep into segments and call them
+ * last segment first).  The first call on each device resolves the scratch array's
+ * device address (cudaGetSymbolAddress) and keeps it for the process: make that first
+ * call before any stream capture, and not across a cudaDeviceReset.  All calls share
+ * the scratch: calls whose work overlaps on the GPU (different streams or host threads)
+ * race and must be serialised by the caller.  Returns VQG_OK or a negative vqg_status. */
 #define VQG_NOALLOC_MAX_GATES 32
 #define VQG_NOALLOC_BLOCKS 512
 int vqg_reverse_noalloc(int n_qubits, int dtype, const vqg_gate *gates, int n_gates,

@@ -90,6 +90,8 @@ def lib():
             "vqg_circuit_create": (i, [i, p, i, i, i, p, pp]),
             "vqg_circuit_destroy": (i, [p]),
             "vqg_set_hamiltonian": (i, [p, i, p, p, p]),
+            "vqg_set_hamiltonian_strings": (i, [p, i, p, p]),
+            "vqg_pauli_strings_to_masks": (i, [i, i, p, p, p]),
             "vqg_set_stream": (i, [p, p]),
             "vqg_energy": (i, [p, p, p]),
             "vqg_energy_and_gradient": (i, [p, p, p, p]),
@@ -135,6 +137,23 @@ def lib():
 def _check(status: int):
     if status != VQG_OK:
         raise VqgError(status, lib().vqg_last_error().decode())
+
+
+def _string_array(strings) -> ctypes.Array:
+    arr = (ctypes.c_char_p * max(len(strings), 1))()
+    for k, t in enumerate(strings):
+        arr[k] = t.encode("ascii") if isinstance(t, str) else t
+    return arr
+
+
+def pauli_strings_to_masks(n_qubits: int, strings) -> tuple[np.ndarray, np.ndarray]:
+    """Host-only conversion by the library (vqg_pauli_strings_to_masks): (x_mask, z_mask)."""
+    arr = _string_array(strings)
+    x = np.zeros(max(len(strings), 1), dtype=np.uint64)
+    z = np.zeros(max(len(strings), 1), dtype=np.uint64)
+    _check(lib().vqg_pauli_strings_to_masks(n_qubits, len(strings), ctypes.cast(arr, ctypes.c_void_p),
+                                            _ptr(x), _ptr(z)))
+    return x[:len(strings)], z[:len(strings)]
 
 
 def gate_array(gates) -> ctypes.Array:
@@ -240,6 +259,15 @@ class Circuit:
     def set_hamiltonian(self, terms):
         x, z, c = pauli_masks(terms, self.n)
         self.set_hamiltonian_masks(x, z, c)
+
+    def set_hamiltonian_strings(self, strings, coef):
+        """Pauli strings, character q acting on qubit q ("XIZY" = X_0 Z_2 Y_3), through
+        vqg_set_hamiltonian_strings."""
+        arr = _string_array(strings)
+        c = np.ascontiguousarray(coef, dtype=np.float64)
+        if len(c) != len(strings):
+            raise ValueError("one coefficient per string")
+        _check(lib().vqg_set_hamiltonian_strings(self._h, len(c), ctypes.cast(arr, ctypes.c_void_p), _ptr(c)))
 
     def set_hamiltonian_masks(self, x, z, coef):
         if np.iscomplexobj(coef):

@@ -368,6 +368,53 @@ extern "C" int vqg_set_hamiltonian(vqg_circuit *c, int n_terms, const uint64_t *
     return cc->set_groups(ham, flat);
 }
 
+// ------------------------------------------------------------------ Pauli strings
+// Character q of strings[t] is the Pauli letter on qubit q (I, X, Y or Z), so the
+// string "XIZY" on 4 qubits is X_0 Z_2 Y_3.  X sets the x bit, Z the z bit, Y both
+// (the mask form's convention: Y = i X Z).
+extern "C" int vqg_pauli_strings_to_masks(int n_qubits, int n_terms, const char *const *strings,
+                                          uint64_t *x_mask, uint64_t *z_mask) {
+    if (n_qubits < 1 || n_qubits > 64) return set_error(VQG_ERR_INVALID, "n_qubits=%d outside 1..64", n_qubits);
+    if (n_terms < 0) return set_error(VQG_ERR_INVALID, "n_terms=%d", n_terms);
+    if (n_terms > 0 && (!strings || !x_mask || !z_mask)) return set_error(VQG_ERR_INVALID, "null pointer");
+    for (int t = 0; t < n_terms; ++t) {
+        const char *s = strings[t];
+        if (!s) return set_error(VQG_ERR_INVALID, "string %d is NULL", t);
+        uint64_t x = 0, z = 0;
+        int q = 0;
+        for (; s[q] != '\0'; ++q) {
+            if (q >= n_qubits)
+                return set_error(VQG_ERR_INVALID, "string %d is longer than %d qubits", t, n_qubits);
+            const uint64_t b = 1ull << q;
+            switch (s[q]) {
+            case 'I': break;
+            case 'X': x |= b; break;
+            case 'Y': x |= b; z |= b; break;
+            case 'Z': z |= b; break;
+            default:
+                return set_error(VQG_ERR_INVALID, "string %d: character %d is '%c', not one of I, X, Y, Z", t, q,
+                                 s[q]);
+            }
+        }
+        if (q != n_qubits)
+            return set_error(VQG_ERR_INVALID, "string %d has %d characters for %d qubits", t, q, n_qubits);
+        x_mask[t] = x;
+        z_mask[t] = z;
+    }
+    return VQG_OK;
+}
+
+extern "C" int vqg_set_hamiltonian_strings(vqg_circuit *c, int n_terms, const char *const *strings,
+                                           const double *coef) {
+    if (!c) return set_error(VQG_ERR_INVALID, "circuit is NULL");
+    Circuit *cc = reinterpret_cast<Circuit *>(c);
+    if (n_terms < 0) return set_error(VQG_ERR_INVALID, "n_terms=%d", n_terms);
+    std::vector<uint64_t> x((size_t)std::max(n_terms, 1)), z((size_t)std::max(n_terms, 1));
+    int st = vqg_pauli_strings_to_masks(cc->n, n_terms, strings, x.data(), z.data());
+    if (st) return st;
+    return vqg_set_hamiltonian(c, n_terms, x.data(), z.data(), coef);
+}
+
 int Circuit::set_groups(const std::vector<HamGroup> &groups, const std::vector<PauliTerm> &flat) {
     ham = groups;
     int st;

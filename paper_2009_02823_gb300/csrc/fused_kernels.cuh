@@ -118,6 +118,15 @@ VQG_DEV void op_ry(amp_t<T> (&a)[NA], T c, T s) {
     }
 }
 
+// Range of the scaled form: each scaled RY drops a factor k with |k| >= 2^-1/2, so a stage
+// of m RY ops holds amplitudes up to 2^(m/2) times their true values (at most 1 in
+// magnitude for a normalised state) and the reverse pass scales its reduction partials by
+// K^2 >= 2^-m.  A forward stage holds at most kMaxPassOps ops and a reverse stage at most
+// kMaxStageValues RY ops (one reduction value each); both bounds keep the held values and
+// K^2 inside FP32's normal range (2^-126 .. 2^128) with a wide margin.
+static_assert(kMaxPassOps / 2 <= 100, "forward scaled-RY stages could leave FP32's range");
+static_assert(kMaxStageValues <= 100, "reverse scaled-RY stages could leave FP32's range");
+
 // Whether a stage's amplitudes carry a scale to undo at the scatter (complex64 only).
 template <typename T> VQG_DEV bool scaled_stage(T kacc) {
     if constexpr (std::is_same<T, float>::value) return kacc != 1.f;

@@ -6,16 +6,17 @@
 // is forbidden to enter cudaMalloc/cudaFree (which can synchronise the device) in a
 // latency-critical loop.  vqg_reverse_noalloc serves them: it runs the fused adjoint
 // step on device state vectors the caller owns and keeps its reduction scratch in the
-// file-scope arrays below, which every process that loads the library holds on each
+// file-scope array below, which every process that loads the library holds on each
 // GPU it touches until the process exits.
 //
 // Scratch (static, per device):
-//   g_noalloc_partials: VQG_NOALLOC_MAX_GATES x 8 x VQG_NOALLOC_BLOCKS doubles (1 MiB)
-//   g_noalloc_mats:     VQG_NOALLOC_MAX_GATES x 32 doubles (8 KiB): U^dagger and the
-//                       derivative matrices D_j = (dU/d slot j) U^dagger of each gate.
-// Every call overwrites the part it reads, so nothing needs clearing between calls;
-// calls whose work overlaps on the GPU (two streams, two host threads) race on the
-// shared arrays and must be serialised by the caller.
+//   g_noalloc_partials: VQG_NOALLOC_MAX_GATES x 8 x VQG_NOALLOC_BLOCKS doubles (1 MiB),
+//                       the per-block partial sums of each gate's four complex sums.
+// The gate matrices (U^dagger per gate, D_j = (dU/d slot j) U^dagger per slot) travel as
+// kernel parameters, so a call copies nothing from host memory.  Every call overwrites
+// the part of the scratch it reads, so nothing needs clearing between calls; calls whose
+// work overlaps on the GPU (two streams, two host threads) race on the shared array and
+// must be serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,28 +40,31 @@ constexpr int kThreads = 256;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[kMaxGates * 8 * kBlocks];
-static __device__ __align__(256) double g_noalloc_mats[kMaxGates * 32];
 
 std::mutex g_setup_mutex;
 double *g_partials_ptr[kMaxDevices] = {};
-double *g_mats_ptr[kMaxDevices] = {};
 
-// Resolve the device addresses of the scratch arrays for the current device (once).
-int setup_device(int dev, double **partials, double **mats) {
+// Resolve the device address of the scratch array for the current device, once per
+// device: host code may not pass the symbol itself to a kernel (on the host it names a
+// stand-in, not device memory).  The cached address belongs to the device's primary
+// context; after cudaDeviceReset it is stale.
+int setup_device(int dev, double **partials) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_partials_ptr[dev]) {
-        void *p = nullptr, *m = nullptr;
+        void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e == cudaSuccess) e = cudaGetSymbolAddress(&m, g_noalloc_mats);
         if (e != cudaSuccess)
             return vqg::set_error(VQG_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         g_partials_ptr[dev] = (double *)p;
-        g_mats_ptr[dev] = (double *)m;
     }
     *partials = g_partials_ptr[dev];
-    *mats = g_mats_ptr[dev];
     return VQG_OK;
 }
+
+// U^dagger of one gate (row-major (re, im) pairs), passed by value.
+struct GateMat {
+    double m[8];
+};
 
 // One adjoint step on pairs of qubit qp (the target for CNOT/CZ): reduce the four
 // complex sums o_rc = sum conj(lambda_r) phi_c (phi = phi_{i+1}, lambda = lambda_i),
@@ -69,12 +73,15 @@ int setup_device(int dev, double **partials, double **mats) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_adj_noalloc(amp_t<T> *__restrict__ phi, amp_t<T> *__restrict__ lam, int kind, int q0, int q1,
-                  const double *__restrict__ mat, uint64_t units, double *__restrict__ partials) {
+                  const GateMat mat, uint64_t units, double *__restrict__ partials) {
     const bool ent = kind == K_CNOT || kind == K_CZ;
     const int qp = ent ? q1 : q0;
     const uint64_t bit = 1ull << qp, cbit = 1ull << q0;
     Mat2<T> ud;
-    if (!ent) ud = load_mat<T>(mat);  // the table holds U^dagger
+    if (!ent) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ud.m[k] = mk<T>((T)mat.m[2 * k], (T)mat.m[2 * k + 1]);
+    }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < units; p += stride) {
@@ -102,29 +109,40 @@ __global__ void __launch_bounds__(kThreads)
     block_reduce_store<8>(acc, partials, kBlocks);
 }
 
-// grad[param of slot j of gate k] += 2 Re sum_rc D_rc o_rc, gates in the order they
-// were processed; one thread, fixed order (deterministic).
-struct SlotMap {
-    int param[kMaxGates * 3];  // parameter index of slot j of the k-th processed gate, or -1
+// grad[param of slot j of gate k] += 2 Re sum_rc D_rc o_rc.  Warp k sums gate k's eight
+// partial columns over the grid (lane l takes blocks l, l+32, ... in order, then a fixed
+// shuffle tree), so the result does not depend on timing; thread 0 then adds the slot
+// contributions gate by gate in processing order, which keeps the order fixed when
+// gates share a parameter.
+struct FinishArgs {
+    int param[kMaxGates * 3];        // parameter index of slot j of the k-th processed gate, or -1
+    double d[kMaxGates * 3 * 8];     // D_j = (dU/d slot j) U^dagger, row-major (re, im) pairs
 };
 
-__global__ void k_noalloc_finish(const double *__restrict__ partials, const double *__restrict__ mats,
-                                 const SlotMap slots, int n_gates, int grid, double *__restrict__ grad) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int k = 0; k < n_gates; ++k) {
-        double o[8];
+__global__ void __launch_bounds__(32 * kMaxGates)
+    k_noalloc_finish(const double *__restrict__ partials, const FinishArgs args, int n_gates, int grid,
+                     double *__restrict__ grad) {
+    __shared__ double o[kMaxGates][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < n_gates) {
         for (int v = 0; v < 8; ++v) {
-            const double *p = partials + ((size_t)k * 8 + v) * kBlocks;
+            const double *p = partials + ((size_t)warp * 8 + v) * kBlocks;
             double s = 0.0;
-            for (int b = 0; b < grid; ++b) s += p[b];
-            o[v] = s;
+            for (int b = lane; b < grid; b += 32) s += p[b];
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+            if (lane == 0) o[warp][v] = s;
         }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < n_gates; ++k) {
         for (int j = 0; j < 3; ++j) {
-            const int param = slots.param[3 * k + j];
+            const int param = args.param[3 * k + j];
             if (param < 0) continue;
-            const double *d = mats + 32 * (size_t)k + 8 * (j + 1);
+            const double *d = args.d + 8 * (3 * k + j);
             double acc = 0.0;
-            for (int e = 0; e < 4; ++e) acc += d[2 * e] * o[2 * e] - d[2 * e + 1] * o[2 * e + 1];
+            for (int e = 0; e < 4; ++e) acc += d[2 * e] * o[k][2 * e] - d[2 * e + 1] * o[k][2 * e + 1];
             grad[param] += 2.0 * acc;
         }
     }
@@ -189,38 +207,42 @@ extern "C" int vqg_reverse_noalloc(int n_qubits, int dtype, const vqg_gate *gate
     if (n_gates == 0) return VQG_OK;
     if (!gates || !phi || !lam || !grad || (!theta && n_params > 0))
         return set_error(VQG_ERR_INVALID, "null pointer");
-    // host-side tables on the stack: U^dagger and D_j per gate, parameter of each slot
-    double mats[kMaxGates * 32];
-    int slot_param[kMaxGates * 3];
+    // host-side tables on the stack, handed to the kernels as parameters: U^dagger per
+    // gate, D_j and the parameter index per slot
+    GateMat udag[kMaxGates];
+    FinishArgs fin;
     for (int k = 0; k < n_gates; ++k) {
         const vqg_gate &g = gates[n_gates - 1 - k];  // processing order: last gate first
         const bool one = g.kind >= VQG_RX && g.kind <= VQG_U3;
-        if (g.kind < VQG_RX || g.kind > VQG_CZ) return set_error(VQG_ERR_INVALID, "gate kind %d", g.kind);
+        if (g.kind < VQG_RX || g.kind > VQG_CZ)
+            return set_error(VQG_ERR_INVALID, "gate kind %d: vqg_reverse_noalloc takes RX, RY, RZ, U3, CNOT and CZ",
+                             g.kind);
         if (g.q0 < 0 || g.q0 >= n_qubits) return set_error(VQG_ERR_INVALID, "qubit %d out of range", g.q0);
         if (!one && (g.q1 < 0 || g.q1 >= n_qubits || g.q1 == g.q0))
             return set_error(VQG_ERR_INVALID, "bad second qubit %d", g.q1);
         const int np = g.kind == VQG_U3 ? 3 : (one ? 1 : 0);
         double a[3] = {0, 0, 0};
         for (int j = 0; j < 3; ++j) {
-            slot_param[3 * k + j] = -1;
+            fin.param[3 * k + j] = -1;
             if (j < np) {
                 if (g.param[j] < 0 || g.param[j] >= n_params)
                     return set_error(VQG_ERR_INVALID, "parameter index %d out of range", g.param[j]);
                 a[j] = theta[g.param[j]];
-                slot_param[3 * k + j] = g.param[j];
+                fin.param[3 * k + j] = g.param[j];
             }
         }
-        std::memset(mats + 32 * k, 0, 32 * sizeof(double));
+        std::memset(udag[k].m, 0, sizeof(udag[k].m));
+        std::memset(fin.d + 24 * k, 0, 24 * sizeof(double));
         if (one) {
             cd u[4], ud[4], du[4], dm[4];
             gate_u(g.kind, a, u);
             ud[0] = std::conj(u[0]); ud[1] = std::conj(u[2]); ud[2] = std::conj(u[1]); ud[3] = std::conj(u[3]);
-            put(mats + 32 * k, ud);
+            put(udag[k].m, ud);
             for (int j = 0; j < np; ++j) {
                 gate_du(g.kind, j, a, du);
                 for (int r = 0; r < 2; ++r)
                     for (int c = 0; c < 2; ++c) dm[2 * r + c] = du[2 * r] * ud[c] + du[2 * r + 1] * ud[2 + c];
-                put(mats + 32 * k + 8 * (j + 1), dm);
+                put(fin.d + 8 * (3 * k + j), dm);
             }
         }
     }
@@ -228,13 +250,10 @@ extern "C" int vqg_reverse_noalloc(int n_qubits, int dtype, const vqg_gate *gate
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return set_error(VQG_ERR_UNSUPPORTED, "device %d", dev);
-    double *partials = nullptr, *dmats = nullptr;
-    int st = setup_device(dev, &partials, &dmats);
+    double *partials = nullptr;
+    int st = setup_device(dev, &partials);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemcpyToSymbolAsync(g_noalloc_mats, mats, sizeof(double) * 32 * n_gates, 0,
-                                cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "copy of gate tables: %s", cudaGetErrorString(e));
     const uint64_t pairs = 1ull << (n_qubits - 1);
     const int grid = (int)std::min<uint64_t>(kBlocks, std::max<uint64_t>(1, (pairs + kThreads - 1) / kThreads));
     for (int k = 0; k < n_gates; ++k) {
@@ -242,14 +261,12 @@ extern "C" int vqg_reverse_noalloc(int n_qubits, int dtype, const vqg_gate *gate
         double *part = partials + (size_t)k * 8 * kBlocks;
         if (dtype == VQG_C64)
             k_adj_noalloc<float><<<grid, kThreads, 0, s>>>((float2 *)phi, (float2 *)lam, g.kind, g.q0, g.q1,
-                                                          dmats + 32 * (size_t)k, pairs, part);
+                                                          udag[k], pairs, part);
         else
             k_adj_noalloc<double><<<grid, kThreads, 0, s>>>((double2 *)phi, (double2 *)lam, g.kind, g.q0, g.q1,
-                                                           dmats + 32 * (size_t)k, pairs, part);
+                                                           udag[k], pairs, part);
     }
-    SlotMap sm;
-    std::memcpy(sm.param, slot_param, sizeof(int) * 3 * n_gates);
-    k_noalloc_finish<<<1, 32, 0, s>>>(partials, dmats, sm, n_gates, grid, grad);
+    k_noalloc_finish<<<1, 32 * n_gates, 0, s>>>(partials, fin, n_gates, grid, grad);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
     return VQG_OK;

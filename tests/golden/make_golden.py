@@ -7,7 +7,11 @@ workload recipe, the oracle routine used and the paper passage it follows:
     Algorithm 2 routes and dense brute force in tests/test_oracle_pins.py;
   * E alone by oracle.energy (Sec. 2.2) where the gradient is out of reach on the CPU.
 
-python tests/golden/make_golden.py cfg2 cfg5 cfg3e
+python tests/golden/make_golden.py cfg2 cfg5 cfg3e cfg3n29
+
+cfg3n29 is the n=30 bench recipe (RY/RZ + CZ brickwork, 200 random Pauli strings) at
+n=29: its full Algorithm 1 gradient needs four complex128 states (32 GiB) of host memory,
+the largest size of that recipe that fits a 62 GB host.
 """
 import json
 import os
@@ -30,8 +34,8 @@ def write(name, payload):
     print("wrote", path, flush=True)
 
 
-def grad_fixture(cfg):
-    w = W.config(cfg)
+def grad_fixture(cfg, n=None):
+    w = W.config(cfg, n=n)
     t0 = time.time()
     e, g = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
     write(f"cfg{cfg}_n{w.n}", {
@@ -56,5 +60,7 @@ if __name__ == "__main__":
     for arg in sys.argv[1:] or ["cfg2", "cfg5", "cfg3e"]:
         if arg == "cfg3e":
             energy_fixture(3)
+        elif arg == "cfg3n29":
+            grad_fixture(3, n=29)
         else:
             grad_fixture(int(arg[3:]))

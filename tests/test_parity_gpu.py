@@ -522,3 +522,28 @@ def test_hadamard_product_full_size_closed_form(dtype):
         c.set_product_operator([(1.0, [HAD] * n)])
         e, g = c.energy_and_gradient(t)
         assert_parity(dtype, e, g, e_ref, g_ref, "H^30")
+
+
+@pytest.mark.parametrize("theta0", [np.pi / 2, np.pi / 2 + 1e-6, 3 * np.pi / 2, np.pi / 2 - 3e-7])
+def test_long_scaled_ry_stages(theta0):
+    """complex64 RY ops run in a scaled form whose dropped factors |k| >= 2^-1/2 multiply up
+    over a register stage; theta = pi/2 (+-) makes every |k| = 2^-1/2, the largest total
+    scale.  Long runs of RY on the low qubits (register qubits of the tile passes) with a
+    CZ ladder between runs, against the oracle at the complex64 bar."""
+    n = 12
+    rng = np.random.default_rng(31)
+    gates, P = [], 0
+    for rep in range(12):
+        for q in range(6):
+            gates.append(("RY", q, -1, (P, -1, -1)))
+            P += 1
+        if rep % 3 == 2:
+            for q in range(0, n - 1, 2):
+                gates.append(("CZ", q, q + 1, (-1, -1, -1)))
+    theta = np.full(P, theta0) + rng.uniform(-1e-7, 1e-7, P) * (theta0 != np.pi / 2)
+    terms = W.random_paulis(rng, n, 12, 4)
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    with _circ(n, gates, P, "c64", terms) as c:
+        assert c.plan()["tile_qubits"] > 0
+        e, g = c.energy_and_gradient(theta)
+        assert_parity("c64", e, g, e_ref, g_ref, f"theta0={theta0}")

@@ -1,5 +1,6 @@
 """vqg_reverse_noalloc, the entry point that allocates nothing, checked against the
-regular vqg_energy_and_gradient on the same circuit.
+regular vqg_energy_and_gradient on the same circuit and against the CPU oracle's
+Algorithm 1 gradient.
 
 Callers that may not allocate device memory while they run (a framework's caching
 pool owns the GPU, the footprint is fixed at start-up, or a latency-critical thread
@@ -25,6 +26,14 @@ def _case():
     return n, gates, P, theta, terms
 
 
+@pytest.mark.parametrize("kind", ["CRX", "CRY", "CRZ", "PHASE", "CPHASE"])
+def test_rejects_controlled_and_phase_gates(kind):
+    gate = (kind, 0, 1, (0, -1, -1)) if kind != "PHASE" else (kind, 0, -1, (0, -1, -1))
+    with pytest.raises(B.VqgError) as ei:
+        B.reverse_noalloc(3, "c64", [gate], np.zeros(1), 1, 1, 1, 1)
+    assert ei.value.status == -1 and "RX, RY, RZ, U3, CNOT and CZ" in str(ei.value)
+
+
 def test_rejects_too_many_gates():
     n, gates, P, theta, _terms = _case()
     big = gates[: B.NOALLOC_MAX_GATES + 1]
@@ -46,6 +55,7 @@ def test_noalloc_matches_energy_and_gradient(dtype):
     # psi and lambda = H psi as the reverse sweep starts (Algorithm 1, before the reverse loop)
     psi = oracle.state(n, gates, theta)
     lam = oracle.apply_hamiltonian(psi, terms)
+    e_or, g_or = oracle.gradient_alg1(n, gates, theta, P, terms)
     cdt = torch.complex64 if dtype == "c64" else torch.complex128
     stream = torch.cuda.current_stream()
     segments = [gates[i:i + B.NOALLOC_MAX_GATES] for i in range(0, len(gates), B.NOALLOC_MAX_GATES)]
@@ -69,6 +79,7 @@ def test_noalloc_matches_energy_and_gradient(dtype):
             assert abs(np.linalg.norm(l_) - nl) <= tol * max(1.0, nl)
         g = grad_d.cpu().numpy()
         assert grad_err(g, g_ref) <= TOL[dtype], grad_err(g, g_ref)
+        assert grad_err(g, g_or) <= TOL[dtype], grad_err(g, g_or)
         # phi has been swept back to the input state |0...0>
         phi_end = phi_d.cpu().numpy()
         assert abs(phi_end[0]) == pytest.approx(1.0, abs=1e-10 if dtype == "c128" else 1e-5)
