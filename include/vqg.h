@@ -227,6 +227,42 @@ typedef struct vqg_plan_info {
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 
+/* Precision diagnostics (complex64 amplitudes with FP64 reductions and forward
+ * checkpoints; the invariants of Algorithm 1's recurrence, Sec. 2.3: phi and lambda are
+ * un-applied by the same unitaries, so <lambda_i|phi_{i+1}> = E and ||lambda_i|| is
+ * constant).  vqg_set_diagnostics(c, 1) makes every later gradient call of c also take,
+ * in FP64 on the GPU: ||psi||^2, E and ||lambda||^2 after the Hamiltonian; ||psi_c||^2 of
+ * every forward checkpoint when it is stored; and at every reverse restart from a
+ * checkpoint, <lambda|psi_c>, ||lambda||^2, the norm of the phi the sweep had un-applied
+ * up to there and its distance to psi_c (the drift the restart removes).  It costs one
+ * streaming pass over one or two states per value set, makes the reverse sweep store
+ * its un-applied phi, and runs the calls eagerly (no CUDA graph); 0 turns it off.
+ * vqg_diagnostics reads the values of the last gradient call (blocking on the circuit's
+ * stream): summary (nullable) and entries[0 .. min(count, max_entries)) (host memory),
+ * one per checkpoint in forward order; returns the checkpoint count, or VQG_ERR_STATE when
+ * no call recorded diagnostics.  Results are unchanged by diagnostics. */
+typedef struct vqg_diag_summary {
+    double energy;        /* Re <psi|lambda> of the final state                           */
+    double norm2_psi;     /* ||psi||^2 of the final forward state                          */
+    double norm2_lambda;  /* ||lambda||^2 = ||H psi||^2 as the reverse sweep starts        */
+    int32_t checkpoints;  /* checkpoint entries recorded                                    */
+    int32_t reserved;
+} vqg_diag_summary;
+typedef struct vqg_checkpoint_diag {
+    int32_t checkpoint;      /* index, forward order                                        */
+    int32_t stored;          /* 1: the forward sweep stored it in the last call             */
+    int32_t restarted;       /* 1: the reverse sweep restarted phi from it                   */
+    int32_t reserved;
+    double norm2;            /* ||psi_c||^2 when stored                                      */
+    double lam_phi_re;       /* Re <lambda|psi_c> at the restart (invariant: E)              */
+    double lam_phi_im;       /* Im <lambda|psi_c> at the restart (invariant: 0)              */
+    double norm2_lambda;     /* ||lambda||^2 at the restart (invariant: ||H psi||^2)         */
+    double norm2_unapplied;  /* ||phi||^2 of the un-applied phi the restart replaces         */
+    double drift2;           /* ||phi_unapplied - psi_c||^2                                  */
+} vqg_checkpoint_diag;
+int vqg_set_diagnostics(vqg_circuit *c, int enable);
+int vqg_diagnostics(vqg_circuit *c, vqg_diag_summary *summary, int max_entries, vqg_checkpoint_diag *entries);
+
 /* Plan a circuit and Hamiltonian on the host only (no GPU is touched): the same tile
  * passes, register stages and Hamiltonian passes a vqg_circuit with these options
  * would run, checked index by index, with the stage, op and diagonal-block counts

@@ -50,6 +50,18 @@ class vqg_options(ctypes.Structure):
 C128_ARITH = {"fp64": 0, "float-float": 1}
 
 
+class vqg_diag_summary(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("norm2_psi", ctypes.c_double), ("norm2_lambda", ctypes.c_double),
+                ("checkpoints", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class vqg_checkpoint_diag(ctypes.Structure):
+    _fields_ = [("checkpoint", ctypes.c_int32), ("stored", ctypes.c_int32), ("restarted", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("norm2", ctypes.c_double), ("lam_phi_re", ctypes.c_double),
+                ("lam_phi_im", ctypes.c_double), ("norm2_lambda", ctypes.c_double),
+                ("norm2_unapplied", ctypes.c_double), ("drift2", ctypes.c_double)]
+
+
 class vqg_plan_info(ctypes.Structure):
     _fields_ = [("forward_passes", ctypes.c_int32), ("hamiltonian_passes", ctypes.c_int32),
                 ("reverse_passes", ctypes.c_int32), ("launches_per_gradient", ctypes.c_int32),
@@ -91,6 +103,8 @@ def lib():
             "vqg_circuit_destroy": (i, [p]),
             "vqg_set_hamiltonian": (i, [p, i, p, p, p]),
             "vqg_set_hamiltonian_strings": (i, [p, i, p, p]),
+            "vqg_set_diagnostics": (i, [p, i]),
+            "vqg_diagnostics": (i, [p, p, i, p]),
             "vqg_pauli_strings_to_masks": (i, [i, i, p, p, p]),
             "vqg_set_stream": (i, [p, p]),
             "vqg_energy": (i, [p, p, p]),
@@ -378,6 +392,24 @@ class Circuit:
         _check(lib().vqg_plan(self._h, ctypes.byref(info)))
         return {k: getattr(info, k) for k, _t in vqg_plan_info._fields_
                 if k not in ("reserved", "forward_stages", "reverse_stages", "stage_ops", "diag_blocks")}
+
+    def set_diagnostics(self, enable: bool = True):
+        """Record FP64 norms and inner products along later gradient calls (vqg_set_diagnostics)."""
+        _check(lib().vqg_set_diagnostics(self._h, 1 if enable else 0))
+
+    def diagnostics(self) -> dict:
+        """Values of the last gradient call with diagnostics on: the summary plus one dict
+        per forward checkpoint (vqg_diagnostics)."""
+        summ = vqg_diag_summary()
+        cap = 64
+        arr = (vqg_checkpoint_diag * cap)()
+        n = lib().vqg_diagnostics(self._h, ctypes.byref(summ), cap, ctypes.cast(arr, ctypes.c_void_p))
+        if n < 0:
+            _check(n)
+        out = {k: getattr(summ, k) for k, _t in vqg_diag_summary._fields_ if k != "reserved"}
+        out["entries"] = [{k: getattr(arr[i], k) for k, _t in vqg_checkpoint_diag._fields_ if k != "reserved"}
+                          for i in range(min(n, cap))]
+        return out
 
     def autotune(self, theta=None) -> dict:
         """Time candidate fused schedules on this circuit and keep the fastest."""

@@ -468,6 +468,7 @@ int Circuit::issue_forward(bool with_ckpt) {
             prof_begin(FAM_CKPT);
             VQG_CUDA(cudaMemcpyAsync(ckpt_buf[k], psi, state_bytes, cudaMemcpyDeviceToDevice, stream));
             prof_end();
+            if (int st = diag_reduce(ckpt_buf[k], nullptr, DIAG_STORE, (int)k)) return st;
             ++k;
         }
     }
@@ -508,7 +509,11 @@ int Circuit::issue_reverse() {
         const vqg_gate &g = gates[i];
         const void *src = psi;
         while (k >= 0 && ckpt_pos[k] > i + 1) --k;
-        if (k >= 0 && ckpt_pos[k] == i + 1) src = ckpt_buf[k];  // restart phi from the stored state
+        if (k >= 0 && ckpt_pos[k] == i + 1) {  // restart phi from the stored state
+            src = ckpt_buf[k];
+            if (int st = diag_reduce(ckpt_buf[k], lam, DIAG_RESTART, k)) return st;
+            if (int st = diag_reduce(psi, ckpt_buf[k], DIAG_UNAPPLIED, k)) return st;
+        }
         prof_begin(FAM_ADJ_GATE);
         launch_adj_gate(src, psi, lam, n, dbl, g.kind, g.q0, g.q1, d_mats + 8 * (size_t)i,
                         gpart + (size_t)slot_base[i] * nb, nb, i > 0, i > 0, stream);
@@ -530,11 +535,17 @@ int Circuit::issue_finalize(double *energy_dev, double *grad_dev, const double *
 
 int Circuit::issue_gradient(const double *theta_dev, double *energy_dev, double *grad_dev) {
     int st;
-    if ((st = issue_table(theta_dev, -1, -1, 0.0))) return st;
-    if ((st = issue_forward(true))) return st;
-    if ((st = issue_hamiltonian(true))) return st;
-    if ((st = issue_reverse())) return st;
-    return issue_finalize(energy_dev, grad_dev, theta_dev);
+    diag_active = false;
+    if (diagnostics) {  // FP64 norms and inner products along the sweep (diag.cu)
+        if ((st = diag_prepare())) return st;
+        diag_active = true;
+    }
+    if (!(st = issue_table(theta_dev, -1, -1, 0.0)) && !(st = issue_forward(true)) && !(st = issue_hamiltonian(true)) &&
+        !(st = diag_reduce(psi, lam, DIAG_FINAL, 0)) && !(st = issue_reverse()) &&
+        !(st = issue_finalize(energy_dev, grad_dev, theta_dev)))
+        st = diag_finish();
+    diag_active = false;
+    return st;
 }
 
 // With use_graph, the launch sequence of one call (it does not depend on theta: the
@@ -553,7 +564,8 @@ int Circuit::run_gradient(const double *theta_dev, double *energy_dev, double *g
         int st = autotune(theta_dev, nullptr);
         if (st) return st;
     }
-    const bool graphable = opt.use_graph && !profiling && stream != cudaStreamLegacy && stream != nullptr;
+    const bool graphable =
+        opt.use_graph && !profiling && !diagnostics && stream != cudaStreamLegacy && stream != nullptr;
     if (!graphable) return issue_gradient(theta_dev, energy_dev, grad_dev);
     const void *key[3] = {theta_dev, energy_dev, grad_dev};
     if (graph_exec_grad && std::memcmp(key, graph_key_grad, sizeof key) != 0) {

@@ -898,6 +898,8 @@ int Circuit::issue_forward_fused(bool with_ckpt) {
         launch_fused_fwd(dbl, float_float(dbl, opt), pl->K, pl->Rf, in, out, pl->d_passes, (int)j, pl->d_stages,
                          pl->d_ops, pl->d_diags, pl->d_items, mats, pl->n_tiles, pl->grid_fwd, stream);
         prof_end();
+        if (k >= 0)
+            if (int st = diag_reduce(out, nullptr, DIAG_STORE, k)) return st;
         in = out;
     }
     cudaError_t e = cudaGetLastError();
@@ -930,9 +932,14 @@ int Circuit::issue_reverse_fused() {
     for (int j = (int)pl->passes.size() - 1; j >= 0; --j) {
         const int k = pl->ckpt_of_pass[j];
         const void *src = k >= 0 ? ckpt_buf[k] : psi;  // restart phi from the stored state
-        // phi_j is read only if the next reverse pass does not restart from a checkpoint;
-        // nothing reads phi or lambda after the last reverse pass
-        const bool write_phi = j > 0 && pl->ckpt_of_pass[j - 1] < 0, write_lam = j > 0;
+        if (k >= 0) {
+            if (int st = diag_reduce(src, lam, DIAG_RESTART, k)) return st;
+            if (int st = diag_reduce(psi, src, DIAG_UNAPPLIED, k)) return st;
+        }
+        // phi_j is read only if the next reverse pass does not restart from a checkpoint
+        // (or diagnostics compare it with that checkpoint); nothing reads phi or lambda
+        // after the last reverse pass
+        const bool write_phi = j > 0 && (pl->ckpt_of_pass[j - 1] < 0 || diag_active), write_lam = j > 0;
         prof_begin(FAM_ADJ_FUSED);
         auto rev = !dbl ? launch_fused_rev_c64 : float_float(dbl, opt) ? launch_fused_rev_df : launch_fused_rev_c128;
         rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,

@@ -31,6 +31,9 @@ struct HamGroup {
 int group_pauli_terms(int n, int n_terms, const uint64_t *x_mask, const uint64_t *z_mask,
                       const double *coef, std::vector<HamGroup> &ham, std::vector<PauliTerm> &flat);
 
+// What a diagnostic reduction measured (diag.cu).
+enum { DIAG_FINAL = 0, DIAG_STORE = 1, DIAG_RESTART = 2, DIAG_UNAPPLIED = 3 };
+
 struct PendingEvent {
     int fam;
     cudaEvent_t start, stop;
@@ -110,6 +113,19 @@ struct Circuit {
     void free_products();
     int upload_plan(Plan *pl);
     void release_plan(Plan *pl);
+
+    // precision diagnostics (diag.cu): FP64 norms and inner products of the stored
+    // checkpoints and of phi and lambda at every reverse restart, recorded by gradient
+    // calls while enabled (those calls run eagerly, outside any graph)
+    bool diagnostics = false;
+    bool diag_active = false;          // set during a gradient call with diagnostics on
+    double *d_diag_part = nullptr;     // [5 * reduction][nb] block partials (k_norm.cu)
+    double *d_diag_red = nullptr;      // [5 * reduction] reduced values
+    int diag_cap = 0;                  // reductions the buffers hold
+    std::vector<int> diag_tag;         // kind and checkpoint of each queued reduction
+    int diag_prepare();                // size the buffers for this circuit's checkpoints
+    int diag_reduce(const void *a, const void *b, int kind, int ckpt);
+    int diag_finish();
 
     // graphs
     cudaGraphExec_t graph_exec_grad = nullptr, graph_exec_energy = nullptr;

@@ -31,6 +31,12 @@ void launch_finalize(const double *red_e, int e_count, const double *red_g, cons
                      const Occurrence *occ, int P, double *out_energy, double *out_grad,
                      cudaStream_t s);
 
+// --- FP64 norms and inner products (k_norm.cu): per-block partials of ||a||^2, Re <a|b>,
+// Im <a|b>, ||b||^2, ||a - b||^2 into partials[v * nb + block], v = 0..4 (kNormValues);
+// b = nullptr means b = a.
+constexpr int kNormValues = 5;
+void launch_norm_dot(const void *a, const void *b, int n, bool dbl, double *partials, int nb, cudaStream_t s);
+
 // --- one kernel per gate (k_gate.cu)
 void launch_fwd_gate(void *psi, int n, bool dbl, int kind, int q0, int q1, const double *mat,
                      int nb, cudaStream_t s);
