@@ -81,6 +81,20 @@ template <int R, typename F> VQG_DEV void with_k(int k, F &&f) {
 
 template <typename T> VQG_DEV amp_t<T> neg(amp_t<T> a) { return mk<T>(-a.x, -a.y); }
 
+// a * b + c in the tile arithmetic
+template <typename T> VQG_DEV T fma_t(T a, T b, T c);
+template <> VQG_DEV float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> VQG_DEV double fma_t<double>(double a, double b, double c) { return ::fma(a, b, c); }
+template <> VQG_DEV df fma_t<df>(df a, df b, df c) { return vqg::fma(a, b, c); }
+
+// v with its sign flipped where s (0 or 0x80000000) is set: a logic op on the sign bit.
+template <typename T> VQG_DEV T flip_sign(T v, uint32_t s);
+template <> VQG_DEV float flip_sign<float>(float v, uint32_t s) { return __uint_as_float(__float_as_uint(v) ^ s); }
+template <> VQG_DEV double flip_sign<double>(double v, uint32_t s) {
+    return __hiloint2double(__double2hiint(v) ^ (int)s, __double2loint(v));
+}
+template <> VQG_DEV df flip_sign<df>(df v, uint32_t s) { return df(flip_sign<float>(v.hi, s), flip_sign<float>(v.lo, s)); }
+
 // ------------------------------------------------------------------ gate ops (forward)
 template <int KB, int NA, typename T>
 VQG_DEV void op_ry(amp_t<T> (&a)[NA], T c, T s) {
@@ -1224,7 +1238,7 @@ struct HamCfg {
     static constexpr int NT = 256;
     static constexpr size_t o_row = (size_t)(1 << K) * FT<T>::AB;
     static constexpr size_t o_tab = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
-    static constexpr size_t tab_bytes = (sizeof(uint32_t) * 5 + 2 * sizeof(T)) * kMaxHamGroups +
+    static constexpr size_t tab_bytes = (sizeof(uint32_t) * 6 + 2 * sizeof(T)) * kMaxHamGroups +
                                         (2 * sizeof(uint32_t) + sizeof(uint64_t) + 2 * 2 * sizeof(T)) * kMaxHamTerms;
     static constexpr size_t smem() { return o_tab + tab_bytes; }
 };
@@ -1240,8 +1254,10 @@ struct HamTab {
     amp_t<T> *t_w, *t_weff;
     uint32_t *t_zl, *t_cls, *g_xs, *g_t0, *g_nt;
     // a single-term group's term, indexed by the group (no dependent second lookup);
-    // g_w is its weight with the tile's sign, refreshed per tile
-    uint32_t *g_zl, *g_cls;
+    // g_w is its weight with the tile's sign, refreshed per tile; g_kind says whether the
+    // weight is real (0), imaginary (1) or neither (2): a Pauli string's weight is its real
+    // coefficient times i^{popcount(x & z)}, so it is real or imaginary
+    uint32_t *g_zl, *g_cls, *g_kind;
     amp_t<T> *g_w;
     int ng, n_terms;
     VQG_DEV void bind(unsigned char *p) {
@@ -1256,6 +1272,7 @@ struct HamTab {
         g_zl = g_nt + kMaxHamGroups;
         g_cls = g_zl + kMaxHamGroups;
         g_w = reinterpret_cast<amp_t<T> *>(g_cls + kMaxHamGroups);  // 16-byte aligned: see tab_bytes
+        g_kind = reinterpret_cast<uint32_t *>(g_w + kMaxHamGroups);
     }
     // class bit d = bit of z_l at the d-th varying position of a batch
     template <int D, int SH, int E0>
@@ -1280,9 +1297,10 @@ struct HamTab {
             g_t0[g] = (uint32_t)(G.term0 - term_base);
             g_nt[g] = (uint32_t)G.n_term;
             if (G.n_term == 1) {
-                const uint32_t zl = terms[G.term0].zl;
-                g_zl[g] = zl;
-                g_cls[g] = class_of<D, SH, E0>(zl);
+                const HTerm &tm = terms[G.term0];
+                g_zl[g] = tm.zl;
+                g_cls[g] = class_of<D, SH, E0>(tm.zl);
+                g_kind[g] = tm.wi == 0.0 ? 0u : (tm.wr == 0.0 ? 1u : 2u);
             }
         }
         for (int k = tid; k < n_terms; k += nt) {
@@ -1368,6 +1386,35 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
         for (int g = 0; g < tb.ng; ++g) {
             const uint32_t xs = tb.g_xs[g];
             const int j0 = tb.g_t0[g], nt_g = tb.g_nt[g];
+            if (nt_g == 1 && tb.g_kind[g] < 2) {
+                // one term with a real (or imaginary) weight w: the factor at batch amplitude
+                // k is +-w, the sign bit parity(t0 & z_l) ^ parity(k & class) set straight
+                // into w's sign (one logic op), then a real (or i times real) multiply-add
+                const uint32_t zl = tb.g_zl[g], cls = tb.g_cls[g];
+                const uint32_t s0 = (uint32_t)__popc(t0 & zl) << 31;
+                const uint32_t c0 = cls << 31, c1 = (cls >> 1) << 31, c2 = (cls >> 2) << 31;
+                const A w = tb.g_w[g];
+                if (tb.g_kind[g] == 0) {
+#pragma unroll
+                    for (int k = 0; k < BA; ++k) {
+                        const uint32_t sk = s0 ^ ((k & 1) ? c0 : 0u) ^ ((k & 2) ? c1 : 0u) ^ ((k & 4) ? c2 : 0u);
+                        const T ws = flip_sign<T>(w.x, sk);
+                        const A p = tile[sw[k] ^ xs];
+                        delta[k].x = fma_t<T>(ws, p.x, delta[k].x);
+                        delta[k].y = fma_t<T>(ws, p.y, delta[k].y);
+                    }
+                } else {  // w = i v: w p = (-v p.y, v p.x)
+#pragma unroll
+                    for (int k = 0; k < BA; ++k) {
+                        const uint32_t sk = s0 ^ ((k & 1) ? c0 : 0u) ^ ((k & 2) ? c1 : 0u) ^ ((k & 4) ? c2 : 0u);
+                        const T vs = flip_sign<T>(w.y, sk);
+                        const A p = tile[sw[k] ^ xs];
+                        delta[k].x = fma_t<T>(-vs, p.y, delta[k].x);
+                        delta[k].y = fma_t<T>(vs, p.x, delta[k].y);
+                    }
+                }
+                continue;
+            }
             A f[BA];
             if (nt_g == 1) {  // one term: f = +-w with the sign pattern of its class
                 const uint32_t zl = tb.g_zl[g], cls = tb.g_cls[g];

@@ -533,6 +533,11 @@ def test_long_scaled_ry_stages(theta0):
     n = 12
     rng = np.random.default_rng(31)
     gates, P = [], 0
+    for q in range(n):  # a random preparing layer, so that no gradient entry vanishes by symmetry
+        gates.append(("RX", q, -1, (P, -1, -1)))
+        gates.append(("RZ", q, -1, (P + 1, -1, -1)))
+        P += 2
+    n_prep = P
     for rep in range(12):
         for q in range(6):
             gates.append(("RY", q, -1, (P, -1, -1)))
@@ -541,6 +546,7 @@ def test_long_scaled_ry_stages(theta0):
             for q in range(0, n - 1, 2):
                 gates.append(("CZ", q, q + 1, (-1, -1, -1)))
     theta = np.full(P, theta0) + rng.uniform(-1e-7, 1e-7, P) * (theta0 != np.pi / 2)
+    theta[:n_prep] = rng.uniform(0, 2 * np.pi, n_prep)
     terms = W.random_paulis(rng, n, 12, 4)
     e_ref, g_ref = _oracle(n, gates, theta, P, terms)
     with _circ(n, gates, P, "c64", terms) as c:
