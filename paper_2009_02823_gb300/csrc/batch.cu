@@ -294,7 +294,7 @@ struct vqg_batch {
     int upload(X **d, const std::vector<X> &h) {
         int st = dalloc((void **)d, sizeof(X) * std::max<size_t>(h.size(), 1));
         if (st) return st;
-        if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(X) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (!h.empty() && h2d(*d, h.data(), sizeof(X) * h.size()) != cudaSuccess)
             return set_error(VQG_ERR_CUDA, "batch upload failed");
         return VQG_OK;
     }

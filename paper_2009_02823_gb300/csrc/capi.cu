@@ -31,6 +31,11 @@ int vqg::set_error(int status, const char *fmt, ...) {
     return status;
 }
 
+cudaError_t vqg::h2d(void *dst, const void *src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cudaStreamLegacy);
+    return e == cudaSuccess ? cudaStreamSynchronize(cudaStreamLegacy) : e;
+}
+
 extern "C" const char *vqg_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char *vqg_status_string(int status) {
@@ -252,15 +257,15 @@ int Circuit::init(int n_, const vqg_gate *gates_, int G_, int P_, int dtype_, co
     std::vector<DevGate> dg(std::max(G, 1));
     for (int i = 0; i < G; ++i) dg[i] = {gates[i].kind, gates[i].q0, gates[i].q1, gates[i].param[0], gates[i].param[1], gates[i].param[2]};
     if ((st = dalloc((void **)&d_gates, sizeof(DevGate) * dg.size()))) return st;
-    VQG_CUDA(cudaMemcpy(d_gates, dg.data(), sizeof(DevGate) * dg.size(), cudaMemcpyHostToDevice));
+    VQG_CUDA(h2d(d_gates, dg.data(), sizeof(DevGate) * dg.size()));
     if ((st = dalloc((void **)&d_mats, sizeof(double) * 8 * std::max(G, 1)))) return st;
     if ((st = dalloc((void **)&d_slot_base, sizeof(int) * slot_base.size()))) return st;
-    VQG_CUDA(cudaMemcpy(d_slot_base, slot_base.data(), sizeof(int) * slot_base.size(), cudaMemcpyHostToDevice));
+    VQG_CUDA(h2d(d_slot_base, slot_base.data(), sizeof(int) * slot_base.size()));
     if ((st = dalloc((void **)&d_occ_ptr, sizeof(int) * occ_ptr.size()))) return st;
-    VQG_CUDA(cudaMemcpy(d_occ_ptr, occ_ptr.data(), sizeof(int) * occ_ptr.size(), cudaMemcpyHostToDevice));
+    VQG_CUDA(h2d(d_occ_ptr, occ_ptr.data(), sizeof(int) * occ_ptr.size()));
     if ((st = dalloc((void **)&d_occ, sizeof(Occurrence) * std::max<size_t>(occ.size(), 1)))) return st;
     if (!occ.empty())
-        VQG_CUDA(cudaMemcpy(d_occ, occ.data(), sizeof(Occurrence) * occ.size(), cudaMemcpyHostToDevice));
+        VQG_CUDA(h2d(d_occ, occ.data(), sizeof(Occurrence) * occ.size()));
     if ((st = dalloc((void **)&d_theta, sizeof(double) * std::max(P, 1)))) return st;
     if ((st = dalloc((void **)&d_out, sizeof(double) * (P + 1)))) return st;
     VQG_CUDA(cudaMallocHost((void **)&h_pinned, sizeof(double) * (2 * (size_t)P + 2)));
@@ -422,7 +427,7 @@ int Circuit::set_groups(const std::vector<HamGroup> &groups, const std::vector<P
     d_terms = nullptr;
     if ((st = dalloc((void **)&d_terms, sizeof(PauliTerm) * std::max<size_t>(flat.size(), 1)))) return st;
     if (!flat.empty())
-        VQG_CUDA(cudaMemcpy(d_terms, flat.data(), sizeof(PauliTerm) * flat.size(), cudaMemcpyHostToDevice));
+        VQG_CUDA(h2d(d_terms, flat.data(), sizeof(PauliTerm) * flat.size()));
     n_terms = (int)flat.size();
     host_terms = flat;
     n_eslots = std::max(n_eslots, (int)ham.size());

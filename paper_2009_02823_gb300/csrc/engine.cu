@@ -663,7 +663,7 @@ int Circuit::upload_plan(Plan *pl) {
         const size_t elem = sizeof(vec[0]);
         int s2 = dalloc(d, elem * std::max<size_t>(vec.size(), 1));
         if (s2) return s2;
-        if (!vec.empty() && cudaMemcpy(*d, vec.data(), elem * vec.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (!vec.empty() && h2d(*d, vec.data(), elem * vec.size()) != cudaSuccess)
             return set_error(VQG_ERR_CUDA, "plan upload failed");
         return VQG_OK;
     };
@@ -849,9 +849,9 @@ int Circuit::build_ham_plan() {
     if ((st = dalloc((void **)&pl->d_hp, sizeof(HPass) * pl->hp.size()))) return st;
     if ((st = dalloc((void **)&pl->d_hg, sizeof(HGroup) * std::max<size_t>(pl->hg.size(), 1)))) return st;
     if ((st = dalloc((void **)&pl->d_ht, sizeof(HTerm) * std::max<size_t>(pl->ht.size(), 1)))) return st;
-    cudaMemcpy(pl->d_hp, pl->hp.data(), sizeof(HPass) * pl->hp.size(), cudaMemcpyHostToDevice);
-    if (!pl->hg.empty()) cudaMemcpy(pl->d_hg, pl->hg.data(), sizeof(HGroup) * pl->hg.size(), cudaMemcpyHostToDevice);
-    if (!pl->ht.empty()) cudaMemcpy(pl->d_ht, pl->ht.data(), sizeof(HTerm) * pl->ht.size(), cudaMemcpyHostToDevice);
+    h2d(pl->d_hp, pl->hp.data(), sizeof(HPass) * pl->hp.size());
+    if (!pl->hg.empty()) h2d(pl->d_hg, pl->hg.data(), sizeof(HGroup) * pl->hg.size());
+    if (!pl->ht.empty()) h2d(pl->d_ht, pl->ht.data(), sizeof(HTerm) * pl->ht.size());
     if (cudaGetLastError() != cudaSuccess) return set_error(VQG_ERR_CUDA, "Hamiltonian plan upload failed");
     ham_plan_ok = true;
     return VQG_OK;

@@ -15,6 +15,10 @@ namespace vqg {
 struct Plan;
 struct AltHam;
 int set_error(int status, const char *fmt, ...);
+// Host-to-device copy of a table that has landed when the call returns.  A plain cudaMemcpy
+// from pageable memory may return before its DMA completes, and it runs on the legacy
+// stream, which the library's non-blocking streams do not wait for.
+cudaError_t h2d(void *dst, const void *src, size_t bytes);
 int vqg_validate_circuit(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype);
 
 enum Family {

@@ -1233,6 +1233,10 @@ __global__ void __launch_bounds__(1 << (K - R))
 //   (-1)^{popcount(j & z)} = (-1)^{popcount(base & z_nt)} (-1)^{popcount(t & z_l)},
 // so the first factor is folded into the weight once per tile and the inner loop is a
 // 32-bit popcount per amplitude.
+// Groups of up to this many terms add each term into the batch factors directly; larger
+// ones sum per class and transform (see ham_tile).
+constexpr int kHamDirectTerms = 6;
+
 template <typename T, int K>
 struct HamCfg {
     static constexpr int NT = 256;
@@ -1252,11 +1256,14 @@ struct HamTab {
     static constexpr int AB = FT<T>::AB;
     uint64_t *t_znt;
     amp_t<T> *t_w, *t_weff;
-    uint32_t *t_zl, *t_cls, *g_xs, *g_t0, *g_nt;
+    uint32_t *t_zl, *g_xs, *g_t0, *g_nt;
+    // the terms of a group are sorted by class once per launch; g_cend[8 g + c] is the end
+    // of class c's run, counted from the group's first term
+    uint16_t *g_cend;
     // a single-term group's term, indexed by the group (no dependent second lookup);
-    // g_w is its weight with the tile's sign, refreshed per tile; g_kind says whether the
-    // weight is real (0), imaginary (1) or neither (2): a Pauli string's weight is its real
-    // coefficient times i^{popcount(x & z)}, so it is real or imaginary
+    // g_w is its weight with the tile's sign, refreshed per tile.  g_kind says whether the
+    // group's weights are all real (0), all imaginary (1) or mixed (2): a Pauli string's
+    // weight is its real coefficient times i^{popcount(x & z)}, so it is real or imaginary
     uint32_t *g_zl, *g_cls, *g_kind;
     amp_t<T> *g_w;
     int ng, n_terms;
@@ -1265,8 +1272,10 @@ struct HamTab {
         t_w = reinterpret_cast<amp_t<T> *>(t_znt + kMaxHamTerms);
         t_weff = t_w + kMaxHamTerms;
         t_zl = reinterpret_cast<uint32_t *>(t_weff + kMaxHamTerms);
-        t_cls = t_zl + kMaxHamTerms;
-        g_xs = t_cls + kMaxHamTerms;
+        g_cend = reinterpret_cast<uint16_t *>(t_zl + kMaxHamTerms);
+        static_assert(8 * kMaxHamGroups * sizeof(uint16_t) == kMaxHamTerms * sizeof(uint32_t),
+                      "class ends take the place of a per-term word");
+        g_xs = reinterpret_cast<uint32_t *>(g_cend + 8 * kMaxHamGroups);
         g_t0 = g_xs + kMaxHamGroups;
         g_nt = g_t0 + kMaxHamGroups;
         g_zl = g_nt + kMaxHamGroups;
@@ -1296,20 +1305,53 @@ struct HamTab {
             g_xs[g] = swz<AB>(G.xl);  // swz is linear: swz(t ^ x) = swz(t) ^ swz(x)
             g_t0[g] = (uint32_t)(G.term0 - term_base);
             g_nt[g] = (uint32_t)G.n_term;
+            bool re = true, im = true;
+            for (int i = 0; i < G.n_term; ++i) {
+                re = re && terms[G.term0 + i].wi == 0.0;
+                im = im && terms[G.term0 + i].wr == 0.0;
+            }
+            g_kind[g] = re ? 0u : (im ? 1u : 2u);
             if (G.n_term == 1) {
                 const HTerm &tm = terms[G.term0];
                 g_zl[g] = tm.zl;
                 g_cls[g] = class_of<D, SH, E0>(tm.zl);
-                g_kind[g] = tm.wi == 0.0 ? 0u : (tm.wr == 0.0 ? 1u : 2u);
             }
         }
         for (int k = tid; k < n_terms; k += nt) {
             const HTerm tm = terms[term_base + k];
             t_znt[k] = tm.znt;
-            t_zl[k] = tm.zl;
-            t_cls[k] = class_of<D, SH, E0>(tm.zl);
+            // the term's class rides in bits 24..26 (z_l itself has at most 13 bits)
+            t_zl[k] = tm.zl | (class_of<D, SH, E0>(tm.zl) << 24);
             if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
             else t_w[k] = mk<T>(tm.wr, tm.wi);
+        }
+        __syncthreads();
+        // one thread per multi-term group: insertion sort of its terms by class (stable),
+        // then the class ends
+        for (int g = tid; g < ng; g += nt) {
+            const int j0 = (int)g_t0[g], m = (int)g_nt[g];
+            if (m < 2) continue;
+            for (int a = j0 + 1; a < j0 + m; ++a) {
+                const uint64_t znt = t_znt[a];
+                const uint32_t zl = t_zl[a];
+                const amp_t<T> w = t_w[a];
+                const uint32_t c = class_of<D, SH, E0>(zl);
+                int b = a;
+                while (b > j0 && class_of<D, SH, E0>(t_zl[b - 1]) > c) {
+                    t_znt[b] = t_znt[b - 1];
+                    t_zl[b] = t_zl[b - 1];
+                    t_w[b] = t_w[b - 1];
+                    --b;
+                }
+                t_znt[b] = znt;
+                t_zl[b] = zl;
+                t_w[b] = w;
+            }
+            int j = j0;
+            for (uint32_t c = 0; c < 8; ++c) {
+                while (j < j0 + m && class_of<D, SH, E0>(t_zl[j]) == c) ++j;
+                g_cend[8 * g + c] = (uint16_t)(j - j0);
+            }
         }
     }
 };
@@ -1386,6 +1428,7 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
         for (int g = 0; g < tb.ng; ++g) {
             const uint32_t xs = tb.g_xs[g];
             const int j0 = tb.g_t0[g], nt_g = tb.g_nt[g];
+            if (nt_g == 0) continue;  // the diagonal group exists even without terms
             if (nt_g == 1 && tb.g_kind[g] < 2) {
                 // one term with a real (or imaginary) weight w: the factor at batch amplitude
                 // k is +-w, the sign bit parity(t0 & z_l) ^ parity(k & class) set straight
@@ -1415,8 +1458,102 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
                 }
                 continue;
             }
+            if (nt_g > 1) {
+                // several terms: the factor at batch amplitude k is
+                //   f(k) = sum_j w_j (-1)^{parity(t0 & z_j)} (-1)^{parity(k & class_j)}.
+                // Small groups add each term's signed weight into the BA factors directly (a
+                // logic op sets the sign); large ones sum the signed weights per class (the
+                // terms are sorted by class, so each class is one run) and take the BA-point
+                // Walsh-Hadamard transform.  KIND 0 / 1: every weight real / imaginary, so
+                // only that component is summed and multiplied.
+                auto multi = [&](auto kc, auto dc) {
+                    constexpr int KIND = decltype(kc)::value;
+                    constexpr bool DIRECT = decltype(dc)::value;
+                    T ux[BA], uy[BA];
+                    if constexpr (DIRECT) {
+#pragma unroll
+                        for (int k = 0; k < BA; ++k) ux[k] = (T)0, uy[k] = (T)0;
+                        for (int j = j0; j < j0 + nt_g; ++j) {
+                            const A w = tb.t_weff[j];
+                            const uint32_t zl = tb.t_zl[j];
+                            const uint32_t s0 = (uint32_t)__popc(t0 & zl) << 31;
+                            const uint32_t c0 = (zl >> 24) << 31, c1 = (zl >> 25) << 31, c2 = (zl >> 26) << 31;
+#pragma unroll
+                            for (int k = 0; k < BA; ++k) {
+                                const uint32_t sk =
+                                    s0 ^ ((k & 1) ? c0 : 0u) ^ ((k & 2) ? c1 : 0u) ^ ((k & 4) ? c2 : 0u);
+                                if constexpr (KIND != 1) ux[k] += flip_sign<T>(w.x, sk);
+                                if constexpr (KIND != 0) uy[k] += flip_sign<T>(w.y, sk);
+                            }
+                        }
+                    } else {
+                        const uint16_t *ce = tb.g_cend + 8 * g;
+                        int jb = j0;
+#pragma unroll
+                        for (int c = 0; c < BA; ++c) {
+                            const int je = j0 + (int)ce[c];
+                            T sx = (T)0, sy = (T)0;
+                            for (int j = jb; j < je; ++j) {
+                                const A w = tb.t_weff[j];
+                                const uint32_t sj = (uint32_t)__popc(t0 & tb.t_zl[j]) << 31;
+                                if constexpr (KIND != 1) sx += flip_sign<T>(w.x, sj);
+                                if constexpr (KIND != 0) sy += flip_sign<T>(w.y, sj);
+                            }
+                            ux[c] = sx;
+                            uy[c] = sy;
+                            jb = je;
+                        }
+#pragma unroll
+                        for (int h = 1; h < BA; h <<= 1)
+#pragma unroll
+                            for (int c = 0; c < BA; ++c)
+                                if (!(c & h)) {
+                                    if constexpr (KIND != 1) {
+                                        const T a = ux[c], b = ux[c | h];
+                                        ux[c] = a + b;
+                                        ux[c | h] = a - b;
+                                    }
+                                    if constexpr (KIND != 0) {
+                                        const T a = uy[c], b = uy[c | h];
+                                        uy[c] = a + b;
+                                        uy[c | h] = a - b;
+                                    }
+                                }
+                    }
+#pragma unroll
+                    for (int k = 0; k < BA; ++k) {
+                        const A p = tile[sw[k] ^ xs];
+                        if constexpr (KIND == 0) {
+                            delta[k].x = fma_t<T>(ux[k], p.x, delta[k].x);
+                            delta[k].y = fma_t<T>(ux[k], p.y, delta[k].y);
+                        } else if constexpr (KIND == 1) {
+                            delta[k].x = fma_t<T>(-uy[k], p.y, delta[k].x);
+                            delta[k].y = fma_t<T>(uy[k], p.x, delta[k].y);
+                        } else {
+                            delta[k] = cfma<T>(mk<T>(ux[k], uy[k]), p, delta[k]);
+                        }
+                    }
+                };
+                using I0 = std::integral_constant<int, 0>;
+                using I1 = std::integral_constant<int, 1>;
+                using I2 = std::integral_constant<int, 2>;
+                using DT = std::true_type;
+                using DF = std::false_type;
+                const uint32_t kind = tb.g_kind[g];
+                if (nt_g <= kHamDirectTerms) {
+                    if (kind == 0) multi(I0{}, DT{});
+                    else if (kind == 1) multi(I1{}, DT{});
+                    else multi(I2{}, DT{});
+                } else {
+                    if (kind == 0) multi(I0{}, DF{});
+                    else if (kind == 1) multi(I1{}, DF{});
+                    else multi(I2{}, DF{});
+                }
+                continue;
+            }
+            // one term with a complex weight: f = +-w with the sign pattern of its class
             A f[BA];
-            if (nt_g == 1) {  // one term: f = +-w with the sign pattern of its class
+            {
                 const uint32_t zl = tb.g_zl[g], cls = tb.g_cls[g];
                 const A w = tb.g_w[g];
                 uint32_t m = (__popc(t0 & zl) & 1) ? 0xFFu : 0u;
@@ -1425,29 +1562,6 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
                 if (cls & 4u) m ^= 0xF0u;
 #pragma unroll
                 for (int k = 0; k < BA; ++k) f[k] = ((m >> k) & 1u) ? mk<T>(-w.x, -w.y) : w;
-            } else {  // class accumulators, then the Walsh-Hadamard transform over the batch
-                A U[BA];
-#pragma unroll
-                for (int c = 0; c < BA; ++c) U[c] = mk<T>((T)0, (T)0);
-                for (int j = j0; j < j0 + nt_g; ++j) {
-                    const A w = tb.t_weff[j];
-                    const A u = (__popc(t0 & tb.t_zl[j]) & 1) ? mk<T>(-w.x, -w.y) : w;
-                    const uint32_t cls = tb.t_cls[j];
-#pragma unroll
-                    for (int c = 0; c < BA; ++c)
-                        if (cls == (uint32_t)c) U[c] = cadd<T>(U[c], u);
-                }
-#pragma unroll
-                for (int h = 1; h < BA; h <<= 1)
-#pragma unroll
-                    for (int c = 0; c < BA; ++c)
-                        if (!(c & h)) {
-                            const A x = U[c], y = U[c | h];
-                            U[c] = cadd<T>(x, y);
-                            U[c | h] = mk<T>(x.x - y.x, x.y - y.y);
-                        }
-#pragma unroll
-                for (int k = 0; k < BA; ++k) f[k] = U[k];
             }
 #pragma unroll
             for (int k = 0; k < BA; ++k) delta[k] = cfma<T>(f[k], tile[sw[k] ^ xs], delta[k]);
@@ -1465,8 +1579,10 @@ VQG_DEV T ham_tile(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, ui
     return run;
 }
 
+// complex64: two 256-thread blocks per SM (shared memory allows two); complex128 arithmetic
+// needs more registers than two blocks' share and gets them.
 template <typename T, int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     k_fused_ham(const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam,
                 const HPass *__restrict__ hp, int pi, const HGroup *__restrict__ groups,
                 const HTerm *__restrict__ terms, uint64_t n_tiles, double *__restrict__ partials, int nb) {

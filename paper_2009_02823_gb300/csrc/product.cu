@@ -119,8 +119,8 @@ int Circuit::set_products(int np, const double *coef, const double *mats) {
     int st;
     if ((st = dalloc((void **)&d_prod_mats, sizeof(double) * h.size()))) return st;
     if ((st = dalloc((void **)&d_prod_mats_f, sizeof(float) * hf.size()))) return st;
-    if (cudaMemcpy(d_prod_mats, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d_prod_mats_f, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (h2d(d_prod_mats, h.data(), sizeof(double) * h.size()) != cudaSuccess ||
+        h2d(d_prod_mats_f, hf.data(), sizeof(float) * hf.size()) != cudaSuccess)
         return set_error(VQG_ERR_CUDA, "product operator upload failed");
     if (np > 1 && (st = dalloc(&d_prod_tmp, state_bytes))) return st;
     n_products = np;
@@ -184,7 +184,7 @@ int Circuit::set_input(const void *state, bool on_device) {
     }
     if (plan && !plan->passes.empty()) {  // pass 0: synthesise |0...0> or read the input
         plan->passes[0].from_zero = has_input ? 0 : 1;
-        if (cudaMemcpy(plan->d_passes, plan->passes.data(), sizeof(FPass), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (h2d(plan->d_passes, plan->passes.data(), sizeof(FPass)) != cudaSuccess)
             return set_error(VQG_ERR_CUDA, "plan update failed");
     }
     invalidate_graphs();

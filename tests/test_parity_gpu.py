@@ -553,3 +553,22 @@ def test_long_scaled_ry_stages(theta0):
         assert c.plan()["tile_qubits"] > 0
         e, g = c.energy_and_gradient(theta)
         assert_parity("c64", e, g, e_ref, g_ref, f"theta0={theta0}")
+
+
+@pytest.mark.parametrize("K", [10, 12])
+def test_hamiltonian_without_diagonal_terms(K):
+    """Every term flips a qubit, so the diagonal (x = 0) group exists but holds no term;
+    one group mixes a real-weight and an imaginary-weight term (X3 and Y3).  K = n puts
+    the whole state in one tile."""
+    n = 12
+    rng = np.random.default_rng(5)
+    gates, P = W.random_circuit(rng, n, 60, share_params=False)
+    theta = rng.uniform(0, 2 * np.pi, P)
+    terms = [(c, ops) for c, ops in W.random_paulis(rng, n, 14, 4) if any(l in "XY" for _q, l in ops)]
+    terms += [(-0.23, ((3, "X"),)), (1.31, ((3, "Y"),)), (0.7, ((1, "X"), (5, "Z"))), (0.4, ((1, "Y"), (5, "Y")))]
+    e_ref, g_ref = _oracle(n, gates, theta, P, terms)
+    for dtype in DTYPES:
+        with _circ(n, gates, P, dtype, terms, tile_qubits=K) as c:
+            e, g = c.energy_and_gradient(theta)
+            assert_parity(dtype, e, g, e_ref, g_ref, f"K={K}")
+            assert energy_err(c.energy(theta), e_ref) <= TOL[dtype]
