@@ -190,7 +190,8 @@ def run_ours(args, rank, world, dist):
     w = _workload(args)
     S = (8 if args.dtype == "c64" else 16) << w.n
     stream = torch.cuda.Stream()  # every kernel of the step and both timing events go here
-    circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream, c128_arith=args.c128_arith)
+    circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream, c128_arith=args.c128_arith,
+                   specialize=args.specialize if args.dtype == "c64" else 0)
     circ.set_hamiltonian(w.terms)
     theta_h = replica_theta(w.theta, rank)
     theta_d = torch.tensor(theta_h, dtype=torch.float64, device="cuda")
@@ -782,6 +783,8 @@ def main():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--c128-arith", default="fp64", choices=["fp64", "float-float"],
                     help="arithmetic of the complex128 tile passes")
+    ap.add_argument("--specialize", type=int, default=0,
+                    help="1: complex64 tile passes run per-pass specialised kernels (compiled when the circuit is made)")
     ap.add_argument("--cfg", type=int, default=3)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--layers", type=int, default=None)

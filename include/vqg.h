@@ -110,7 +110,16 @@ typedef struct vqg_options {
                                     keep the fastest (see vqg_autotune)                     */
     int32_t c128_arith;          /* complex128 tile-pass arithmetic (vqg_c128_arith):
                                     VQG_C128_FP64 (default) or VQG_C128_FLOAT_FLOAT      */
-    int32_t reserved[7];
+    int32_t specialize;          /* 1: the complex64 forward tile passes run kernels
+                                    generated for this circuit's passes (straight-line op
+                                    sequences, compiled with nvcc when the schedule is
+                                    planned and cached on disk; needs nvcc and the
+                                    library's headers at run time, VQG_ERR_UNSUPPORTED
+                                    otherwise); 2: the reverse passes too (their generated
+                                    code outgrows the instruction cache on long passes:
+                                    slower at 30 qubits); results equal the default
+                                    kernels'.  0 (default): the generic kernels only       */
+    int32_t reserved[6];
 } vqg_options;
 
 typedef struct vqg_circuit vqg_circuit;
@@ -223,7 +232,8 @@ typedef struct vqg_plan_info {
     int32_t reverse_stages;
     int32_t stage_ops;
     int32_t diag_blocks;
-    int32_t reserved[3];
+    int32_t specialized;  /* the specialize level in effect: 0 none, 1 forward, 2 both */
+    int32_t reserved[2];
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 
@@ -271,6 +281,22 @@ int vqg_diagnostics(vqg_circuit *c, vqg_diag_summary *summary, int max_entries, 
 int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates, int n_params, int dtype,
                      const vqg_options *opt, int n_terms, const uint64_t *x_mask,
                      const uint64_t *z_mask, const double *coef, vqg_plan_info *info);
+
+/* Specialised kernels (options.specialize): plan a complex64 circuit on the host exactly
+ * as vqg_circuit_create would with these options and compile the per-pass kernels into
+ * the on-disk cache (directory VQG_SPEC_CACHE, default $TMPDIR/vqg_spec_<uid>), so that a
+ * later vqg_circuit_create with specialize = 1 only loads them.  No GPU is touched; needs
+ * nvcc.  With n_terms > 0 the Hamiltonian passes of that Pauli sum (masks and coefficients
+ * as vqg_set_hamiltonian) are compiled too.  gates, opt and the term arrays: host, read
+ * during the call; *n_kernels (nullable) receives the
+ * number of kernels (one per pass and specialised direction; 0 when unfused).  Errors:
+ * VQG_ERR_INVALID for malformed gates, VQG_ERR_UNSUPPORTED when a kernel does not compile
+ * (the message holds the compiler's output).  The paper has no counterpart: this is
+ * the GB300 implementation's way to run a fixed circuit's gate sequence as compiled code
+ * (Algorithm 1's primitives, Sec. 2.1, are otherwise interpreted per op). */
+int vqg_specialize_prepare(int n_qubits, const vqg_gate *gates, int n_gates, int n_params,
+                           const vqg_options *opt, int n_terms, const uint64_t *x_mask,
+                           const uint64_t *z_mask, const double *coef, int *n_kernels);
 
 /* Tensor-product cost operators (the paper's benchmark operator Hadamard^{(x)N}, Sec. 3;
  * Sec. 2.1 asks only that the operator can be applied to a state).

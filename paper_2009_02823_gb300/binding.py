@@ -44,7 +44,8 @@ class vqg_options(ctypes.Structure):
                 ("tile_qubits", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("max_checkpoint_mib", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
                 ("rev_reg_qubits", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("c128_arith", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("c128_arith", ctypes.c_int32), ("specialize", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 # vqg_c128_arith: arithmetic of the complex128 tile passes
 C128_ARITH = {"fp64": 0, "float-float": 1}
@@ -69,7 +70,8 @@ class vqg_plan_info(ctypes.Structure):
                 ("hamiltonian_groups", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
                 ("rev_reg_qubits", ctypes.c_int32), ("forward_stages", ctypes.c_int32),
                 ("reverse_stages", ctypes.c_int32), ("stage_ops", ctypes.c_int32),
-                ("diag_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("diag_blocks", ctypes.c_int32), ("specialized", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class vqg_tune_result(ctypes.Structure):
@@ -104,6 +106,7 @@ def lib():
             "vqg_set_hamiltonian": (i, [p, i, p, p, p]),
             "vqg_set_hamiltonian_strings": (i, [p, i, p, p]),
             "vqg_set_diagnostics": (i, [p, i]),
+            "vqg_specialize_prepare": (i, [i, p, i, i, p, i, p, p, p, p]),
             "vqg_diagnostics": (i, [p, p, i, p]),
             "vqg_pauli_strings_to_masks": (i, [i, i, p, p, p]),
             "vqg_set_stream": (i, [p, p]),
@@ -170,6 +173,30 @@ def pauli_strings_to_masks(n_qubits: int, strings) -> tuple[np.ndarray, np.ndarr
     return x[:len(strings)], z[:len(strings)]
 
 
+def specialize_prepare(n: int, gates, n_params: int, terms=None, **options) -> int:
+    """Compile the specialised kernels of a complex64 circuit (and of its Hamiltonian's
+    passes when terms are given) into the on-disk cache on the host
+    (vqg_specialize_prepare); options as for Circuit.  Returns the kernel count."""
+    opt = vqg_options()
+    lib().vqg_default_options(ctypes.byref(opt))
+    for k, v in options.items():
+        setattr(opt, k, int(v))
+    opt.specialize = int(options.get("specialize", 1))
+    arr = gate_array(gates)
+    nk = ctypes.c_int(0)
+    if terms:
+        x, z, c = pauli_masks(terms, n)
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        z = np.ascontiguousarray(z, dtype=np.uint64)
+        c = np.ascontiguousarray(np.real(c), dtype=np.float64)
+        _check(lib().vqg_specialize_prepare(n, arr, len(gates), n_params, ctypes.byref(opt), len(c), _ptr(x), _ptr(z),
+                                            _ptr(c), ctypes.byref(nk)))
+    else:
+        _check(lib().vqg_specialize_prepare(n, arr, len(gates), n_params, ctypes.byref(opt), 0, None, None, None,
+                                            ctypes.byref(nk)))
+    return nk.value
+
+
 def gate_array(gates) -> ctypes.Array:
     arr = (vqg_gate * max(len(gates), 1))()
     for k, (kind, q0, q1, ps) in enumerate(gates):
@@ -222,7 +249,7 @@ class Circuit:
     def __init__(self, n: int, gates, n_params: int, dtype: str = "c64", *, fusion: bool = True,
                  checkpoint_interval: int = 0, tile_qubits: int = 0, use_graph: bool = False,
                  max_checkpoint_mib: int = 0, fwd_reg_qubits: int = 0, rev_reg_qubits: int = 0,
-                 autotune: bool = False, c128_arith: str = "fp64", stream=None):
+                 autotune: bool = False, c128_arith: str = "fp64", stream=None, specialize: int = 0):
         L = lib()
         self.n, self.n_params, self.n_gates = n, n_params, len(gates)
         self.dtype = dtype
@@ -237,6 +264,7 @@ class Circuit:
         opt.rev_reg_qubits = rev_reg_qubits
         opt.autotune = int(autotune)
         opt.c128_arith = C128_ARITH[c128_arith]
+        opt.specialize = int(specialize)
         self._gates = gate_array(gates)
         h = ctypes.c_void_p()
         _check(L.vqg_circuit_create(n, self._gates, len(gates), n_params, DTYPE[dtype],

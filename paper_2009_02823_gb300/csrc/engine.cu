@@ -703,6 +703,7 @@ int Circuit::build_plan() {
         int st;
         if ((st = upload_plan(pl))) return st;
         if (!dbl && (st = dalloc((void **)&pl->d_mats_f, sizeof(float) * 8 * std::max(G, 1)))) return st;
+        if (!dbl && opt.specialize && (st = spec_build(pl, opt.specialize >= 2))) return st;
         plan_ok = true;
         if (prod_active && (st = build_product_plans())) return st;  // same tile geometry
     }
@@ -854,6 +855,9 @@ int Circuit::build_ham_plan() {
     if (!pl->ht.empty()) h2d(pl->d_ht, pl->ht.data(), sizeof(HTerm) * pl->ht.size());
     if (cudaGetLastError() != cudaSuccess) return set_error(VQG_ERR_CUDA, "Hamiltonian plan upload failed");
     ham_plan_ok = true;
+    pl->spec_ham.clear();
+    pl->spec_ham_for = nullptr;
+    if (!dbl && opt.specialize && (st = spec_build_ham(pl))) return st;
     return VQG_OK;
 }
 
@@ -895,8 +899,11 @@ int Circuit::issue_forward_fused(bool with_ckpt) {
         const int k = with_ckpt ? pl->ckpt_of_pass[j] : -1;
         void *out = k >= 0 ? ckpt_buf[k] : psi;
         prof_begin(FAM_FWD_FUSED);
-        launch_fused_fwd(dbl, float_float(dbl, opt), pl->K, pl->Rf, in, out, pl->d_passes, (int)j, pl->d_stages,
-                         pl->d_ops, pl->d_diags, pl->d_items, mats, pl->n_tiles, pl->grid_fwd, stream);
+        if (j < pl->spec_fwd.size())
+            spec_launch_fwd(pl, (int)j, in, out, mats, stream);
+        else
+            launch_fused_fwd(dbl, float_float(dbl, opt), pl->K, pl->Rf, in, out, pl->d_passes, (int)j, pl->d_stages,
+                             pl->d_ops, pl->d_diags, pl->d_items, mats, pl->n_tiles, pl->grid_fwd, stream);
         prof_end();
         if (k >= 0)
             if (int st = diag_reduce(out, nullptr, DIAG_STORE, k)) return st;
@@ -911,7 +918,9 @@ int Circuit::issue_hamiltonian_fused() {
     Plan *pl = plan;
     for (size_t h = 0; h < pl->hp.size(); ++h) {
         prof_begin(FAM_HAM_FUSED);
-        if (float_float(dbl, opt))
+        if (!dbl && h < pl->spec_ham.size() && pl->spec_ham_for == pl->d_hp)
+            spec_launch_ham(pl, (int)h, psi, lam, d_partials, nb, stream);
+        else if (float_float(dbl, opt))
             launch_fused_ham_df(pl->K, psi, lam, pl->d_hp, (int)h, pl->d_hg, pl->d_ht, pl->n_tiles, d_partials, nb,
                                 stream);
         else
@@ -941,9 +950,14 @@ int Circuit::issue_reverse_fused() {
         // after the last reverse pass
         const bool write_phi = j > 0 && (pl->ckpt_of_pass[j - 1] < 0 || diag_active), write_lam = j > 0;
         prof_begin(FAM_ADJ_FUSED);
-        auto rev = !dbl ? launch_fused_rev_c64 : float_float(dbl, opt) ? launch_fused_rev_df : launch_fused_rev_c128;
-        rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
-            pl->d_slot_map, mats, pl->n_tiles, gpart, nb, (write_phi ? 1 : 0) | (write_lam ? 2 : 0), stream);
+        const int wmask = (write_phi ? 1 : 0) | (write_lam ? 2 : 0);
+        if (j < (int)pl->spec_rev.size()) {
+            spec_launch_rev(pl, j, src, psi, lam, mats, gpart, nb, wmask, stream);
+        } else {
+            auto rev = !dbl ? launch_fused_rev_c64 : float_float(dbl, opt) ? launch_fused_rev_df : launch_fused_rev_c128;
+            rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
+                pl->d_slot_map, mats, pl->n_tiles, gpart, nb, wmask, stream);
+        }
         prof_end();
     }
     cudaError_t e = cudaGetLastError();
@@ -966,6 +980,7 @@ void Circuit::fill_plan_info(vqg_plan_info *info) const {
     }
     info->checkpoints = nck;
     info->tile_qubits = fused ? plan->K : 0;
+    info->specialized = !fused || plan->spec_fwd.empty() ? 0 : (plan->spec_rev.empty() ? 1 : 2);
     info->fwd_reg_qubits = fused ? plan->Rf : 0;
     info->rev_reg_qubits = fused ? plan->Rr : 0;
     info->hamiltonian_groups = (int)ham.size();

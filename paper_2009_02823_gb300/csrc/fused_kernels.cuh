@@ -970,6 +970,129 @@ VQG_DEV void reduce_stash(const T *stash, const FStage &st, double *acc, int tid
 
 template <typename T> constexpr int stash_rows() { return sizeof(T) == 4 ? kMaxStageRows : kMaxStageRowsDbl; }
 
+// Per-thread geometry of one register stage: shared-memory slot sb and global index gb of
+// register index 0, and the swizzled offsets of the register bits.
+template <typename T, int K, int R>
+struct StageGeo {
+    uint32_t sb;
+    uint64_t gb;
+    uint32_t w[R];
+    VQG_DEV void init(const FStage &st, int tid, uint64_t base) {
+        thread_base<K, R, FT<T>::AB>(st, tid, base, sb, gb);
+#pragma unroll
+        for (int k = 0; k < R; ++k) w[k] = st.reg_sw[k];
+    }
+};
+
+// Reverse op bodies, shared by the interpreted tile pass and the per-pass specialised
+// kernels.  Each returns the thread's partial of the op's reduction value (stored by the
+// caller in the op's stash row) where the op has one; m is the op's parameter row.
+template <int KB, int R, typename T>
+VQG_DEV T rev_op_ry(amp_t<T> (&a)[1 << R], amp_t<T> (&l)[1 << R], const amp_t<T> *m, T &kacc, T &k2acc) {
+    constexpr int NA = 1 << R;
+    T v1;
+    if constexpr (std::is_same<T, float>::value) {  // scaled form (see load_prog)
+        const float2 p1 = m[1], p2 = m[2];
+        v1 = rev_ry_scaled<KB, NA>(a, l, p1.x, p1.y != 0.f);
+        v1 *= k2acc;  // the inputs held the true values divided by K so far
+        kacc *= p2.x;
+        k2acc *= p2.y;
+    } else {
+        const amp_t<T> cs = m[0];
+        v1 = rev_ry<KB, NA, T>(a, l, cs.x, cs.y);
+    }
+    return v1;
+}
+template <int KB, int R, typename T>
+VQG_DEV T rev_op_rx(amp_t<T> (&a)[1 << R], amp_t<T> (&l)[1 << R], const amp_t<T> *m, T k2acc) {
+    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+    T v1 = rev_rx<KB, 1 << R, T>(a, l, ud);
+    if constexpr (std::is_same<T, float>::value) v1 *= k2acc;
+    return v1;
+}
+// U3: eight values, stored in stash rows row .. row + 7 (srow points at row, stride nt)
+template <int KB, int R, typename T>
+VQG_DEV void rev_op_u3(amp_t<T> (&a)[1 << R], amp_t<T> (&l)[1 << R], const amp_t<T> *m, T k2acc, T *srow, int nt) {
+    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+    T v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    rev_u3<KB, 1 << R, T>(a, l, ud, v8);
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        if constexpr (std::is_same<T, float>::value) v8[x] *= k2acc;
+        srow[x * nt] = v8[x];
+    }
+}
+template <int KB, int R, typename T>
+VQG_DEV void rev_op_cnot(amp_t<T> (&a)[1 << R], amp_t<T> (&l)[1 << R], uint32_t rm0, bool thr_c) {
+    op_cnot<KB, 1 << R, T>(a, rm0, thr_c);
+    op_cnot<KB, 1 << R, T>(l, rm0, thr_c);
+}
+// controlled rotations (G = 0, 1, 2: X, Y, Z generator) and phase gates (G = 3)
+template <int G, int KB, int R, typename T>
+VQG_DEV T rev_op_cgen(amp_t<T> (&a)[1 << R], amp_t<T> (&l)[1 << R], const amp_t<T> *m, uint32_t rm0, bool thr_c,
+                      T k2acc) {
+    const Mat2<T> ud = dagger<T>(mat_of<T>(m));
+    T v1 = rev_cgen<G, KB, 1 << R, T>(a, l, ud, rm0, thr_c);
+    if constexpr (std::is_same<T, float>::value) v1 *= k2acc;
+    return v1;
+}
+
+template <typename T, int K, int R>
+VQG_DEV void rev_gather(const StageGeo<T, K, R> &g, const amp_t<T> *tphi, const amp_t<T> *tlam,
+                        amp_t<T> (&a)[1 << R], amp_t<T> (&l)[1 << R]) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        const uint32_t ad = reg_addr<R, 1 << R>(g.sb, g.w, j);
+        a[j] = tphi[ad];
+        l[j] = tlam[ad];
+    }
+}
+
+// Write the stage's amplitudes back: multiplied by the stage's per-thread phase (which
+// also carries the scaled-RY factor K) or by K alone, or as they are.
+template <typename T, int K, int R>
+VQG_DEV void rev_scatter(StageGeo<T, K, R> &g, bool has_phase, amp_t<T> *tphi, amp_t<T> *tlam,
+                         const amp_t<T> (&a)[1 << R], const amp_t<T> (&l)[1 << R], amp_t<T> phase, T kacc) {
+    constexpr int NA = 1 << R;
+    asm volatile("" : "+r"(g.sb));  // recompute the addresses instead of keeping them live
+    if (has_phase) {
+        if constexpr (std::is_same<T, float>::value) {  // packed, broadcasts shared by both states
+            phase = mk<T>(phase.x * kacc, phase.y * kacc);
+            const float2 pr = make_float2(phase.x, phase.x), pi2 = make_float2(-phase.y, phase.y);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(g.sb, g.w, j);
+                tphi[ad] = __ffma2_rn(pr, a[j], __fmul2_rn(pi2, make_float2(a[j].y, a[j].x)));
+                tlam[ad] = __ffma2_rn(pr, l[j], __fmul2_rn(pi2, make_float2(l[j].y, l[j].x)));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(g.sb, g.w, j);
+                tphi[ad] = cmul<T>(phase, a[j]);
+                tlam[ad] = cmul<T>(phase, l[j]);
+            }
+        }
+    } else if (scaled_stage<T>(kacc)) {
+        if constexpr (std::is_same<T, float>::value) {
+            const float2 sv = make_float2(kacc, kacc);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                const uint32_t ad = reg_addr<R, NA>(g.sb, g.w, j);
+                tphi[ad] = __fmul2_rn(sv, a[j]);
+                tlam[ad] = __fmul2_rn(sv, l[j]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const uint32_t ad = reg_addr<R, NA>(g.sb, g.w, j);
+            tphi[ad] = a[j];
+            tlam[ad] = l[j];
+        }
+    }
+}
+
 // One tile of a reverse pass.  Each op stores its per-thread FP32 partial(s) in the
 // stage's stash rows (no cross-lane dependency in the op loop); after the stage the
 // rows are reduced into acc (FP64, one value per local slot).
@@ -1294,7 +1417,9 @@ struct HamTab {
         }
         return cls;
     }
-    template <int D, int SH, int E0>
+    // SORT: sort the terms of each multi-term group by class (the interpreted pass); the
+    // specialised passes take the terms in plan order.
+    template <int D, int SH, int E0, bool SORT = true>
     VQG_DEV void load(const HPass &P, const HGroup *__restrict__ groups, const HTerm *__restrict__ terms,
                       int tid, int nt) {
         ng = P.n_group;
@@ -1325,6 +1450,7 @@ struct HamTab {
             if constexpr (sizeof(T) == 4) t_w[k] = mk<T>(tm.fr, tm.fi);
             else t_w[k] = mk<T>(tm.wr, tm.wi);
         }
+        if constexpr (!SORT) return;
         __syncthreads();
         // one thread per multi-term group: insertion sort of its terms by class (stable),
         // then the class ends
@@ -1610,6 +1736,225 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
         }
         const T run = ham_tile<T, K, false>(tile, row_off, tb, tile_base(ti, P.nontile, P.n_nontile),
                                             P.first != 0, psi, lam, tid);
+        eacc += (double)warp_tree<T>(run);
+    }
+    if ((tid & 31) == 0) wsum[tid >> 5] = eacc;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += wsum[w];
+        partials[(size_t)P.eslot * nb + blockIdx.x] = s;
+    }
+}
+
+
+// ------------------------------------------------------------------ specialised passes
+// Kernels generated for one pass of one plan (spec.cu) run these bodies: the same launch
+// geometry, shared-memory program and tile I/O as k_fused_fwd / k_fused_rev, with the
+// pass's stage and op sequence written out as straight-line code in Body::tile (every op
+// type, register bit, stash row and block index a literal), so the op loop's dispatch,
+// the register-bit switch and the register moves at its merge points disappear.
+template <typename T, int K, int R, typename Body>
+VQG_DEV void fwd_pass_spec(const amp_t<T> *__restrict__ src, amp_t<T> *__restrict__ dst,
+                           const FPass *__restrict__ passes, int pi, const FStage *__restrict__ stages,
+                           const FOp *__restrict__ ops, const FDiag *__restrict__ diags,
+                           const FDItem *__restrict__ items, const typename FT<T>::mat_t *__restrict__ mats,
+                           uint64_t n_tiles) {
+    using C = FwdCfg<T, K, R>;
+    constexpr int NT = C::NT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    amp_t<T> *tile = reinterpret_cast<amp_t<T> *>(smem);
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
+    Prog<T, R> pg;
+    pg.template bind<typename C::Caps>(smem + C::o_prog);
+    const FPass &P = passes[pi];
+    const int tid = threadIdx.x;
+    fill_row_offsets<T, K>(P.high, row_off, tid, NT);
+    load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, stages, ops, diags, items, mats, false, tid, NT);
+    __syncthreads();
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        if (ti + gridDim.x < n_tiles && !P.from_zero)
+            TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid);
+        Body::tile(tile, row_off, pg, tile_base(ti, P.nontile, P.n_nontile), P.from_zero != 0, src, dst, tid);
+    }
+}
+
+template <typename T, int K, int R, typename Body>
+VQG_DEV void rev_pass_spec(const amp_t<T> *__restrict__ phi_src, amp_t<T> *__restrict__ phi_dst,
+                           amp_t<T> *__restrict__ lam, const FPass *__restrict__ passes, int pi,
+                           const FStage *__restrict__ stages, const FOp *__restrict__ ops,
+                           const FDiag *__restrict__ diags, const FDItem *__restrict__ items,
+                           const int *__restrict__ slot_map, const typename FT<T>::mat_t *__restrict__ mats,
+                           uint64_t n_tiles, double *__restrict__ partials, int nb, int wmask) {
+    using C = RevCfg<T, K, R>;
+    constexpr int NT = C::NT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    amp_t<T> *tphi = reinterpret_cast<amp_t<T> *>(smem);
+    amp_t<T> *tlam = tphi + (1 << K);
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
+    Prog<T, R> pg;
+    pg.template bind<typename C::Caps>(smem + C::o_prog);
+    double *acc = reinterpret_cast<double *>(smem + C::o_acc);
+    T *stash = reinterpret_cast<T *>(smem + C::o_stash);
+    int *smap = reinterpret_cast<int *>(smem + C::o_map);
+    const FPass &P = passes[pi];
+    const int tid = threadIdx.x;
+    const int n_ls = P.n_lslots;
+    fill_row_offsets<T, K>(P.high, row_off, tid, NT);
+    for (int i = tid; i < n_ls; i += NT) acc[i] = 0.0, smap[i] = slot_map[P.slotmap0 + i];
+    load_prog<T, R>(pg, P.rstage0, P.n_rstage, P.rdiag0, P.n_rdiag, stages, ops, diags, items, mats, true, tid, NT);
+    __syncthreads();
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        if (ti + gridDim.x < n_tiles) {
+            const uint64_t next = tile_base(ti + gridDim.x, P.nontile, P.n_nontile);
+            TileIO<T, K>::template prefetch<NT>(phi_src, next, row_off, tid);
+            TileIO<T, K>::template prefetch<NT>(lam, next, row_off, tid);
+        }
+        Body::tile(tphi, tlam, row_off, pg, tile_base(ti, P.nontile, P.n_nontile), phi_src, phi_dst, lam, acc,
+                   stash, tid, (wmask & 1) != 0, (wmask & 2) != 0);
+    }
+    __syncthreads();
+    for (int i = tid; i < n_ls; i += NT) partials[(size_t)smap[i] * nb + blockIdx.x] = acc[i];
+}
+
+template <typename T, int K, int R>
+VQG_DEV void fwd_gather(const StageGeo<T, K, R> &g, const amp_t<T> *tile, amp_t<T> (&a)[1 << R]) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) a[j] = tile[reg_addr<R, 1 << R>(g.sb, g.w, j)];
+}
+template <typename T, int K, int R>
+VQG_DEV void fwd_scatter(StageGeo<T, K, R> &g, bool has_phase, amp_t<T> *tile, const amp_t<T> (&a)[1 << R],
+                         amp_t<T> phase, T kacc) {
+    constexpr int NA = 1 << R;
+    asm volatile("" : "+r"(g.sb));  // recompute the addresses instead of keeping them live
+    if (has_phase) {
+        if constexpr (std::is_same<T, float>::value) phase = mk<T>(phase.x * kacc, phase.y * kacc);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(g.sb, g.w, j)] = cmul<T>(phase, a[j]);
+    } else if (scaled_stage<T>(kacc)) {
+        if constexpr (std::is_same<T, float>::value) {
+            const float2 sv = make_float2(kacc, kacc);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(g.sb, g.w, j)] = __fmul2_rn(sv, a[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) tile[reg_addr<R, NA>(g.sb, g.w, j)] = a[j];
+    }
+}
+
+// Forward op bodies for the specialised kernels (the interpreted pass runs apply_fwd_op).
+template <int KB, int R, typename T>
+VQG_DEV void fwd_op_ry(amp_t<T> (&a)[1 << R], const amp_t<T> *m, T &kacc) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 p1 = m[1];
+        op_ry_scaled<KB, 1 << R>(a, p1.x, p1.y != 0.f);
+        kacc *= m[2].x;
+    } else {
+        const amp_t<T> cs = m[0];
+        op_ry<KB, 1 << R, T>(a, cs.x, cs.y);
+    }
+}
+template <typename T, int R>
+VQG_DEV void fwd_op_diag(amp_t<T> (&a)[1 << R], const Prog<T, R> &pg, int d, uint64_t gb, amp_t<T> &phase,
+                         bool has_rt) {
+    amp_t<T> tau;
+    uint32_t c;
+    diag_thread<T, R>(pg, pg.dg[d], gb, tau, c);
+    phase = cmul<T>(tau, phase);
+    diag_apply<1 << R, T>(a, pg.tab + d * (1 << R), c, has_rt);
+}
+
+
+// Specialised Hamiltonian pass (spec.cu): ham_tile with the group loop replaced by the
+// generated Body::groups, which visits the pass's groups with their flip masks, term masks,
+// classes and weight kinds as literals (weights and the tile's signs still come from the
+// shared-memory table, in plan order).
+template <typename T, int K, bool L2ONLY, typename Body>
+VQG_DEV T ham_tile_spec(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, uint64_t base, bool first,
+                        const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam, int tid) {
+    using A = amp_t<T>;
+    using IO = TileIO<T, K>;
+    using G = HamGeo<T, K>;
+    constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
+    constexpr int CPT = G::CPT, BCH = G::BCH, BA = G::BA;
+    IO::template load<NT, L2ONLY>(tile, psi, base, row_off, tid);
+    for (int k = tid; k < tb.n_terms; k += NT) {
+        const A w = tb.t_w[k];
+        tb.t_weff[k] = (__popcll(base & tb.t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;
+    }
+    for (int g = tid; g < tb.ng; g += NT)
+        if (tb.g_nt[g] == 1) {
+            const int j = (int)tb.g_t0[g];
+            const A w = tb.t_w[j];
+            tb.g_w[g] = (__popcll(base & tb.t_znt[j]) & 1) ? mk<T>(-w.x, -w.y) : w;
+        }
+    __syncthreads();
+    T run = 0;
+#pragma unroll 1
+    for (int b0 = 0; b0 < CPT; b0 += BCH) {
+        uint32_t t0, sw[BA];
+        uint64_t gch[BCH];
+        A mine[BA], out[BA], delta[BA];
+#pragma unroll
+        for (int i = 0; i < BCH; ++i) {
+            const int c = tid + NT * (b0 + i);
+            const int row = c / IO::CPR, col = c % IO::CPR;
+            const uint32_t tc = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
+            if (i == 0) t0 = tc;
+            gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
+#pragma unroll
+            for (int e = 0; e < IO::CA; ++e) {
+                sw[i * IO::CA + e] = swz<AB>(tc + e);
+                mine[i * IO::CA + e] = tile[sw[i * IO::CA + e]];
+                out[i * IO::CA + e] = mk<T>((T)0, (T)0);
+                delta[i * IO::CA + e] = mk<T>((T)0, (T)0);
+            }
+            if (!first) {
+                const float4 *g = reinterpret_cast<const float4 *>(lam + gch[i]);
+                IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), out + i * IO::CA);
+            }
+        }
+        Body::groups(tb, tile, t0, sw, delta);
+#pragma unroll
+        for (int k = 0; k < BA; ++k) {
+            run += mine[k].x * delta[k].x + mine[k].y * delta[k].y;
+            out[k] = cadd<T>(out[k], delta[k]);
+        }
+#pragma unroll
+        for (int i = 0; i < BCH; ++i) __stcs(reinterpret_cast<float4 *>(lam + gch[i]), IO::pack(out + i * IO::CA));
+    }
+    __syncthreads();
+    return run;
+}
+
+template <typename T, int K, typename Body>
+VQG_DEV void ham_pass_spec(const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam, const HPass *__restrict__ hp,
+                           int pi, const HGroup *__restrict__ groups, const HTerm *__restrict__ terms, uint64_t n_tiles,
+                           double *__restrict__ partials, int nb) {
+    using C = HamCfg<T, K>;
+    constexpr int NT = 256;
+    extern __shared__ __align__(16) unsigned char smem[];
+    amp_t<T> *tile = reinterpret_cast<amp_t<T> *>(smem);
+    uint64_t *row_off = reinterpret_cast<uint64_t *>(smem + C::o_row);
+    HamTab<T, K> tb;
+    tb.bind(smem + C::o_tab);
+    __shared__ double wsum[NT / 32];
+    const HPass &P = hp[pi];
+    const int tid = threadIdx.x;
+    fill_row_offsets<T, K>(P.high, row_off, tid, NT);
+    using G = HamGeo<T, K>;
+    tb.template load<G::D, G::SH, G::E0, false>(P, groups, terms, tid, NT);
+    double eacc = 0.0;
+    __syncthreads();
+    for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        if (ti + gridDim.x < n_tiles) {
+            const uint64_t next = tile_base(ti + gridDim.x, P.nontile, P.n_nontile);
+            TileIO<T, K>::template prefetch<NT>(psi, next, row_off, tid);
+            if (!P.first) TileIO<T, K>::template prefetch<NT>(lam, next, row_off, tid);
+        }
+        const T run = ham_tile_spec<T, K, false, Body>(tile, row_off, tb, tile_base(ti, P.nontile, P.n_nontile),
+                                                       P.first != 0, psi, lam, tid);
         eacc += (double)warp_tree<T>(run);
     }
     if ((tid & 31) == 0) wsum[tid >> 5] = eacc;

@@ -36,6 +36,11 @@ struct Plan {
     HGroup *d_hg = nullptr;
     HTerm *d_ht = nullptr;
     float *d_mats_f = nullptr;
+    // specialised kernels of each pass (spec.cu; cudaKernel_t handles), empty when the
+    // passes run on the interpreted kernels
+    std::vector<void *> spec_fwd, spec_rev, spec_ham;
+    size_t spec_smem_fwd = 0, spec_smem_rev = 0, spec_smem_ham = 0;
+    const void *spec_ham_for = nullptr;  // the Hamiltonian tables (d_hp) spec_ham was built for
 };
 
 // Plan the gate passes of one circuit (host only; nullptr + empty err: no fused
@@ -57,5 +62,14 @@ bool float_float(bool dbl, const vqg_options &opt);
         int grid, cudaStream_t s
 bool launch_fused_fwd(bool dbl, bool ff, VQG_FWD_LAUNCH_ARGS);
 int default_tile_qubits(int n, bool dbl);
+// Per-pass specialised complex64 kernels (spec.cu): build them for every pass of a plan
+// (generated, compiled, cached, loaded), and launch pass j of either direction.
+int spec_compile(const Plan *pl, bool with_rev, std::vector<std::string> &cubins);
+int spec_build(Plan *pl, bool with_rev);
+int spec_build_ham(Plan *pl);
+int spec_launch_ham(const Plan *pl, int h, const void *psi, void *lam, double *partials, int nb, cudaStream_t s);
+int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const void *mats, cudaStream_t s);
+int spec_launch_rev(const Plan *pl, int j, const void *phi_src, void *phi_dst, void *lam, const void *mats,
+                    double *partials, int nb, int wmask, cudaStream_t s);
 
 }  // namespace vqg
