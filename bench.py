@@ -32,15 +32,16 @@ from paper_2009_02823_gb300.replicas import (circuit_cost, max_over_ranks, parti
 METRIC = "adjoint gradients/s at n=30,P=600"
 
 # DRAM bytes (read + write) per launch per amplitude of the state, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of each fused complex64 kernel on the
-# bench recipe at n=26 (0.5 GB per state, far larger than L2), taken on the kernels as
-# they are now: reverse 1.0792 + 0.4791 GB, forward 0.5405 + 0.4823 GB, Hamiltonian
-# 1.1276 + 0.4777 GB per launch.  Every launch streams whole states, so traffic scales
-# with 2^n.  Reset an entry to None whenever its kernel changes until it is captured again.
+# (dram__bytes_read.sum + dram__bytes_write.sum) of each complex64 pass kernel the bench
+# runs, on the bench recipe at n=26 (0.5 GB per state, far larger than L2): reverse
+# k_fused_rev 1.0794 + 0.4786 GB, specialised forward 0.5386 + 0.4763 GB, specialised
+# Hamiltonian 1.1328 + 0.4777 GB per launch.  Every launch streams whole states, so
+# traffic scales with 2^n.  Reset an entry to None whenever its kernel changes until it is
+# captured again.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    "adj_fused": (1.079234e9 + 0.479091456e9) / 2**26,
-    "fwd_fused": (0.540485376e9 + 0.482346752e9) / 2**26,
-    "ham_fused": (1.127569e9 + 0.477710592e9) / 2**26,
+    "adj_fused": (1.079387e9 + 0.478561024e9) / 2**26,
+    "fwd_fused": (0.538553088e9 + 0.476307968e9) / 2**26,
+    "ham_fused": (1.132832e9 + 0.47766272e9) / 2**26,
 }
 UNIT = "gradients/s"
 
@@ -190,10 +191,10 @@ def run_ours(args, rank, world, dist):
     w = _workload(args)
     S = (8 if args.dtype == "c64" else 16) << w.n
     stream = torch.cuda.Stream()  # every kernel of the step and both timing events go here
-    spec = args.specialize if args.dtype == "c64" else 0
+    spec = args.specialize if args.dtype == "c64" and args.fusion else 0
     t_make = time.perf_counter()  # includes compiling the specialised kernels (cached on disk)
     circ = Circuit(w.n, w.gates, w.n_params, args.dtype, stream=stream, c128_arith=args.c128_arith,
-                   specialize=spec)
+                   specialize=spec, fusion=bool(args.fusion))
     circ.set_hamiltonian(w.terms)
     t_make = time.perf_counter() - t_make
     theta_h = replica_theta(w.theta, rank)
@@ -790,6 +791,8 @@ def main():
     ap.add_argument("--specialize", type=int, default=1,
                     help="complex64: 1 (default) forward and Hamiltonian passes run kernels generated for the "
                          "circuit's passes, compiled when the circuit is made (outside the timed region); 0 generic")
+    ap.add_argument("--fusion", type=int, default=1,
+                    help="0: one kernel per gate (the unfused passes, for their HBM figures)")
     ap.add_argument("--cfg", type=int, default=3)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--layers", type=int, default=None)
