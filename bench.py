@@ -788,9 +788,10 @@ def main():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--c128-arith", default="fp64", choices=["fp64", "float-float"],
                     help="arithmetic of the complex128 tile passes")
-    ap.add_argument("--specialize", type=int, default=1,
-                    help="complex64: 1 (default) forward and Hamiltonian passes run kernels generated for the "
-                         "circuit's passes, compiled when the circuit is made (outside the timed region); 0 generic")
+    ap.add_argument("--specialize", type=int, default=2,
+                    help="complex64: kernels generated for the circuit's passes, compiled when the circuit is made "
+                         "(outside the timed region): 1 forward and Hamiltonian passes, 2 (default) also the "
+                         "reverse passes; 0 the generic kernels")
     ap.add_argument("--fusion", type=int, default=1,
                     help="0: one kernel per gate (the unfused passes, for their HBM figures)")
     ap.add_argument("--cfg", type=int, default=3)

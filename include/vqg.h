@@ -110,15 +110,14 @@ typedef struct vqg_options {
                                     keep the fastest (see vqg_autotune)                     */
     int32_t c128_arith;          /* complex128 tile-pass arithmetic (vqg_c128_arith):
                                     VQG_C128_FP64 (default) or VQG_C128_FLOAT_FLOAT      */
-    int32_t specialize;          /* 1: the complex64 forward tile passes run kernels
-                                    generated for this circuit's passes (straight-line op
-                                    sequences, compiled with nvcc when the schedule is
-                                    planned and cached on disk; needs nvcc and the
-                                    library's headers at run time, VQG_ERR_UNSUPPORTED
-                                    otherwise); 2: the reverse passes too (their generated
-                                    code outgrows the instruction cache on long passes:
-                                    slower at 30 qubits); results equal the default
-                                    kernels'.  0 (default): the generic kernels only       */
+    int32_t specialize;          /* complex64 tile passes run kernels generated for this
+                                    circuit's passes (straight-line op sequences, compiled
+                                    with nvcc when the schedule or Hamiltonian is set and
+                                    cached on disk; needs nvcc and the library's headers
+                                    at run time, VQG_ERR_UNSUPPORTED otherwise): 1 the
+                                    forward and Hamiltonian passes, 2 the reverse passes
+                                    too; results agree with the default kernels to
+                                    rounding.  0 (default): the generic kernels only       */
     int32_t reserved[6];
 } vqg_options;
 
@@ -232,7 +231,8 @@ typedef struct vqg_plan_info {
     int32_t reverse_stages;
     int32_t stage_ops;
     int32_t diag_blocks;
-    int32_t specialized;  /* the specialize level in effect: 0 none, 1 forward, 2 both */
+    int32_t specialized;  /* the specialize level in effect: 0 none, 1 forward (and
+                             Hamiltonian), 2 also reverse */
     int32_t reserved[2];
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);

@@ -1843,6 +1843,57 @@ VQG_DEV void fwd_scatter(StageGeo<T, K, R> &g, bool has_phase, amp_t<T> *tile, c
     }
 }
 
+// Reverse diagonal block, split for the specialised kernels (rev_diag does both parts for
+// the interpreted pass, for any item list): rev_diag_sums forms the block's input sums
+// H[k] = sum over register index bit k = 0 of p_j and S = sum of all p_j, with
+// p_j = Im(conj(lambda_j) phi_j), from the same pairwise tree as rev_diag; an RZ on register
+// bit k then has Im<lambda|Z|phi> = 2 H[k] - S, one on a thread-level qubit +-S.
+template <int R>
+VQG_DEV void rev_diag_sums(const float2 (&a)[1 << R], const float2 (&l)[1 << R], float (&H)[R], float &S) {
+    constexpr int NA = 1 << R;
+    float2 q[NA / 2];
+#pragma unroll
+    for (int m = 0; m < NA / 2; ++m)
+        q[m] = make_float2(l[2 * m].x * a[2 * m].y - l[2 * m].y * a[2 * m].x,
+                           l[2 * m + 1].x * a[2 * m + 1].y - l[2 * m + 1].y * a[2 * m + 1].x);
+#pragma unroll
+    for (int k = 1; k < R; ++k) {  // fold index bit k (bit k - 1 of m)
+        const int len = (NA / 2) >> (k - 1);
+        float2 h = q[0];
+#pragma unroll
+        for (int m = 1; m < len / 2; ++m) h = __fadd2_rn(h, q[2 * m]);
+        H[k] = h.x + h.y;
+#pragma unroll
+        for (int m = 0; m < len / 2; ++m) q[m] = __fadd2_rn(q[2 * m], q[2 * m + 1]);
+    }
+    H[0] = q[0].x;
+    S = q[0].x + q[0].y;
+}
+// The block's table times its per-thread factor on phi and lambda (rev_diag's second part);
+// the per-thread sign pattern only exists where the block has a CZ between a register bit
+// and a thread-level qubit (HAS_RT), otherwise c = 0 and the pattern is all +1.
+template <int R, bool HAS_RT>
+VQG_DEV void rev_diag_apply(float2 (&a)[1 << R], float2 (&l)[1 << R], const Prog<float, R> &pg, int d,
+                            uint64_t gb, float2 &phase) {
+    constexpr int NA = 1 << R;
+    float2 tau;
+    uint32_t c;
+    diag_thread<float, R>(pg, pg.dg[d], gb, tau, c);
+    phase = cmul<float>(tau, phase);
+    const float2 *tab = pg.tab + d * NA;
+    uint32_t w = 0;
+    if constexpr (HAS_RT) w = walsh_bits(c);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        float2 dj = tab[j];
+        if constexpr (HAS_RT)
+            if ((w >> j) & 1u) dj = neg<float>(dj);
+        const float2 dr = make_float2(dj.x, dj.x), di2 = make_float2(-dj.y, dj.y);
+        a[j] = __ffma2_rn(dr, a[j], __fmul2_rn(di2, make_float2(a[j].y, a[j].x)));
+        l[j] = __ffma2_rn(dr, l[j], __fmul2_rn(di2, make_float2(l[j].y, l[j].x)));
+    }
+}
+
 // Forward op bodies for the specialised kernels (the interpreted pass runs apply_fwd_op).
 template <int KB, int R, typename T>
 VQG_DEV void fwd_op_ry(amp_t<T> (&a)[1 << R], const amp_t<T> *m, T &kacc) {

@@ -182,10 +182,25 @@ std::string gen_rev(const Plan &pl, int pass) {
                 o << "      " << srow << " = rev_op_cgen<" << (op.type - OP_CRX) << ", " << kb << ", " << R
                   << ", T>(a, l, " << prm(ol) << ", " << op.rm0 << "u, " << ctrl_expr(op) << ", k2acc);\n";
                 break;
-            case OP_DIAG:
-                o << "      rev_diag<" << R << ", NA, T>(a, l, pg, pg.dg[" << op.diag << "], " << op.diag << ", gb, "
-                  << sptr << ", NT, phase, k2acc);\n";
+            case OP_DIAG: {
+                // the block's own RZ items only, and the sign pattern only with a register-thread CZ
+                const FDiag &D = pl.diags[P.rdiag0 + op.diag];
+                o << "      {  // diagonal block " << op.diag << "\n";
+                if (D.n_rz > 0) {
+                    o << "        float H[" << R << "], S; rev_diag_sums<" << R << ">(a, l, H, S);\n";
+                    for (int r = 0; r < D.n_rz; ++r) {
+                        const FDItem &x = pl.items[D.item0 + r];
+                        const std::string dst = "stash[" + std::to_string((int)op.row + r) + " * NT + tid]";
+                        if (x.type == DI_RZ_REG)
+                            o << "        " << dst << " = (2.f * H[" << x.k0 << "] - S) * k2acc;\n";
+                        else
+                            o << "        " << dst << " = ((gb & " << (unsigned long long)x.g0 << "ull) ? -S : S) * k2acc;\n";
+                    }
+                }
+                o << "        rev_diag_apply<" << R << ", " << (D.has_rt ? "true" : "false") << ">(a, l, pg, " << op.diag
+                  << ", gb, phase);\n      }\n";
                 break;
+            }
             case OP_FLUSH:
                 o << "      __syncthreads(); reduce_rows<T, NT>(stash, " << op.lslot << ", " << (int)op.row
                   << ", acc, tid); __syncthreads();\n";
