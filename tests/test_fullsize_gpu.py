@@ -44,17 +44,20 @@ def test_full_gradient_vs_oracle(cfg, dtype):
     assert_parity(dtype, e, g, gold["energy"], np.array(gold["grad"]), w.name)
 
 
-def test_n30_bench_configuration():
+@pytest.mark.parametrize("spec", [2, 0])
+def test_n30_bench_configuration(spec):
     """n=30, 745 gates, 200 Pauli strings, complex64 with the default fused schedule
-    and checkpoints (what bench.py times)."""
+    and checkpoints, on the specialised kernels (what bench.py times) and the generic ones."""
     w = W.config(3)
     gold = _gold(f"cfg3_n{w.n}_energy")
-    with _circ(w, "c64") as c:
+    with _circ(w, "c64", specialize=spec) as c:
         e64, g64 = c.energy_and_gradient(w.theta)
         assert c.plan()["checkpoints"] >= 1
         e64b, g64b = c.energy_and_gradient(w.theta)
     assert e64 == e64b and np.array_equal(g64, g64b)  # deterministic reductions
     assert energy_err(e64, gold["energy"]) <= TOL["c64"]
+    if spec == 0:  # the complex128 comparison below is made once, for the benched kernels
+        return
     with _circ(w, "c128") as c:
         e128, g128 = c.energy_and_gradient(w.theta)
         assert energy_err(e128, gold["energy"]) <= TOL["c128"]
@@ -69,8 +72,9 @@ def test_n30_bench_configuration():
             assert g128[p] == pytest.approx(fd, abs=1e-7)
 
 
-@pytest.mark.parametrize("dtype,arith", [("c128", "fp64"), ("c128", "float-float"), ("c64", "fp64")])
-def test_n29_bench_recipe_vs_oracle(dtype, arith):
+@pytest.mark.parametrize("dtype,arith,spec", [("c128", "fp64", 0), ("c128", "float-float", 0), ("c64", "fp64", 0),
+                                              ("c64", "fp64", 2)])
+def test_n29_bench_recipe_vs_oracle(dtype, arith, spec):
     """The bench recipe at n=29 (the largest size whose full Algorithm 1 gradient the
     oracle computes on a 62 GB host) against the oracle's complete gradient: the default
     fused schedule (13-qubit tiles for complex64, 12 for complex128) leaves at least 16
@@ -79,13 +83,14 @@ def test_n29_bench_recipe_vs_oracle(dtype, arith):
     w = W.config(3, n=29)
     gold = _gold(f"cfg3_n{w.n}")
     assert gold["workload"] == w.name and len(gold["grad"]) == w.n_params
-    with _circ(w, dtype, c128_arith=arith) as c:
+    with _circ(w, dtype, c128_arith=arith, specialize=spec) as c:
         e, g = c.energy_and_gradient(w.theta)
         plan = c.plan()
+    assert plan["specialized"] == spec
     assert plan["tile_qubits"] == (13 if dtype == "c64" else 12) and w.n - plan["tile_qubits"] >= 16
     if dtype == "c64":
         assert plan["checkpoints"] >= 1
-    assert_parity(dtype, e, g, gold["energy"], np.array(gold["grad"]), f"{w.name} {dtype} {arith}")
+    assert_parity(dtype, e, g, gold["energy"], np.array(gold["grad"]), f"{w.name} {dtype} {arith} spec={spec}")
 
 
 def _central_differences(w, g64, g_gold, count=8, d=1e-4):
