@@ -14,7 +14,8 @@
 // nvcc into a cubin (cached on disk by a hash of the source and the compiler command),
 // loaded with cudaLibraryLoadData and launched with cudaLaunchKernel on the circuit's
 // stream.  Compilation needs nvcc (VQG_NVCC, $CUDA_HOME/bin/nvcc, /usr/local/cuda/bin/nvcc
-// or PATH) and the library's own headers, found next to libvqg.so.
+// or PATH) and the library's own headers, found next to libvqg.so (or in VQG_SPEC_SRC and
+// VQG_SPEC_INC).  The cache directory is VQG_SPEC_CACHE (default $TMPDIR/vqg_spec_<uid>).
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <sys/stat.h>
@@ -243,6 +244,8 @@ void source_dirs(std::string &csrc, std::string &inc) {
     const std::string pkg = dirname_of(info.dli_fname ? info.dli_fname : "./libvqg.so");
     csrc = pkg + "/csrc";
     inc = dirname_of(pkg) + "/include";
+    if (const char *e = std::getenv("VQG_SPEC_SRC")) csrc = e;  // headers kept elsewhere
+    if (const char *e = std::getenv("VQG_SPEC_INC")) inc = e;
 }
 
 bool exists(const std::string &p) {
