@@ -1917,36 +1917,45 @@ VQG_DEV void fwd_op_diag(amp_t<T> (&a)[1 << R], const Prog<T, R> &pg, int d, uin
 }
 
 
-// Specialised Hamiltonian pass (spec.cu): ham_tile with the group loop replaced by the
-// generated Body::groups, which visits the pass's groups with their flip masks, term masks,
-// classes and weight kinds as literals (weights and the tile's signs still come from the
-// shared-memory table, in plan order).
-template <typename T, int K, bool L2ONLY, typename Body>
-VQG_DEV T ham_tile_spec(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &tb, uint64_t base, bool first,
-                        const amp_t<T> *__restrict__ psi, amp_t<T> *__restrict__ lam, int tid) {
-    using A = amp_t<T>;
-    using IO = TileIO<T, K>;
-    using G = HamGeo<T, K>;
-    constexpr int AB = FT<T>::AB, L = FT<T>::L, NT = 256;
+// Specialised Hamiltonian pass (spec.cu), complex64: ham_tile with the group loop replaced
+// by the generated Body::groups, which visits the pass's groups with their flip masks, term
+// masks, classes and weight kinds as literals (weights and the tile's signs still come from
+// the shared-memory table, in plan order).
+//
+// Amplitudes are held in slot order: a 16-byte chunk of the tile holds the two amplitudes
+// t and t ^ 1 (swz(t ^ 1) = swz(t) ^ 1), in an order given by bit 0 of swz(t), which the
+// swizzle folds from higher index bits (b_i, per chunk at run time).  Slot j of own chunk i
+// (logical amplitude j ^ b_i) has its partner under a flip mask x at slot j ^ x0 of the chunk
+// at B_i ^ (swz(x) & ~1): the partners of both slots come with one 16-byte load and their
+// positions are literals.  b_i enters only the sign of terms whose class has bit 0 (b31[i] =
+// b_i << 31), and the logical order is restored once per batch when lambda is written.
+template <int K, bool L2ONLY, typename Body>
+VQG_DEV float ham_tile_spec(float2 *tile, const uint64_t *row_off, HamTab<float, K> &tb, uint64_t base, bool first,
+                            const float2 *__restrict__ psi, float2 *__restrict__ lam, int tid) {
+    using A = float2;
+    using IO = TileIO<float, K>;
+    using G = HamGeo<float, K>;
+    constexpr int AB = 8, L = FT<float>::L, NT = 256;
     constexpr int CPT = G::CPT, BCH = G::BCH, BA = G::BA;
+    static_assert(IO::CA == 2 && BA == 2 * BCH, "two amplitudes per chunk");
     IO::template load<NT, L2ONLY>(tile, psi, base, row_off, tid);
     for (int k = tid; k < tb.n_terms; k += NT) {
         const A w = tb.t_w[k];
-        tb.t_weff[k] = (__popcll(base & tb.t_znt[k]) & 1) ? mk<T>(-w.x, -w.y) : w;
+        tb.t_weff[k] = (__popcll(base & tb.t_znt[k]) & 1) ? mk<float>(-w.x, -w.y) : w;
     }
     for (int g = tid; g < tb.ng; g += NT)
         if (tb.g_nt[g] == 1) {
             const int j = (int)tb.g_t0[g];
             const A w = tb.t_w[j];
-            tb.g_w[g] = (__popcll(base & tb.t_znt[j]) & 1) ? mk<T>(-w.x, -w.y) : w;
+            tb.g_w[g] = (__popcll(base & tb.t_znt[j]) & 1) ? mk<float>(-w.x, -w.y) : w;
         }
     __syncthreads();
-    T run = 0;
+    float run = 0;
 #pragma unroll 1
     for (int b0 = 0; b0 < CPT; b0 += BCH) {
-        uint32_t t0, sw[BA];
+        uint32_t t0, B[BCH], b31[BCH];
         uint64_t gch[BCH];
-        A mine[BA], out[BA], delta[BA];
+        A mine[BA], out[BA], delta[BA];  // mine, delta: slot order; out: logical order
 #pragma unroll
         for (int i = 0; i < BCH; ++i) {
             const int c = tid + NT * (b0 + i);
@@ -1954,26 +1963,29 @@ VQG_DEV T ham_tile_spec(amp_t<T> *tile, const uint64_t *row_off, HamTab<T, K> &t
             const uint32_t tc = (uint32_t)(row << L) | (uint32_t)(col * IO::CA);
             if (i == 0) t0 = tc;
             gch[i] = base | row_off[row] | (uint64_t)(col * IO::CA);
-#pragma unroll
-            for (int e = 0; e < IO::CA; ++e) {
-                sw[i * IO::CA + e] = swz<AB>(tc + e);
-                mine[i * IO::CA + e] = tile[sw[i * IO::CA + e]];
-                out[i * IO::CA + e] = mk<T>((T)0, (T)0);
-                delta[i * IO::CA + e] = mk<T>((T)0, (T)0);
-            }
+            const uint32_t sw = swz<AB>(tc);
+            B[i] = sw & ~1u;
+            b31[i] = sw << 31;
+            const float4 m = *reinterpret_cast<const float4 *>(tile + B[i]);
+            mine[2 * i] = make_float2(m.x, m.y);
+            mine[2 * i + 1] = make_float2(m.z, m.w);
+            out[2 * i] = out[2 * i + 1] = delta[2 * i] = delta[2 * i + 1] = make_float2(0.f, 0.f);
             if (!first) {
                 const float4 *g = reinterpret_cast<const float4 *>(lam + gch[i]);
-                IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), out + i * IO::CA);
+                IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), out + 2 * i);
             }
         }
-        Body::groups(tb, tile, t0, sw, delta);
+        Body::groups(tb, tile, t0, B, b31, delta);
 #pragma unroll
-        for (int k = 0; k < BA; ++k) {
-            run += mine[k].x * delta[k].x + mine[k].y * delta[k].y;
-            out[k] = cadd<T>(out[k], delta[k]);
+        for (int k = 0; k < BA; ++k) run += mine[k].x * delta[k].x + mine[k].y * delta[k].y;
+#pragma unroll
+        for (int i = 0; i < BCH; ++i) {
+            const bool swp = b31[i] != 0u;  // logical amplitude e sits at slot e ^ b_i
+            const A d0 = swp ? delta[2 * i + 1] : delta[2 * i], d1 = swp ? delta[2 * i] : delta[2 * i + 1];
+            out[2 * i] = cadd<float>(out[2 * i], d0);
+            out[2 * i + 1] = cadd<float>(out[2 * i + 1], d1);
+            __stcs(reinterpret_cast<float4 *>(lam + gch[i]), IO::pack(out + 2 * i));
         }
-#pragma unroll
-        for (int i = 0; i < BCH; ++i) __stcs(reinterpret_cast<float4 *>(lam + gch[i]), IO::pack(out + i * IO::CA));
     }
     __syncthreads();
     return run;
@@ -2004,8 +2016,8 @@ VQG_DEV void ham_pass_spec(const amp_t<T> *__restrict__ psi, amp_t<T> *__restric
             TileIO<T, K>::template prefetch<NT>(psi, next, row_off, tid);
             if (!P.first) TileIO<T, K>::template prefetch<NT>(lam, next, row_off, tid);
         }
-        const T run = ham_tile_spec<T, K, false, Body>(tile, row_off, tb, tile_base(ti, P.nontile, P.n_nontile),
-                                                       P.first != 0, psi, lam, tid);
+        const T run = ham_tile_spec<K, false, Body>(tile, row_off, tb, tile_base(ti, P.nontile, P.n_nontile),
+                                                    P.first != 0, psi, lam, tid);
         eacc += (double)warp_tree<T>(run);
     }
     if ((tid & 31) == 0) wsum[tid >> 5] = eacc;

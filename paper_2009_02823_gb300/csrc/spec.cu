@@ -359,83 +359,104 @@ std::string hex(uint32_t v) {
     return b;
 }
 
-// Straight-line group work of one Hamiltonian pass (mirrors ham_tile's group loop; every
-// group takes the direct accumulation of its terms into the batch factors).
+// Straight-line group work of one Hamiltonian pass (the arithmetic of ham_tile's group
+// loop; every group takes the direct accumulation of its terms into the batch factors), in
+// the slot order of ham_tile_spec: one 16-byte partner load per chunk and group.
 std::string gen_ham(const Plan &pl, int h) {
     const HPass &P = pl.hp[h];
     const int K = pl.K;
     int BA, D, SH;
     ham_geo(K, BA, D, SH);
+    const int BCH = BA / 2;
     const int term_base = P.n_group ? pl.hg[P.group0].term0 : 0;
     std::ostringstream o;
     o << "#include \"fused_kernels.cuh\"\n"
       << "namespace vqg { namespace spec {\n"
       << "struct Body {\n"
       << "  static VQG_DEV void groups(HamTab<float, " << K << "> &tb, const float2 *tile, uint32_t t0, "
-      << "const uint32_t (&sw)[" << BA << "], float2 (&delta)[" << BA << "]) {\n"
-      << "    using A = float2;\n";
+      << "const uint32_t (&B)[" << BCH << "], const uint32_t (&b31)[" << BCH << "], float2 (&delta)[" << BA << "]) {\n"
+      << "    using A = float2; (void)b31;\n";
+    // the partner of slot j of chunk i: component pair j ^ x0 of the 16-byte load q<i>
+    auto partner = [](int i, int pos) {
+        return "make_float2(q" + std::to_string(i) + (pos ? ".z, q" : ".x, q") + std::to_string(i) + (pos ? ".w)" : ".y)");
+    };
     for (int g = 0; g < P.n_group; ++g) {
         const HGroup &G = pl.hg[P.group0 + g];
         if (G.n_term == 0) continue;  // the diagonal group exists even without terms
         bool re = true, im = true;
-        for (int i = 0; i < G.n_term; ++i) {
-            re = re && pl.ht[G.term0 + i].wi == 0.0;
-            im = im && pl.ht[G.term0 + i].wr == 0.0;
+        for (int t = 0; t < G.n_term; ++t) {
+            re = re && pl.ht[G.term0 + t].wi == 0.0;
+            im = im && pl.ht[G.term0 + t].wr == 0.0;
         }
         const int kind = re ? 0 : (im ? 1 : 2);
-        o << "    {  // group " << g << ": " << G.n_term << " term(s), kind " << kind << "\n"
-          << "      const uint32_t xs = swz<8>(" << hex(G.xl) << ");\n";
+        const uint32_t xs = swz<8>(G.xl), x0 = xs & 1u;
+        o << "    {  // group " << g << ": " << G.n_term << " term(s), kind " << kind << "\n";
+        for (int i = 0; i < BCH; ++i)
+            o << "      const float4 q" << i << " = *reinterpret_cast<const float4 *>(tile + (B[" << i << "] ^ "
+              << hex(xs & ~1u) << "));\n";
+        // the sign of slot j of chunk i for a term of class cls: parity((2i + j) & cls), a
+        // literal, plus b_i where cls has bit 0
+        auto neg = [](int i, int j, uint32_t cls) { return (__builtin_popcount((unsigned)(2 * i + j) & cls) & 1) != 0; };
         if (G.n_term == 1 && kind < 2) {
             const HTerm &t = pl.ht[G.term0];
             const uint32_t cls = class_bits(t.zl, D, SH);
             o << "      const A w = tb.g_w[" << g << "];\n"
               << "      const uint32_t wb = __float_as_uint(" << (kind == 0 ? "w.x" : "w.y") << ") ^ ((uint32_t)__popc(t0 & "
               << hex(t.zl) << ") << 31);\n";
-            for (int k = 0; k < BA; ++k) {
-                const bool neg = __builtin_popcount((unsigned)k & cls) & 1;
-                o << "      { const float v = __uint_as_float(wb" << (neg ? " ^ 0x80000000u" : "") << "); const A p = tile[sw["
-                  << k << "] ^ xs]; ";
-                if (kind == 0)
-                    o << "delta[" << k << "].x = fmaf(v, p.x, delta[" << k << "].x); delta[" << k << "].y = fmaf(v, p.y, delta["
-                      << k << "].y); }\n";
-                else
-                    o << "delta[" << k << "].x = fmaf(-v, p.y, delta[" << k << "].x); delta[" << k << "].y = fmaf(v, p.x, delta["
-                      << k << "].y); }\n";
+            for (int i = 0; i < BCH; ++i) {
+                o << "      { const uint32_t wi = wb" << ((cls & 1u) ? " ^ b31[" + std::to_string(i) + "]" : std::string()) << ";\n";
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int k = 2 * i + jj;
+                    o << "        { const float v = __uint_as_float(wi" << (neg(i, jj, cls) ? " ^ 0x80000000u" : "")
+                      << "); const A p = " << partner(i, jj ^ (int)x0) << "; ";
+                    if (kind == 0)
+                        o << "delta[" << k << "].x = fmaf(v, p.x, delta[" << k << "].x); delta[" << k << "].y = fmaf(v, p.y, delta["
+                          << k << "].y); }\n";
+                    else
+                        o << "delta[" << k << "].x = fmaf(-v, p.y, delta[" << k << "].x); delta[" << k << "].y = fmaf(v, p.x, delta["
+                          << k << "].y); }\n";
+                }
+                o << "      }\n";
             }
         } else {
             o << "      float ux[" << BA << "], uy[" << BA << "];\n"
               << "      #pragma unroll\n      for (int k = 0; k < " << BA << "; ++k) ux[k] = 0.f, uy[k] = 0.f;\n";
-            for (int i = 0; i < G.n_term; ++i) {
-                const HTerm &t = pl.ht[G.term0 + i];
-                const int j = G.term0 + i - term_base;
-                const uint32_t cls = class_bits(t.zl, D, SH);
-                o << "      { const A w = tb.t_weff[" << j << "]; const uint32_t s = (uint32_t)__popc(t0 & " << hex(t.zl)
+            for (int t = 0; t < G.n_term; ++t) {
+                const HTerm &tm = pl.ht[G.term0 + t];
+                const int jt = G.term0 + t - term_base;
+                const uint32_t cls = class_bits(tm.zl, D, SH);
+                o << "      { const A w = tb.t_weff[" << jt << "]; const uint32_t s = (uint32_t)__popc(t0 & " << hex(tm.zl)
                   << ") << 31;";
                 if (kind != 1) o << " const uint32_t bx = __float_as_uint(w.x) ^ s;";
                 if (kind != 0) o << " const uint32_t by = __float_as_uint(w.y) ^ s;";
                 o << "\n";
-                for (int k = 0; k < BA; ++k) {
-                    const bool neg = __builtin_popcount((unsigned)k & cls) & 1;
-                    const char *f = neg ? " ^ 0x80000000u" : "";
-                    o << "        ";
-                    if (kind != 1) o << "ux[" << k << "] += __uint_as_float(bx" << f << "); ";
-                    if (kind != 0) o << "uy[" << k << "] += __uint_as_float(by" << f << "); ";
-                    o << "\n";
+                for (int i = 0; i < BCH; ++i) {
+                    const std::string bi = (cls & 1u) ? " ^ b31[" + std::to_string(i) + "]" : std::string();
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int k = 2 * i + jj;
+                        const char *f = neg(i, jj, cls) ? " ^ 0x80000000u" : "";
+                        o << "        ";
+                        if (kind != 1) o << "ux[" << k << "] += __uint_as_float(bx" << bi << f << "); ";
+                        if (kind != 0) o << "uy[" << k << "] += __uint_as_float(by" << bi << f << "); ";
+                        o << "\n";
+                    }
                 }
                 o << "      }\n";
             }
-            for (int k = 0; k < BA; ++k) {
-                o << "      { const A p = tile[sw[" << k << "] ^ xs]; ";
-                if (kind == 0)
-                    o << "delta[" << k << "].x = fmaf(ux[" << k << "], p.x, delta[" << k << "].x); delta[" << k
-                      << "].y = fmaf(ux[" << k << "], p.y, delta[" << k << "].y); }\n";
-                else if (kind == 1)
-                    o << "delta[" << k << "].x = fmaf(-uy[" << k << "], p.y, delta[" << k << "].x); delta[" << k
-                      << "].y = fmaf(uy[" << k << "], p.x, delta[" << k << "].y); }\n";
-                else
-                    o << "delta[" << k << "] = cfma<float>(mk<float>(ux[" << k << "], uy[" << k << "]), p, delta[" << k
-                      << "]); }\n";
-            }
+            for (int i = 0; i < BCH; ++i)
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int k = 2 * i + jj;
+                    o << "      { const A p = " << partner(i, jj ^ (int)x0) << "; ";
+                    if (kind == 0)
+                        o << "delta[" << k << "].x = fmaf(ux[" << k << "], p.x, delta[" << k << "].x); delta[" << k
+                          << "].y = fmaf(ux[" << k << "], p.y, delta[" << k << "].y); }\n";
+                    else if (kind == 1)
+                        o << "delta[" << k << "].x = fmaf(-uy[" << k << "], p.y, delta[" << k << "].x); delta[" << k
+                          << "].y = fmaf(uy[" << k << "], p.x, delta[" << k << "].y); }\n";
+                    else
+                        o << "delta[" << k << "] = cfma<float>(mk<float>(ux[" << k << "], uy[" << k << "]), p, delta[" << k
+                          << "]); }\n";
+                }
         }
         o << "    }\n";
     }
