@@ -1869,23 +1869,20 @@ VQG_DEV void rev_diag_sums(const float2 (&a)[1 << R], const float2 (&l)[1 << R],
     H[0] = q[0].x;
     S = q[0].x + q[0].y;
 }
-// The block's table times its per-thread factor on phi and lambda (rev_diag's second part);
-// the per-thread sign pattern only exists where the block has a CZ between a register bit
-// and a thread-level qubit (HAS_RT), otherwise c = 0 and the pattern is all +1.
+// The block's table on phi and lambda (rev_diag's second part); the per-thread factor tau
+// and the sign mask c are computed by the generated code from the block's thread-level
+// items (literal qubits) and the pending phase takes tau.  The sign pattern only exists
+// where the block has a CZ between a register bit and a thread-level qubit (HAS_RT).
 template <int R, bool HAS_RT>
-VQG_DEV void rev_diag_apply(float2 (&a)[1 << R], float2 (&l)[1 << R], const Prog<float, R> &pg, int d,
-                            uint64_t gb, float2 &phase) {
+VQG_DEV void rev_diag_table(float2 (&a)[1 << R], float2 (&l)[1 << R], const float2 *tab, uint32_t c) {
     constexpr int NA = 1 << R;
-    float2 tau;
-    uint32_t c;
-    diag_thread<float, R>(pg, pg.dg[d], gb, tau, c);
-    phase = cmul<float>(tau, phase);
-    const float2 *tab = pg.tab + d * NA;
     uint32_t w = 0;
     if constexpr (HAS_RT) w = walsh_bits(c);
+    const float4 *t4 = reinterpret_cast<const float4 *>(tab);  // two entries per 16-byte load
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
-        float2 dj = tab[j];
+        const float4 q = t4[j >> 1];
+        float2 dj = (j & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
         if constexpr (HAS_RT)
             if ((w >> j) & 1u) dj = neg<float>(dj);
         const float2 dr = make_float2(dj.x, dj.x), di2 = make_float2(-dj.y, dj.y);
@@ -1906,14 +1903,21 @@ VQG_DEV void fwd_op_ry(amp_t<T> (&a)[1 << R], const amp_t<T> *m, T &kacc) {
         op_ry<KB, 1 << R, T>(a, cs.x, cs.y);
     }
 }
-template <typename T, int R>
-VQG_DEV void fwd_op_diag(amp_t<T> (&a)[1 << R], const Prog<T, R> &pg, int d, uint64_t gb, amp_t<T> &phase,
-                         bool has_rt) {
-    amp_t<T> tau;
-    uint32_t c;
-    diag_thread<T, R>(pg, pg.dg[d], gb, tau, c);
-    phase = cmul<T>(tau, phase);
-    diag_apply<1 << R, T>(a, pg.tab + d * (1 << R), c, has_rt);
+// The forward counterpart of rev_diag_table (psi only).
+template <int R, bool HAS_RT>
+VQG_DEV void fwd_diag_table(float2 (&a)[1 << R], const float2 *tab, uint32_t c) {
+    constexpr int NA = 1 << R;
+    uint32_t w = 0;
+    if constexpr (HAS_RT) w = walsh_bits(c);
+    const float4 *t4 = reinterpret_cast<const float4 *>(tab);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const float4 q = t4[j >> 1];
+        float2 dj = (j & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+        if constexpr (HAS_RT)
+            if ((w >> j) & 1u) dj = neg<float>(dj);
+        a[j] = __ffma2_rn(make_float2(dj.x, dj.x), a[j], __fmul2_rn(make_float2(-dj.y, dj.y), make_float2(a[j].y, a[j].x)));
+    }
 }
 
 

@@ -63,6 +63,39 @@ std::string ctrl_expr(const FOp &op) {
 
 std::string prm(int o) { return "pg.prm + " + std::to_string(4 * o); }
 
+// Literal per-thread factor of diagonal block D (what diag_thread computes from the item
+// table at run time): tau from the RZ phases and CZ signs on thread-level qubits, folded
+// into the stage's pending phase, and the sign mask c of the register-thread CZs.
+std::string diag_thread_code(const Plan &pl, const FDiag &D, int item_base, const char *ind) {
+    std::ostringstream o;
+    bool tau = false, sign = false;
+    o << ind << "uint32_t c = 0u; (void)c;\n";
+    for (int k = D.thr0; k < D.thr0 + D.n_thr; ++k) {
+        const FDItem &x = pl.items[D.item0 + k];
+        const int rel = D.item0 + k - item_base;
+        const int q0 = x.g0 ? __builtin_ctzll(x.g0) : 0, q1 = x.g1 ? __builtin_ctzll(x.g1) : 0;
+        if (x.type == DI_RZ_THR) {
+            const std::string f = "pg.iph[" + std::to_string(2 * rel) + " + (int)((gb >> " + std::to_string(q0) + ") & 1ull)]";
+            if (!tau) o << ind << "A tau = " << f << ";\n";
+            else o << ind << "tau = cmul<T>(" << f << ", tau);\n";
+            tau = true;
+        } else if (x.type == DI_CZ_TT) {
+            if (!sign) o << ind << "uint32_t ng = 0u;\n";
+            sign = true;
+            o << ind << "ng ^= (uint32_t)((gb >> " << q0 << ") & (gb >> " << q1 << ") & 1ull);\n";
+        } else if (x.type == DI_CZ_RT) {
+            o << ind << "c ^= (uint32_t)((gb >> " << q0 << ") & 1ull) << " << (int)x.k0 << ";\n";
+        }
+    }
+    if (sign) {
+        if (!tau) o << ind << "A tau = mk<T>((T)1, (T)0);\n";
+        o << ind << "if (ng) tau = neg<T>(tau);\n";
+        tau = true;
+    }
+    if (tau) o << ind << "phase = cmul<T>(tau, phase);\n";
+    return o.str();
+}
+
 // Straight-line body of one forward pass (mirrors fwd_tile + apply_fwd_op).
 std::string gen_fwd(const Plan &pl, int pass) {
     const FPass &P = pl.passes[pass];
@@ -110,10 +143,14 @@ std::string gen_fwd(const Plan &pl, int pass) {
                 o << "      op_cgen<" << kb << ", NA, T>(a, mat_of<T>(" << prm(ol) << "), " << op.rm0 << "u, "
                   << ctrl_expr(op) << ");\n";
                 break;
-            case OP_DIAG:
-                o << "      fwd_op_diag<T, " << R << ">(a, pg, " << op.diag << ", gb, phase, "
-                  << (pl.diags[P.diag0 + op.diag].has_rt ? "true" : "false") << ");\n";
+            case OP_DIAG: {
+                const FDiag &D = pl.diags[P.diag0 + op.diag];
+                o << "      {  // diagonal block " << op.diag << "\n"
+                  << diag_thread_code(pl, D, pl.diags[P.diag0].item0, "        ")
+                  << "        fwd_diag_table<" << R << ", " << (D.has_rt ? "true" : "false") << ">(a, pg.tab + "
+                  << op.diag * (1 << R) << ", c);\n      }\n";
                 break;
+            }
             default:
                 break;
             }
@@ -198,8 +235,9 @@ std::string gen_rev(const Plan &pl, int pass) {
                             o << "        " << dst << " = ((gb & " << (unsigned long long)x.g0 << "ull) ? -S : S) * k2acc;\n";
                     }
                 }
-                o << "        rev_diag_apply<" << R << ", " << (D.has_rt ? "true" : "false") << ">(a, l, pg, " << op.diag
-                  << ", gb, phase);\n      }\n";
+                o << diag_thread_code(pl, D, pl.diags[P.rdiag0].item0, "        ")
+                  << "        rev_diag_table<" << R << ", " << (D.has_rt ? "true" : "false") << ">(a, l, pg.tab + "
+                  << op.diag * (1 << R) << ", c);\n      }\n";
                 break;
             }
             case OP_FLUSH:
