@@ -955,8 +955,9 @@ int Circuit::issue_reverse_fused() {
             spec_launch_rev(pl, j, src, psi, lam, mats, gpart, nb, wmask, stream);
         } else {
             auto rev = !dbl ? launch_fused_rev_c64 : float_float(dbl, opt) ? launch_fused_rev_df : launch_fused_rev_c128;
-            rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags, pl->d_items,
-                pl->d_slot_map, mats, pl->n_tiles, gpart, nb, wmask, stream);
+            if (!rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags,
+                     pl->d_items, pl->d_slot_map, mats, pl->n_tiles, gpart, nb, wmask, stream))
+                return set_error(VQG_ERR_UNSUPPORTED, "no reverse kernel for K=%d Rr=%d", pl->K, pl->Rr);
         }
         prof_end();
     }

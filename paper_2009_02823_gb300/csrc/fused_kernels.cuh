@@ -248,22 +248,35 @@ VQG_DEV uint32_t walsh_bits(uint32_t c) {
 // matrices of the ops (U; the reverse kernel takes U^dagger of them), the RZ phases of
 // the items (conjugated for the reverse), and each diagonal block's 2^R-entry table
 // (RZ phases on register bits times CZ signs between register bits).
+// Byte offsets of a pass program's tables in shared memory for the counts it is sized
+// for; host code sizes the specialised kernels' shared memory with the same function.
+struct ProgOffsets {
+    size_t st, op, dg, it, prm, iph, tab, ti, bytes;
+};
+__host__ __device__ constexpr size_t prog_align(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ constexpr ProgOffsets prog_offsets(size_t ab, int R, int stages, int ops, int diags, int items) {
+    ProgOffsets o{};
+    o.st = 0;
+    o.op = prog_align(o.st + sizeof(FStage) * stages);
+    o.dg = prog_align(o.op + sizeof(FOp) * ops);
+    o.it = prog_align(o.dg + sizeof(FDiag) * diags);
+    o.prm = prog_align(o.it + sizeof(FDItem) * items);
+    o.iph = prog_align(o.prm + ab * 4 * ops);
+    o.tab = prog_align(o.iph + ab * 2 * items);
+    o.ti = prog_align(o.tab + ab * ((size_t)1 << R) * diags);
+    o.bytes = prog_align(o.ti + sizeof(uint32_t) * items);
+    return o;
+}
+
 template <typename T, int R>
 struct Prog {
     static constexpr int AB = FT<T>::AB;
-    static constexpr size_t align8(size_t x) { return (x + 15) & ~(size_t)15; }
     // shared-memory layout for the program budget C
     template <typename C = FullCaps>
     struct Layout {
-        static constexpr size_t o_st = 0;
-        static constexpr size_t o_op = align8(o_st + sizeof(FStage) * C::stages);
-        static constexpr size_t o_dg = align8(o_op + sizeof(FOp) * C::ops);
-        static constexpr size_t o_it = align8(o_dg + sizeof(FDiag) * C::diags);
-        static constexpr size_t o_prm = align8(o_it + sizeof(FDItem) * C::items);
-        static constexpr size_t o_iph = align8(o_prm + (size_t)AB * 4 * C::ops);
-        static constexpr size_t o_tab = align8(o_iph + (size_t)AB * 2 * C::items);
-        static constexpr size_t o_ti = align8(o_tab + (size_t)AB * (1 << R) * C::diags);
-        static constexpr size_t bytes = align8(o_ti + sizeof(uint32_t) * C::items);
+        static constexpr ProgOffsets po = prog_offsets(AB, R, C::stages, C::ops, C::diags, C::items);
+        static constexpr size_t o_st = po.st, o_op = po.op, o_dg = po.dg, o_it = po.it, o_prm = po.prm,
+                                o_iph = po.iph, o_tab = po.tab, o_ti = po.ti, bytes = po.bytes;
     };
 
     FStage *st;
@@ -1294,17 +1307,34 @@ __global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
 }
 
 // ------------------------------------------------------------------ reverse pass
-template <typename T, int K, int R, typename CAPS = FullCaps>
+// Shared-memory layout of a reverse pass: phi and lambda tiles, row offsets, the program,
+// FP64 accumulators, ROWS stash rows of NT values and the slot map.  Host code sizes the
+// specialised kernels (pass-sized programs, ROWS = two stash buffers) with rev_offsets.
+struct RevOffsets {
+    size_t row, prog, acc, stash, map, bytes;
+};
+__host__ __device__ constexpr RevOffsets rev_offsets(int K, int R, int L, size_t ab, size_t tsize, size_t prog_bytes,
+                                                     int rows) {
+    RevOffsets o{};
+    o.row = 2 * ((size_t)1 << K) * ab;
+    o.prog = o.row + sizeof(uint64_t) * ((size_t)1 << (K - L));
+    o.acc = o.prog + prog_bytes;
+    o.stash = o.acc + sizeof(double) * kMaxPassSlots;
+    o.map = o.stash + tsize * (size_t)rows * ((size_t)1 << (K - R));
+    o.bytes = o.map + sizeof(int) * kMaxPassSlots;
+    return o;
+}
+constexpr size_t kMaxSmemBytes = 227 * 1024;
+
+template <typename T, int K, int R, typename CAPS = FullCaps, int ROWS = stash_rows<T>()>
 struct RevCfg {
     using Caps = CAPS;
     static constexpr int NT = 1 << (K - R), NW = NT / 32;
-    static constexpr size_t o_row = 2 * (size_t)(1 << K) * FT<T>::AB;
-    static constexpr size_t o_prog = o_row + sizeof(uint64_t) * (1 << (K - FT<T>::L));
-    static constexpr size_t o_acc = o_prog + Prog<T, R>::template Layout<CAPS>::bytes;
-    static constexpr size_t o_stash = o_acc + sizeof(double) * kMaxPassSlots;
-    static constexpr size_t o_map = o_stash + sizeof(T) * (size_t)stash_rows<T>() * NT;
-    static constexpr size_t smem() { return o_map + sizeof(int) * kMaxPassSlots; }
-    static_assert(o_map + sizeof(int) * kMaxPassSlots <= 227 * 1024, "reverse pass exceeds shared memory");
+    static constexpr RevOffsets ro =
+        rev_offsets(K, R, FT<T>::L, FT<T>::AB, sizeof(T), Prog<T, R>::template Layout<CAPS>::bytes, ROWS);
+    static constexpr size_t o_row = ro.row, o_prog = ro.prog, o_acc = ro.acc, o_stash = ro.stash, o_map = ro.map;
+    static constexpr size_t smem() { return ro.bytes; }
+    static_assert(ro.bytes <= kMaxSmemBytes, "reverse pass exceeds shared memory");
     static_assert(o_stash % 16 == 0, "stash rows are read with 16-byte loads");
 };
 
@@ -1779,14 +1809,14 @@ VQG_DEV void fwd_pass_spec(const amp_t<T> *__restrict__ src, amp_t<T> *__restric
     }
 }
 
-template <typename T, int K, int R, typename Body>
+template <typename T, int K, int R, typename Body, typename CAPS = FullCaps, int ROWS = stash_rows<T>()>
 VQG_DEV void rev_pass_spec(const amp_t<T> *__restrict__ phi_src, amp_t<T> *__restrict__ phi_dst,
                            amp_t<T> *__restrict__ lam, const FPass *__restrict__ passes, int pi,
                            const FStage *__restrict__ stages, const FOp *__restrict__ ops,
                            const FDiag *__restrict__ diags, const FDItem *__restrict__ items,
                            const int *__restrict__ slot_map, const typename FT<T>::mat_t *__restrict__ mats,
                            uint64_t n_tiles, double *__restrict__ partials, int nb, int wmask) {
-    using C = RevCfg<T, K, R>;
+    using C = RevCfg<T, K, R, CAPS, ROWS>;
     constexpr int NT = C::NT;
     extern __shared__ __align__(16) unsigned char smem[];
     amp_t<T> *tphi = reinterpret_cast<amp_t<T> *>(smem);
@@ -1869,6 +1899,12 @@ VQG_DEV void rev_diag_sums(const float2 (&a)[1 << R], const float2 (&l)[1 << R],
     H[0] = q[0].x;
     S = q[0].x + q[0].y;
 }
+// d * a in four scalar FP32 operations (a packed form needs the swapped pair (a.y, a.x)
+// built by moves and measured no faster).
+VQG_DEV float2 cmul_scalar(float2 d, float2 a) {
+    return make_float2(__fmaf_rn(-d.y, a.y, __fmul_rn(d.x, a.x)), __fmaf_rn(d.y, a.x, __fmul_rn(d.x, a.y)));
+}
+
 // The block's table on phi and lambda (rev_diag's second part); the per-thread factor tau
 // and the sign mask c are computed by the generated code from the block's thread-level
 // items (literal qubits) and the pending phase takes tau.  The sign pattern only exists
@@ -1885,9 +1921,8 @@ VQG_DEV void rev_diag_table(float2 (&a)[1 << R], float2 (&l)[1 << R], const floa
         float2 dj = (j & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
         if constexpr (HAS_RT)
             if ((w >> j) & 1u) dj = neg<float>(dj);
-        const float2 dr = make_float2(dj.x, dj.x), di2 = make_float2(-dj.y, dj.y);
-        a[j] = __ffma2_rn(dr, a[j], __fmul2_rn(di2, make_float2(a[j].y, a[j].x)));
-        l[j] = __ffma2_rn(dr, l[j], __fmul2_rn(di2, make_float2(l[j].y, l[j].x)));
+        a[j] = cmul_scalar(dj, a[j]);
+        l[j] = cmul_scalar(dj, l[j]);
     }
 }
 
@@ -1916,7 +1951,7 @@ VQG_DEV void fwd_diag_table(float2 (&a)[1 << R], const float2 *tab, uint32_t c) 
         float2 dj = (j & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
         if constexpr (HAS_RT)
             if ((w >> j) & 1u) dj = neg<float>(dj);
-        a[j] = __ffma2_rn(make_float2(dj.x, dj.x), a[j], __fmul2_rn(make_float2(-dj.y, dj.y), make_float2(a[j].y, a[j].x)));
+        a[j] = cmul_scalar(dj, a[j]);
     }
 }
 

@@ -39,7 +39,8 @@ struct Plan {
     // specialised kernels of each pass (spec.cu; cudaKernel_t handles), empty when the
     // passes run on the interpreted kernels
     std::vector<void *> spec_fwd, spec_rev, spec_ham;
-    size_t spec_smem_fwd = 0, spec_smem_rev = 0, spec_smem_ham = 0;
+    size_t spec_smem_fwd = 0, spec_smem_ham = 0;
+    std::vector<size_t> spec_smem_rev;  // per reverse pass
     const void *spec_ham_for = nullptr;  // the Hamiltonian tables (d_hp) spec_ham was built for
 };
 

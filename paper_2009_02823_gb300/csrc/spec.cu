@@ -168,11 +168,51 @@ std::string gen_fwd(const Plan &pl, int pass) {
     return o.str();
 }
 
+// Shared-memory geometry of one specialised reverse pass: the program sized to the pass's
+// own stages, ops, diagonal blocks and items (what load_prog copies), and two stash buffers
+// of kMaxStageRows rows when they fit (one otherwise).
+struct RevSpecGeo {
+    int ops, stages, diags, items, rows;
+    size_t smem;
+};
+RevSpecGeo rev_spec_geo(const Plan &pl, int pass) {
+    const FPass &P = pl.passes[pass];
+    RevSpecGeo g{};
+    g.stages = std::max(1, (int)P.n_rstage);
+    g.ops = 1;
+    if (P.n_rstage) {
+        const FStage &a = pl.stages[P.rstage0], &b = pl.stages[P.rstage0 + P.n_rstage - 1];
+        g.ops = std::max(1, b.op0 + b.n_op - a.op0);
+    }
+    g.diags = std::max(1, (int)P.n_rdiag);
+    g.items = 1;
+    if (P.n_rdiag) {
+        const FDiag &a = pl.diags[P.rdiag0], &b = pl.diags[P.rdiag0 + P.n_rdiag - 1];
+        g.items = std::max(1, b.item0 + b.n_item - a.item0);
+    }
+    const size_t prog = prog_offsets(sizeof(float2), pl.Rr, g.stages, g.ops, g.diags, g.items).bytes;
+    for (int rows : {2 * kMaxStageRows, kMaxStageRows}) {
+        g.rows = rows;
+        g.smem = rev_offsets(pl.K, pl.Rr, pl.L, sizeof(float2), sizeof(float), prog, rows).bytes;
+        if (g.smem <= kMaxSmemBytes) break;
+    }
+    return g;
+}
+
 // Straight-line body of one reverse pass (mirrors rev_tile).
 std::string gen_rev(const Plan &pl, int pass) {
     const FPass &P = pl.passes[pass];
     const int K = pl.K, R = pl.Rr, NT = 1 << (K - R);
     const int op_base = P.n_rstage ? pl.stages[P.rstage0].op0 : 0;
+    const RevSpecGeo geo = rev_spec_geo(pl, pass);
+    // with two stash buffers, consecutive reduction segments alternate between them: the
+    // barrier before a segment's reduction also orders the reduction of the segment before
+    // it (in the other buffer) ahead of that buffer's next writes, so no barrier follows
+    // a reduction
+    const bool dbuf = geo.rows == 2 * kMaxStageRows;
+    int buf = 0;
+    auto row_of = [&](int r) { return std::to_string(buf * kMaxStageRows + r); };
+    auto buf_ptr = [&]() { return buf ? "stash + " + std::to_string(kMaxStageRows) + " * NT" : std::string("stash"); };
     std::ostringstream o;
     o << "#include \"fused_kernels.cuh\"\n"
       << "namespace vqg { namespace spec {\n"
@@ -195,8 +235,8 @@ std::string gen_rev(const Plan &pl, int pass) {
             const int oi = st.op0 + i, ol = oi - op_base;
             const FOp &op = pl.ops[oi];
             const std::string kb = std::to_string((int)op.k);
-            const std::string srow = "stash[" + std::to_string((int)op.row) + " * NT + tid]";
-            const std::string sptr = "stash + " + std::to_string((int)op.row) + " * NT + tid";
+            const std::string srow = "stash[" + row_of((int)op.row) + " * NT + tid]";
+            const std::string sptr = "stash + " + row_of((int)op.row) + " * NT + tid";
             switch (op.type) {
             case OP_RY:
                 o << "      " << srow << " = rev_op_ry<" << kb << ", " << R << ", T>(a, l, " << prm(ol)
@@ -228,7 +268,7 @@ std::string gen_rev(const Plan &pl, int pass) {
                     o << "        float H[" << R << "], S; rev_diag_sums<" << R << ">(a, l, H, S);\n";
                     for (int r = 0; r < D.n_rz; ++r) {
                         const FDItem &x = pl.items[D.item0 + r];
-                        const std::string dst = "stash[" + std::to_string((int)op.row + r) + " * NT + tid]";
+                        const std::string dst = "stash[" + row_of((int)op.row + r) + " * NT + tid]";
                         if (x.type == DI_RZ_REG)
                             o << "        " << dst << " = (2.f * H[" << x.k0 << "] - S) * k2acc;\n";
                         else
@@ -241,8 +281,9 @@ std::string gen_rev(const Plan &pl, int pass) {
                 break;
             }
             case OP_FLUSH:
-                o << "      __syncthreads(); reduce_rows<T, NT>(stash, " << op.lslot << ", " << (int)op.row
-                  << ", acc, tid); __syncthreads();\n";
+                o << "      __syncthreads(); reduce_rows<T, NT>(" << buf_ptr() << ", " << op.lslot << ", " << (int)op.row
+                  << ", acc, tid);" << (dbuf ? "" : " __syncthreads();") << "\n";
+                if (dbuf) buf ^= 1;
                 break;
             default:
                 break;
@@ -251,7 +292,11 @@ std::string gen_rev(const Plan &pl, int pass) {
         o << "      rev_scatter<T, " << K << ", " << R << ">(g, " << (st.has_phase ? "true" : "false")
           << ", tphi, tlam, a, l, phase, kacc);\n"
           << "      __syncthreads();\n";
-        if (st.n_rows) o << "      reduce_stash<T, NT>(stash, pg.st[" << s << "], acc, tid); __syncthreads();\n";
+        if (st.n_rows) {
+            o << "      reduce_stash<T, NT>(" << buf_ptr() << ", pg.st[" << s << "], acc, tid);"
+              << (dbuf ? "" : " __syncthreads();") << "\n";
+            if (dbuf) buf ^= 1;
+        }
         o << "    }\n";
     }
     o << "    if (write_phi) IO::template store<NT>(tphi, phi_dst, base, row_off, tid);\n"
@@ -259,7 +304,13 @@ std::string gen_rev(const Plan &pl, int pass) {
       << "    __syncthreads();\n"
       << "  }\n};\n} }\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") vqg_spec_rev(" << kRevArgs
-      << ") {\n  vqg::rev_pass_spec<float, " << K << ", " << R << ", vqg::spec::Body>(" << kRevNames << ");\n}\n";
+      << ") {\n  using Caps = vqg::CapsT<" << geo.ops << ", " << geo.stages << ", " << geo.diags << ", " << geo.items
+      << ">;\n"
+      << "  // the launch passes this many bytes of dynamic shared memory (computed on the host)\n"
+      << "  static_assert(vqg::RevCfg<float, " << K << ", " << R << ", Caps, " << geo.rows << ">::smem() == " << geo.smem
+      << "ull, \"shared-memory size\");\n"
+      << "  vqg::rev_pass_spec<float, " << K << ", " << R << ", vqg::spec::Body, Caps, " << geo.rows << ">("
+      << kRevNames << ");\n}\n";
     return o.str();
 }
 
@@ -624,20 +675,22 @@ int spec_build(Plan *pl, bool with_rev) {
     std::vector<std::string> cubins;
     if (int st = spec_compile(pl, with_rev, cubins)) return st;
     const int np = (int)pl->passes.size();
-    const size_t fsm = fwd_smem(pl->K, pl->Rf), rsm = rev_smem(pl->K, pl->Rr);
+    const size_t fsm = fwd_smem(pl->K, pl->Rf);
+    pl->spec_smem_rev.clear();
     int dev = 0;
     cudaGetDevice(&dev);
     for (size_t i = 0; i < cubins.size(); ++i) {
         cudaKernel_t k = nullptr;
         const bool fwd = (int)i < np;
+        // each reverse kernel's program and stash are sized for its own pass
+        const size_t sm = fwd ? fsm : rev_spec_geo(*pl, (int)i - np).smem;
         if (int st = load_kernel(cubins[i], fwd ? "vqg_spec_fwd" : "vqg_spec_rev", &k)) return st;
-        cudaError_t e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)(fwd ? fsm : rsm), dev);
+        cudaError_t e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm, dev);
         if (e != cudaSuccess) return set_error(VQG_ERR_CUDA, "specialised kernel attribute: %s", cudaGetErrorString(e));
         (fwd ? pl->spec_fwd : pl->spec_rev).push_back((void *)k);
+        if (!fwd) pl->spec_smem_rev.push_back(sm);
     }
     pl->spec_smem_fwd = fsm;
-    pl->spec_smem_rev = rsm;
     return VQG_OK;
 }
 
@@ -675,7 +728,7 @@ int spec_launch_rev(const Plan *pl, int j, const void *phi_src, void *phi_dst, v
     int a13 = nb, a14 = wmask;
     void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10, &a11, &a12, &a13, &a14};
     return cudaLaunchKernel((const void *)pl->spec_rev[j], dim3(nb), dim3(1 << (pl->K - pl->Rr)), args,
-                            pl->spec_smem_rev, s) == cudaSuccess ? VQG_OK : VQG_ERR_CUDA;
+                            pl->spec_smem_rev[j], s) == cudaSuccess ? VQG_OK : VQG_ERR_CUDA;
 }
 
 }  // namespace vqg
