@@ -112,7 +112,8 @@ static void greedy(const std::vector<vqg_gate> &gates, const std::vector<int> &o
     }
 }
 
-// Tile layout of a pass: positions 0..L-1 are qubits 0..L-1, then `high` ascending.
+// Tile layout of a pass: positions 0..L-1 are qubits 0..L-1, then `high` in its order
+// (ascending, except where a Hamiltonian pass moves two qubits to its batch positions).
 struct TileMap {
     int K, L;
     std::vector<int> pos_of;   // qubit -> tile position or -1
@@ -761,6 +762,31 @@ bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
         for (int q = L; q < n && (int)high.size() < K - L; ++q)
             if (!((S >> q) & 1)) high.push_back(q), S |= 1ull << q;
         std::sort(high.begin(), high.end());
+        // complex64 batches of the Hamiltonian tile pass hold chunks that differ in tile
+        // positions L+5 and L+6 (HamGeo): flip masks equal outside those two qubits and qubit
+        // 0 share their partner loads, and one with no other bit needs none.  Put there the
+        // pair of high qubits that leaves the fewest distinct other parts.
+        if (L == 4 && (int)high.size() >= 7) {
+            auto loads = [&](int a, int b) {
+                const uint64_t m = 1ull | (1ull << a) | (1ull << b);
+                std::vector<uint64_t> ys;
+                for (int g : rem)
+                    if (chosen[g] && (ham[g].x & ~m)) ys.push_back(ham[g].x & ~m);
+                std::sort(ys.begin(), ys.end());
+                return (int)(std::unique(ys.begin(), ys.end()) - ys.begin());
+            };
+            int ba = high[5], bb = high[6], best = loads(ba, bb);
+            for (size_t i = 0; i < high.size(); ++i)
+                for (size_t j = i + 1; j < high.size(); ++j) {
+                    const int c = loads(high[i], high[j]);
+                    if (c < best) best = c, ba = high[i], bb = high[j];
+                }
+            std::vector<int> rest;
+            for (int q : high)
+                if (q != ba && q != bb) rest.push_back(q);
+            rest.insert(rest.begin() + 5, {ba, bb});
+            high.swap(rest);
+        }
         TileMap tm = make_tilemap(n, K, L, high);
         HPass hp;
         std::memset(&hp, 0, sizeof hp);

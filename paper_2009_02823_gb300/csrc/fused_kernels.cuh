@@ -1966,7 +1966,9 @@ VQG_DEV void fwd_diag_table(float2 (&a)[1 << R], const float2 *tab, uint32_t c) 
 // swizzle folds from higher index bits (b_i, per chunk at run time).  Slot j of own chunk i
 // (logical amplitude j ^ b_i) has its partner under a flip mask x at slot j ^ x0 of the chunk
 // at B_i ^ (swz(x) & ~1): the partners of both slots come with one 16-byte load and their
-// positions are literals.  b_i enters only the sign of terms whose class has bit 0 (b31[i] =
+// positions are literals (the generated body shares these loads between flip masks that
+// differ only in the batch's own bits, and takes the batch's own chunks, mine, where a mask
+// has no other bits).  b_i enters only the sign of terms whose class has bit 0 (b31[i] =
 // b_i << 31), and the logical order is restored once per batch when lambda is written.
 template <int K, bool L2ONLY, typename Body>
 VQG_DEV float ham_tile_spec(float2 *tile, const uint64_t *row_off, HamTab<float, K> &tb, uint64_t base, bool first,
@@ -2014,7 +2016,7 @@ VQG_DEV float ham_tile_spec(float2 *tile, const uint64_t *row_off, HamTab<float,
                 IO::unpack(L2ONLY ? __ldcg(g) : __ldcs(g), out + 2 * i);
             }
         }
-        Body::groups(tb, tile, t0, B, b31, delta);
+        Body::groups(tb, tile, t0, B, b31, mine, delta);
 #pragma unroll
         for (int k = 0; k < BA; ++k) run += mine[k].x * delta[k].x + mine[k].y * delta[k].y;
 #pragma unroll

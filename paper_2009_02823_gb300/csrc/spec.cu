@@ -463,26 +463,58 @@ std::string gen_ham(const Plan &pl, int h) {
       << "namespace vqg { namespace spec {\n"
       << "struct Body {\n"
       << "  static VQG_DEV void groups(HamTab<float, " << K << "> &tb, const float2 *tile, uint32_t t0, "
-      << "const uint32_t (&B)[" << BCH << "], const uint32_t (&b31)[" << BCH << "], float2 (&delta)[" << BA << "]) {\n"
-      << "    using A = float2; (void)b31;\n";
-    // the partner of slot j of chunk i: component pair j ^ x0 of the 16-byte load q<i>
-    auto partner = [](int i, int pos) {
-        return "make_float2(q" + std::to_string(i) + (pos ? ".z, q" : ".x, q") + std::to_string(i) + (pos ? ".w)" : ".y)");
-    };
-    for (int g = 0; g < P.n_group; ++g) {
+      << "const uint32_t (&B)[" << BCH << "], const uint32_t (&b31)[" << BCH << "], const float2 (&mine)[" << BA
+      << "], float2 (&delta)[" << BA << "]) {\n"
+      << "    using A = float2; (void)b31; (void)tile; (void)B;\n";
+    // A flip mask x splits into its bits at the batch's chunk positions (r: own chunk i
+    // finds its partners in chunk i ^ r of the same batch), bit 0 (the slot inside a chunk)
+    // and the rest y: the 16-byte loads q_k = tile[B[k] ^ (swz(y) & ~1)] depend on y alone,
+    // so groups with the same y share them, and y = 0 needs none (the batch's own chunks).
+    // The partner of slot j of chunk i is component j ^ (swz(x) & 1) of q_{i ^ r}.
+    const uint32_t cmask = 1u | ((uint32_t)(BCH - 1) << SH);
+    std::vector<int> order;  // the pass's groups, those with equal y adjacent
+    {
+        std::vector<uint32_t> ys;
+        for (int g = 0; g < P.n_group; ++g) {
+            const uint32_t y = pl.hg[P.group0 + g].xl & ~cmask;
+            if (std::find(ys.begin(), ys.end(), y) == ys.end()) ys.push_back(y);
+        }
+        for (uint32_t y : ys)
+            for (int g = 0; g < P.n_group; ++g)
+                if ((pl.hg[P.group0 + g].xl & ~cmask) == y) order.push_back(g);
+    }
+    bool open = false;
+    uint32_t cur_y = ~0u;
+    for (int g : order) {
         const HGroup &G = pl.hg[P.group0 + g];
         if (G.n_term == 0) continue;  // the diagonal group exists even without terms
+        const uint32_t y = G.xl & ~cmask, r = (G.xl >> SH) & (uint32_t)(BCH - 1);
+        const uint32_t xs0 = swz<8>(G.xl) & 1u;
+        if (y != cur_y) {
+            if (open) o << "    }\n";
+            o << "    {  // flip masks with y = " << hex(y) << "\n";
+            if (y)
+                for (int c = 0; c < BCH; ++c)
+                    o << "      const float4 q" << c << " = *reinterpret_cast<const float4 *>(tile + (B[" << c << "] ^ "
+                      << hex(swz<8>(y) & ~1u) << "));\n";
+            open = true;
+            cur_y = y;
+        }
+        // component pos of the partner chunk of own chunk i
+        auto partner = [&](int i, int pos) {
+            const int c = i ^ (int)r;
+            if (!y) return "mine[" + std::to_string(2 * c + pos) + "]";
+            const std::string q = "q" + std::to_string(c);
+            return "make_float2(" + q + (pos ? ".z, " : ".x, ") + q + (pos ? ".w)" : ".y)");
+        };
+        const uint32_t x0 = xs0;
         bool re = true, im = true;
         for (int t = 0; t < G.n_term; ++t) {
             re = re && pl.ht[G.term0 + t].wi == 0.0;
             im = im && pl.ht[G.term0 + t].wr == 0.0;
         }
         const int kind = re ? 0 : (im ? 1 : 2);
-        const uint32_t xs = swz<8>(G.xl), x0 = xs & 1u;
-        o << "    {  // group " << g << ": " << G.n_term << " term(s), kind " << kind << "\n";
-        for (int i = 0; i < BCH; ++i)
-            o << "      const float4 q" << i << " = *reinterpret_cast<const float4 *>(tile + (B[" << i << "] ^ "
-              << hex(xs & ~1u) << "));\n";
+        o << "      {  // group " << g << ": " << G.n_term << " term(s), kind " << kind << "\n";
         // the sign of slot j of chunk i for a term of class cls: parity((2i + j) & cls), a
         // literal, plus b_i where cls has bit 0
         auto neg = [](int i, int j, uint32_t cls) { return (__builtin_popcount((unsigned)(2 * i + j) & cls) & 1) != 0; };
@@ -547,8 +579,9 @@ std::string gen_ham(const Plan &pl, int h) {
                           << "]); }\n";
                 }
         }
-        o << "    }\n";
+        o << "      }\n";
     }
+    if (open) o << "    }\n";
     o << "  }\n};\n} }\n"
       << "extern \"C\" __global__ void __launch_bounds__(256, 2) vqg_spec_ham(const float2 *__restrict__ psi, "
          "float2 *__restrict__ lam, const vqg::HPass *__restrict__ hp, int pi, const vqg::HGroup *__restrict__ groups, "
