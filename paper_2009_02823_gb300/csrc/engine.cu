@@ -716,6 +716,69 @@ int Circuit::build_plan() {
 // qubits are always inside; each pass adds the groups whose high flip bits fit).
 // Returns false (nothing planned) when some group cannot live in one tile: its flip
 // mask has more high bits than the tile has, or it has more terms than a pass holds.
+// One greedy cover of the groups' high flip bits by tile high sets of at most K - L qubits:
+// each pass adds the group that needs the fewest new qubits (ties: the one whose union covers
+// most remaining groups), until none fits.  With rng, each pick is drawn from the (up to)
+// three best-covering of the fewest-new-qubit candidates.  Returns each pass's high set and
+// its groups (ascending).
+using HamCover = std::vector<std::pair<uint64_t, std::vector<int>>>;
+static HamCover cover_groups(const std::vector<HamGroup> &ham, int K, int L, uint64_t *rng) {
+    const uint64_t lowmask = (1ull << L) - 1ull;
+    auto high_of = [&](int g) { return ham[g].x & ~lowmask; };
+    std::vector<int> rem;
+    for (size_t g = 0; g < ham.size(); ++g) rem.push_back((int)g);
+    HamCover out;
+    while (!rem.empty()) {
+        uint64_t S = 0;
+        std::vector<char> chosen(ham.size(), 0);
+        while (true) {
+            std::vector<std::pair<int, int>> cands;  // (cov, group) of the fewest-new-qubit ones
+            int best_new = 1 << 30;
+            for (int g : rem) {
+                if (chosen[g]) continue;
+                const uint64_t h = high_of(g);
+                if (__builtin_popcountll(S | h) > K - L) continue;
+                const int nw = __builtin_popcountll(h & ~S);
+                if (nw > best_new) continue;
+                const uint64_t cand = S | h;
+                int cov = 0;
+                for (int g2 : rem) cov += ((high_of(g2) & ~cand) == 0);
+                if (nw < best_new) best_new = nw, cands.clear();
+                cands.push_back({cov, g});
+            }
+            if (cands.empty()) break;
+            // highest coverage first; among equal coverage the lowest group index
+            std::stable_sort(cands.begin(), cands.end(), [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+                return a.first > b.first;
+            });
+            size_t pick = 0;
+            if (rng) {
+                *rng = *rng * 6364136223846793005ull + 1442695040888963407ull;  // LCG step
+                pick = (size_t)((*rng >> 33) % std::min<size_t>(3, cands.size()));
+            }
+            const uint64_t S2 = S | high_of(cands[pick].second);
+            int ng = 0, nt = 0;
+            for (int g2 : rem)
+                if ((high_of(g2) & ~S2) == 0) ++ng, nt += ham[g2].count;
+            if (ng > kMaxHamGroups || nt > kMaxHamTerms) break;
+            S = S2;
+            for (int g2 : rem)
+                if ((high_of(g2) & ~S) == 0) chosen[g2] = 1;
+        }
+        std::vector<int> mine, next;
+        for (int g : rem) (chosen[g] ? mine : next).push_back(g);
+        out.push_back({S, mine});
+        rem.swap(next);
+    }
+    return out;
+}
+
+// Hamiltonian passes: greedy set cover of the groups' flip masks by tiles (the low L
+// qubits are always inside; each pass adds the groups whose high flip bits fit).  The
+// deterministic cover and a few randomised ones (fixed seed) are tried and the one with
+// the fewest passes is kept: every pass streams psi and lambda once, so passes are the cost.
+// Returns false (nothing planned) when some group cannot live in one tile: its flip
+// mask has more high bits than the tile has, or it has more terms than a pass holds.
 bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
                              const std::vector<PauliTerm> &host_terms) {
     pl->hp.clear();
@@ -725,36 +788,21 @@ bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
     const uint64_t lowmask = (1ull << L) - 1ull;
     for (const HamGroup &g : ham)
         if (__builtin_popcountll(g.x & ~lowmask) > K - L || g.count > kMaxHamTerms) return false;
-    std::vector<int> rem;
-    for (size_t g = 0; g < ham.size(); ++g) rem.push_back((int)g);
+    HamCover cover = cover_groups(ham, K, L, nullptr);
+    {
+        // restarts while the work (groups^2 per pick) stays small
+        const double work = (double)ham.size() * (double)ham.size() * (double)(K - L) * (double)cover.size();
+        const int restarts = work > 0 ? (int)std::min(32.0, 4e8 / work) : 0;
+        uint64_t rng = 0x9e3779b97f4a7c15ull;
+        for (int r = 0; r < restarts && cover.size() > 1; ++r) {
+            HamCover c = cover_groups(ham, K, L, &rng);
+            if (c.size() < cover.size()) cover.swap(c);
+        }
+    }
     // the diagonal group (x = 0) is group 0 (ordered map) and goes in the first pass
     bool first = true;
-    while (!rem.empty()) {
-        uint64_t S = 0;
-        std::vector<char> chosen(ham.size(), 0);
-        auto high_of = [&](int g) { return ham[g].x & ~lowmask; };
-        while (true) {
-            int best = -1, best_new = 1 << 30, best_cov = -1;
-            for (int g : rem) {
-                if (chosen[g]) continue;
-                const uint64_t h = high_of(g);
-                if (__builtin_popcountll(S | h) > K - L) continue;
-                const int nw = __builtin_popcountll(h & ~S);
-                const uint64_t cand = S | h;
-                int cov = 0;
-                for (int g2 : rem) cov += ((high_of(g2) & ~cand) == 0);
-                if (nw < best_new || (nw == best_new && cov > best_cov)) best = g, best_new = nw, best_cov = cov;
-            }
-            if (best < 0) break;
-            const uint64_t S2 = S | high_of(best);
-            int ng = 0, nt = 0;
-            for (int g2 : rem)
-                if ((high_of(g2) & ~S2) == 0) ++ng, nt += ham[g2].count;
-            if (ng > kMaxHamGroups || nt > kMaxHamTerms) break;
-            S = S2;
-            for (int g2 : rem)
-                if ((high_of(g2) & ~S) == 0) chosen[g2] = 1;
-        }
+    for (const auto &pass : cover) {
+        uint64_t S = pass.first;
         // fill the tile's high set: S's qubits, then the lowest others
         std::vector<int> high;
         for (int q = L; q < n; ++q)
@@ -770,8 +818,8 @@ bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
             auto loads = [&](int a, int b) {
                 const uint64_t m = 1ull | (1ull << a) | (1ull << b);
                 std::vector<uint64_t> ys;
-                for (int g : rem)
-                    if (chosen[g] && (ham[g].x & ~m)) ys.push_back(ham[g].x & ~m);
+                for (int g : pass.second)
+                    if (ham[g].x & ~m) ys.push_back(ham[g].x & ~m);
                 std::sort(ys.begin(), ys.end());
                 return (int)(std::unique(ys.begin(), ys.end()) - ys.begin());
             };
@@ -797,12 +845,7 @@ bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
         hp.group0 = (int)pl->hg.size();
         hp.first = first ? 1 : 0;
         hp.eslot = (int)pl->hp.size();
-        std::vector<int> next;
-        for (int g : rem) {
-            if (!chosen[g]) {
-                next.push_back(g);
-                continue;
-            }
+        for (int g : pass.second) {
             const HamGroup &G0 = ham[g];
             HGroup hg;
             std::memset(&hg, 0, sizeof hg);
@@ -834,7 +877,6 @@ bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
         }
         hp.n_group = (int)pl->hg.size() - hp.group0;
         pl->hp.push_back(hp);
-        rem.swap(next);
         first = false;
     }
     if (pl->hp.empty()) {  // no terms at all: one pass that writes lambda = 0
