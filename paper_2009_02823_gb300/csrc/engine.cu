@@ -10,6 +10,7 @@
 // that only swaps commuting gates, so U(theta) -- and with it E(theta) and every
 // gradient entry -- is unchanged.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -381,6 +382,9 @@ static void build_stages(Plan &pl, const std::vector<vqg_gate> &gates, const std
         st.n_op = (int)pl.ops.size() - st.op0;
         st.n_rows = (int16_t)rows;
         pl.stages.push_back(st);
+        std::array<int8_t, kMaxRegBits> rq{};
+        for (int k = 0; k < R; ++k) rq[k] = (int8_t)tm.qubit_of[regs[k]];
+        pl.stage_reg_q.push_back(rq);
         ++n_stage;
         uns.swap(left);
     }
@@ -641,6 +645,7 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
                 break;
             }
             pl->stages.resize(n_st);
+            pl->stage_reg_q.resize(n_st);
             pl->ops.resize(n_op);
             pl->diags.resize(n_dg);
             pl->items.resize(n_it);

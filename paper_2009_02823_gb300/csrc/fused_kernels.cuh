@@ -1873,6 +1873,71 @@ VQG_DEV void fwd_scatter(StageGeo<T, K, R> &g, bool has_phase, amp_t<T> *tile, c
     }
 }
 
+// First and last stage of a specialised pass: they read the state from HBM into registers
+// and write it back from registers, without the shared tile (one round trip through shared
+// memory less per tile and state).  Amplitude j of the thread is global index gb | gm[j],
+// gm[j] the global bits of the register bits set in j (literals of the generated code); the
+// arithmetic on the way out is rev_scatter's / fwd_scatter's.
+template <int R>
+VQG_DEV void rev_gather_global(uint64_t gb, const uint64_t (&gm)[1 << R], const float2 *__restrict__ phi,
+                               const float2 *__restrict__ lam, float2 (&a)[1 << R], float2 (&l)[1 << R]) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        a[j] = __ldcs(phi + (gb | gm[j]));
+        l[j] = __ldcs(lam + (gb | gm[j]));
+    }
+}
+template <int R>
+VQG_DEV void rev_scatter_global(uint64_t gb, const uint64_t (&gm)[1 << R], bool has_phase, float2 *__restrict__ phi,
+                                float2 *__restrict__ lam, bool write_phi, bool write_lam, const float2 (&a)[1 << R],
+                                const float2 (&l)[1 << R], float2 phase, float kacc) {
+    constexpr int NA = 1 << R;
+    asm volatile("" : "+l"(gb));  // form the addresses here instead of keeping them live
+    const bool scaled = scaled_stage<float>(kacc);
+    phase = make_float2(phase.x * kacc, phase.y * kacc);
+    const float2 pr = make_float2(phase.x, phase.x), pi2 = make_float2(-phase.y, phase.y), sv = make_float2(kacc, kacc);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        float2 va = a[j], vl = l[j];
+        if (has_phase) {
+            va = __ffma2_rn(pr, a[j], __fmul2_rn(pi2, make_float2(a[j].y, a[j].x)));
+            vl = __ffma2_rn(pr, l[j], __fmul2_rn(pi2, make_float2(l[j].y, l[j].x)));
+        } else if (scaled) {
+            va = __fmul2_rn(sv, a[j]);
+            vl = __fmul2_rn(sv, l[j]);
+        }
+        if (write_phi) __stcs(phi + (gb | gm[j]), va);
+        if (write_lam) __stcs(lam + (gb | gm[j]), vl);
+    }
+}
+template <int R>
+VQG_DEV void fwd_gather_global(uint64_t gb, const uint64_t (&gm)[1 << R], bool from_zero,
+                               const float2 *__restrict__ src, float2 (&a)[1 << R]) {
+    if (from_zero) {  // |0...0>
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) a[j] = make_float2((gb | gm[j]) == 0 ? 1.f : 0.f, 0.f);
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) a[j] = __ldcs(src + (gb | gm[j]));
+    }
+}
+template <int R>
+VQG_DEV void fwd_scatter_global(uint64_t gb, const uint64_t (&gm)[1 << R], bool has_phase, float2 *__restrict__ dst,
+                                const float2 (&a)[1 << R], float2 phase, float kacc) {
+    constexpr int NA = 1 << R;
+    asm volatile("" : "+l"(gb));  // form the addresses here instead of keeping them live
+    const bool scaled = scaled_stage<float>(kacc);
+    phase = make_float2(phase.x * kacc, phase.y * kacc);
+    const float2 sv = make_float2(kacc, kacc);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        float2 v = a[j];
+        if (has_phase) v = cmul<float>(phase, a[j]);
+        else if (scaled) v = __fmul2_rn(sv, a[j]);
+        __stcs(dst + (gb | gm[j]), v);
+    }
+}
+
 // Reverse diagonal block, split for the specialised kernels (rev_diag does both parts for
 // the interpreted pass, for any item list): rev_diag_sums forms the block's input sums
 // H[k] = sum over register index bit k = 0 of p_j and S = sum of all p_j, with

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <string>
+#include <array>
 #include <vector>
 
 #include "../../include/vqg.h"
@@ -18,6 +19,7 @@ struct Plan {
     int grid_fwd = 0;
     std::vector<FPass> passes;
     std::vector<FStage> stages;
+    std::vector<std::array<int8_t, kMaxRegBits>> stage_reg_q;  // host only: global qubit of each register bit
     std::vector<FOp> ops;
     std::vector<FDiag> diags;
     std::vector<FDItem> items;

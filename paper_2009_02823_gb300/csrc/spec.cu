@@ -63,6 +63,32 @@ std::string ctrl_expr(const FOp &op) {
 
 std::string prm(int o) { return "pg.prm + " + std::to_string(4 * o); }
 
+// A stage reads and writes HBM directly only when no register bit is one of the row qubits
+// 0..L-1: its lanes then run over those qubits (the thread bits take the lowest free tile
+// positions of each residue mod 4 first), so a warp's access for one register index covers
+// whole 128-byte rows.  Other stages go through the shared tile, whose loads and stores
+// are row-coalesced by construction.
+bool direct_io(const Plan &pl, int stage, int R) {
+    for (int k = 0; k < R; ++k)
+        if (pl.stage_reg_q[stage][k] < pl.L) return false;
+    return true;
+}
+
+// Global-index offsets of a stage's register indices: gm[j] has the global bit of every
+// register bit set in j (the first and last stage of a pass address HBM directly).
+std::string gm_decl(const Plan &pl, int stage, int R) {
+    std::ostringstream o;
+    o << "const uint64_t gm[" << (1 << R) << "] = {";
+    for (int j = 0; j < (1 << R); ++j) {
+        uint64_t m = 0;
+        for (int k = 0; k < R; ++k)
+            if ((j >> k) & 1) m |= 1ull << pl.stage_reg_q[stage][k];
+        o << (j ? ", " : "") << "0x" << std::hex << m << std::dec << "ull";
+    }
+    o << "};";
+    return o.str();
+}
+
 // Literal per-thread factor of diagonal block D (what diag_thread computes from the item
 // table at run time): tau from the RZ phases and CZ signs on thread-level qubits, folded
 // into the stage's pending phase, and the sign mask c of the register-thread CZs.
@@ -109,16 +135,23 @@ std::string gen_fwd(const Plan &pl, int pass) {
       << "> &pg, uint64_t base, bool from_zero, const float2 *__restrict__ src, float2 *__restrict__ dst, int tid) {\n"
       << "    using T = float; using A = float2; using IO = TileIO<T, " << K << ">;\n"
       << "    constexpr int NT = " << NT << ", NA = " << (1 << R) << "; (void)NA;\n"
-      << "    if (from_zero) IO::template zero<NT>(tile, base, tid);\n"
-      << "    else IO::template load<NT, false>(tile, src, base, row_off, tid);\n"
-      << "    __syncthreads();\n";
+      << "    (void)row_off; (void)IO{};\n";
+    const bool dfirst = P.n_stage > 0 && direct_io(pl, P.stage0, R);
+    const bool dlast = P.n_stage > 0 && direct_io(pl, P.stage0 + P.n_stage - 1, R);
+    if (!dfirst)
+        o << "    if (from_zero) IO::template zero<NT>(tile, base, tid);\n"
+          << "    else IO::template load<NT, false>(tile, src, base, row_off, tid);\n"
+          << "    __syncthreads();\n";
     for (int s = 0; s < P.n_stage; ++s) {
         const FStage &st = pl.stages[P.stage0 + s];
+        const bool first = s == 0 && dfirst, last = s == P.n_stage - 1 && dlast;
         o << "    {  // stage " << s << "\n"
           << "      StageGeo<T, " << K << ", " << R << "> g; g.init(pg.st[" << s << "], tid, base);\n"
-          << "      const uint64_t gb = g.gb; (void)gb;\n"
-          << "      A a[NA]; fwd_gather<T, " << K << ", " << R << ">(g, tile, a);\n"
-          << "      A phase = mk<T>((T)1, (T)0); T kacc = (T)1;\n";
+          << "      const uint64_t gb = g.gb; (void)gb;\n";
+        if (first || last) o << "      " << gm_decl(pl, P.stage0 + s, R) << "\n";
+        if (first) o << "      A a[NA]; fwd_gather_global<" << R << ">(gb, gm, from_zero, src, a);\n";
+        else o << "      A a[NA]; fwd_gather<T, " << K << ", " << R << ">(g, tile, a);\n";
+        o << "      A phase = mk<T>((T)1, (T)0); T kacc = (T)1;\n";
         for (int i = 0; i < st.n_op; ++i) {
             const int oi = st.op0 + i, ol = oi - op_base;
             const FOp &op = pl.ops[oi];
@@ -155,14 +188,19 @@ std::string gen_fwd(const Plan &pl, int pass) {
                 break;
             }
         }
-        o << "      fwd_scatter<T, " << K << ", " << R << ">(g, " << (st.has_phase ? "true" : "false")
-          << ", tile, a, phase, kacc);\n"
-          << "      __syncthreads();\n"
-          << "    }\n";
+        if (last)
+            o << "      fwd_scatter_global<" << R << ">(gb, gm, " << (st.has_phase ? "true" : "false")
+              << ", dst, a, phase, kacc);\n";
+        else
+            o << "      fwd_scatter<T, " << K << ", " << R << ">(g, " << (st.has_phase ? "true" : "false")
+              << ", tile, a, phase, kacc);\n"
+              << "      __syncthreads();\n";
+        o << "    }\n";
     }
-    o << "    IO::template store<NT>(tile, dst, base, row_off, tid);\n"
-      << "    __syncthreads();\n"
-      << "  }\n};\n} }\n"
+    if (!dlast) o << "    IO::template store<NT>(tile, dst, base, row_off, tid);\n";
+    // the next tile's first tile write must not overtake this tile's last tile reads
+    if (P.n_stage > 1 || !dfirst || !dlast) o << "    __syncthreads();\n";
+    o << "  }\n};\n} }\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << NT << ", " << (NT >= 512 ? 1 : 2) << ") vqg_spec_fwd(" << kFwdArgs
       << ") {\n  vqg::fwd_pass_spec<float, " << K << ", " << R << ", vqg::spec::Body>(" << kFwdNames << ");\n}\n";
     return o.str();
@@ -222,15 +260,22 @@ std::string gen_rev(const Plan &pl, int pass) {
          "float2 *__restrict__ lam, double *acc, float *stash, int tid, bool write_phi, bool write_lam) {\n"
       << "    using T = float; using A = float2; using IO = TileIO<T, " << K << ">;\n"
       << "    constexpr int NT = " << NT << ", NA = " << (1 << R) << "; (void)NA;\n"
-      << "    IO::template load2<NT, false>(tphi, phi_src, tlam, lam, base, row_off, tid);\n"
-      << "    __syncthreads();\n";
+      << "    (void)row_off; (void)IO{};\n";
+    const bool dfirst = P.n_rstage > 0 && direct_io(pl, P.rstage0, R);
+    const bool dlast = P.n_rstage > 0 && direct_io(pl, P.rstage0 + P.n_rstage - 1, R);
+    if (!dfirst)
+        o << "    IO::template load2<NT, false>(tphi, phi_src, tlam, lam, base, row_off, tid);\n"
+          << "    __syncthreads();\n";
     for (int s = 0; s < P.n_rstage; ++s) {
         const FStage &st = pl.stages[P.rstage0 + s];
+        const bool first = s == 0 && dfirst, last = s == P.n_rstage - 1 && dlast;
         o << "    {  // stage " << s << "\n"
           << "      StageGeo<T, " << K << ", " << R << "> g; g.init(pg.st[" << s << "], tid, base);\n"
-          << "      const uint64_t gb = g.gb; (void)gb;\n"
-          << "      A a[NA], l[NA]; rev_gather<T, " << K << ", " << R << ">(g, tphi, tlam, a, l);\n"
-          << "      A phase = mk<T>((T)1, (T)0); T kacc = (T)1, k2acc = (T)1;\n";
+          << "      const uint64_t gb = g.gb; (void)gb;\n";
+        if (first || last) o << "      " << gm_decl(pl, P.rstage0 + s, R) << "\n";
+        if (first) o << "      A a[NA], l[NA]; rev_gather_global<" << R << ">(gb, gm, phi_src, lam, a, l);\n";
+        else o << "      A a[NA], l[NA]; rev_gather<T, " << K << ", " << R << ">(g, tphi, tlam, a, l);\n";
+        o << "      A phase = mk<T>((T)1, (T)0); T kacc = (T)1, k2acc = (T)1;\n";
         for (int i = 0; i < st.n_op; ++i) {
             const int oi = st.op0 + i, ol = oi - op_base;
             const FOp &op = pl.ops[oi];
@@ -289,9 +334,14 @@ std::string gen_rev(const Plan &pl, int pass) {
                 break;
             }
         }
-        o << "      rev_scatter<T, " << K << ", " << R << ">(g, " << (st.has_phase ? "true" : "false")
-          << ", tphi, tlam, a, l, phase, kacc);\n"
-          << "      __syncthreads();\n";
+        if (last)  // straight to HBM; the stash rows still need every thread's values
+            o << "      rev_scatter_global<" << R << ">(gb, gm, " << (st.has_phase ? "true" : "false")
+              << ", phi_dst, lam, write_phi, write_lam, a, l, phase, kacc);\n"
+              << (st.n_rows ? "      __syncthreads();\n" : "");
+        else
+            o << "      rev_scatter<T, " << K << ", " << R << ">(g, " << (st.has_phase ? "true" : "false")
+              << ", tphi, tlam, a, l, phase, kacc);\n"
+              << "      __syncthreads();\n";
         if (st.n_rows) {
             o << "      reduce_stash<T, NT>(" << buf_ptr() << ", pg.st[" << s << "], acc, tid);"
               << (dbuf ? "" : " __syncthreads();") << "\n";
@@ -299,9 +349,12 @@ std::string gen_rev(const Plan &pl, int pass) {
         }
         o << "    }\n";
     }
-    o << "    if (write_phi) IO::template store<NT>(tphi, phi_dst, base, row_off, tid);\n"
-      << "    if (write_lam) IO::template store<NT>(tlam, lam, base, row_off, tid);\n"
-      << "    __syncthreads();\n"
+    if (!dlast)
+        o << "    if (write_phi) IO::template store<NT>(tphi, phi_dst, base, row_off, tid);\n"
+          << "    if (write_lam) IO::template store<NT>(tlam, lam, base, row_off, tid);\n";
+    // the next tile's first tile writes and stash rows must not overtake this tile's last
+    // tile reads and reductions
+    o << "    __syncthreads();\n"
       << "  }\n};\n} }\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") vqg_spec_rev(" << kRevArgs
       << ") {\n  using Caps = vqg::CapsT<" << geo.ops << ", " << geo.stages << ", " << geo.diags << ", " << geo.items
