@@ -98,3 +98,35 @@ def test_specialized_hamiltonian_edge_cases():
     ex_ref, gx_ref = oracle.gradient_alg1_operator(n, gates, theta, P, cterms)
     assert abs(ex - ex_ref) <= TOL["c64"] * max(1.0, abs(ex_ref))
     assert np.max(np.abs(gx - gx_ref)) <= TOL["c64"] * max(1e-300, np.max(np.abs(gx_ref)))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,layers", [(16, 4), (17, 3)])
+def test_specialized_13_qubit_tiles(n, layers):
+    """The bench recipe with 13-qubit tiles at sizes the oracle finishes quickly: several
+    passes, Hamiltonian passes with shared partner loads and planner-chosen batch qubits, and
+    first / last stages that read and write HBM directly next to ones that use the tile."""
+    import oracle
+    w = W.config(3, n=n, layers=layers)
+    e_ref, g_ref = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
+    with B.Circuit(w.n, w.gates, w.n_params, "c64", tile_qubits=13, specialize=2) as c:
+        c.set_hamiltonian(w.terms)
+        plan = c.plan()
+        assert plan["tile_qubits"] == 13 and plan["specialized"] == 2
+        e, g = c.energy_and_gradient(w.theta)
+        assert_parity("c64", e, g, e_ref, g_ref, w.name)
+        assert np.max(np.abs(c.get_state() - oracle.state(w.n, w.gates, w.theta))) <= 2e-5
+
+
+@pytest.mark.gpu
+def test_hamiltonian_plan_is_reproducible():
+    """The Hamiltonian cover's randomised restarts use a fixed seed: two circuits planned
+    from the same input get the same passes and bit-identical results."""
+    w = W.config(3, n=20, layers=3)
+    out = []
+    for _ in range(2):
+        with B.Circuit(w.n, w.gates, w.n_params, "c64", specialize=1) as c:
+            c.set_hamiltonian(w.terms)
+            out.append((c.plan()["hamiltonian_passes"],) + c.energy_and_gradient(w.theta))
+    assert out[0][0] == out[1][0]
+    assert out[0][1] == out[1][1] and np.array_equal(out[0][2], out[1][2])
