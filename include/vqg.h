@@ -237,6 +237,34 @@ typedef struct vqg_plan_info {
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 
+/* One fused tile pass of the schedule (forward order; vqg_plan's forward_passes of them):
+ * the gates it applies and how many of the state's tiles it computes.  A sweep that starts
+ * from |0...0> (Sec. 2.2's U(theta)|0>) leaves a tile at zero until some gate acts
+ * non-diagonally on a qubit outside the tile on which the tile's index has a set bit: the
+ * forward pass writes zeros to those tiles and the reverse pass skips them (phi is zero
+ * there, so they add nothing to any gradient sum, and no earlier pass reads their lambda).
+ * The results are those of computing every tile.  With an input state
+ * (vqg_set_input_state), or while diagnostics are on (reverse passes), every tile is
+ * computed. */
+typedef struct vqg_pass_info {
+    int32_t n_gates;         /* gates applied by the pass */
+    int32_t forward_stages;  /* register stages of its forward pass */
+    int32_t reverse_stages;  /* register stages of its reverse pass */
+    int32_t from_zero;       /* 1: the pass synthesises |0...0> instead of reading a state */
+    uint64_t tiles;          /* tiles of 2^tile_qubits amplitudes in the state */
+    uint64_t active_tiles;   /* tiles the pass computes (the rest hold zeros) */
+    uint64_t tile_mask;      /* bit q set: qubit q lies inside the pass's tiles */
+    int32_t reserved[2];
+} vqg_pass_info;
+
+/* Fill *info for pass `pass` (0-based) and, when gates is not NULL, its first
+ * min(max_gates, n_gates) gate indices (positions in the list given to
+ * vqg_circuit_create) in the order the pass applies them.  Returns VQG_OK.  Errors:
+ * VQG_ERR_INVALID for a NULL circuit or info, a negative max_gates, or a pass outside
+ * 0..forward_passes-1; VQG_ERR_STATE when the circuit has no fused schedule (one kernel
+ * per gate). */
+int vqg_plan_pass(vqg_circuit *c, int pass, vqg_pass_info *info, int max_gates, int32_t *gates);
+
 /* Precision diagnostics (complex64 amplitudes with FP64 reductions and forward
  * checkpoints; the invariants of Algorithm 1's recurrence, Sec. 2.3: phi and lambda are
  * un-applied by the same unitaries, so <lambda_i|phi_{i+1}> = E and ||lambda_i|| is

@@ -74,6 +74,13 @@ class vqg_plan_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 
+class vqg_pass_info(ctypes.Structure):
+    _fields_ = [("n_gates", ctypes.c_int32), ("forward_stages", ctypes.c_int32),
+                ("reverse_stages", ctypes.c_int32), ("from_zero", ctypes.c_int32),
+                ("tiles", ctypes.c_uint64), ("active_tiles", ctypes.c_uint64),
+                ("tile_mask", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 2)]
+
+
 class vqg_tune_result(ctypes.Structure):
     _fields_ = [("tile_qubits", ctypes.c_int32), ("fwd_reg_qubits", ctypes.c_int32),
                 ("rev_reg_qubits", ctypes.c_int32), ("candidates", ctypes.c_int32),
@@ -120,6 +127,7 @@ def lib():
             "vqg_kernel_stats": (i, [p, i, p, p, p]),
             "vqg_kernel_family_name": (ctypes.c_char_p, [i]),
             "vqg_plan": (i, [p, p]),
+            "vqg_plan_pass": (i, [p, i, p, i, p]),
             "vqg_autotune": (i, [p, p, p]),
             "vqg_set_operator": (i, [p, i, p, p, p, p]),
             "vqg_set_product_operator": (i, [p, i, p, p]),
@@ -420,6 +428,22 @@ class Circuit:
         _check(lib().vqg_plan(self._h, ctypes.byref(info)))
         return {k: getattr(info, k) for k, _t in vqg_plan_info._fields_
                 if k not in ("reserved", "forward_stages", "reverse_stages", "stage_ops", "diag_blocks")}
+
+    def plan_passes(self) -> list:
+        """The fused passes of the schedule (vqg_plan_pass): per pass its gate indices, stage
+        counts, and how many of the state's tiles it computes (tiles that a |0...0> start
+        leaves at zero are skipped)."""
+        out = []
+        for j in range(self.plan()["forward_passes"] if self.plan()["tile_qubits"] else 0):
+            info = vqg_pass_info()
+            _check(lib().vqg_plan_pass(self._h, j, ctypes.byref(info), 0, None))
+            gates = (ctypes.c_int32 * max(info.n_gates, 1))()
+            _check(lib().vqg_plan_pass(self._h, j, ctypes.byref(info), info.n_gates, gates))
+            out.append({"gates": list(gates[:info.n_gates]), "forward_stages": info.forward_stages,
+                        "reverse_stages": info.reverse_stages, "from_zero": info.from_zero,
+                        "tiles": info.tiles, "active_tiles": info.active_tiles,
+                        "tile_qubits": [q for q in range(self.n) if (info.tile_mask >> q) & 1]})
+        return out
 
     def set_diagnostics(self, enable: bool = True):
         """Record FP64 norms and inner products along later gradient calls (vqg_set_diagnostics)."""

@@ -425,6 +425,8 @@ std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl) {
         if (p.n_stage < 1 || p.n_stage > pl.caps.stages || p.n_rstage < 1 || p.n_rstage > pl.caps.stages)
             return fail("stage count", p.n_stage, p.n_rstage);
         if (p.n_lslots < 0 || p.n_lslots > kMaxPassSlots) return fail("slot count", (int)j, p.n_lslots);
+        if (p.n_active < 0 || p.n_active > p.n_nontile || p.n_active_zero < 0 || p.n_active_zero > p.n_nontile)
+            return fail("active non-tile qubits", (int)j, p.n_active);
         if (p.slotmap0 < 0 || p.slotmap0 + p.n_lslots > (int)pl.slot_map.size()) return fail("slot map", (int)j, p.slotmap0);
         for (int i = 0; i < p.n_lslots; ++i)
             if (pl.slot_map[p.slotmap0 + i] < 0 || pl.slot_map[p.slotmap0 + i] >= n_gslots)
@@ -608,6 +610,7 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
     const int L = pl->L;
     std::vector<int> rem(G), applied, left;
     for (int i = 0; i < G; ++i) rem[i] = i;
+    uint64_t support = 0;  // qubits on which a |0...0> start may have a set bit before the pass
     while (!rem.empty()) {
         std::vector<int> high = choose_high(gates, rem, n, K, L);
         TileMap tm = make_tilemap(n, K, L, high);
@@ -622,8 +625,12 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
             std::memset(&p, 0, sizeof p);
             p.n_high = (int)high.size();
             for (size_t i = 0; i < high.size(); ++i) p.high[i] = high[i];
+            // non-tile qubits that may carry a set bit come first (see FPass::n_active)
             for (int q = 0; q < n; ++q)
-                if (tm.pos_of[q] < 0) p.nontile[p.n_nontile++] = q;
+                if (tm.pos_of[q] < 0 && ((support >> q) & 1)) p.nontile[p.n_nontile++] = q;
+            p.n_active_zero = p.n_active = p.n_nontile;
+            for (int q = 0; q < n; ++q)
+                if (tm.pos_of[q] < 0 && !((support >> q) & 1)) p.nontile[p.n_nontile++] = q;
             p.from_zero = pl->passes.empty() ? 1 : 0;
             p.n_gates = (int)applied.size();
             int nls;
@@ -642,6 +649,14 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
                               items_of(p.rdiag0, p.n_rdiag) <= caps.items;
             if (fits || cap == 1) {
                 pl->passes.push_back(p);
+                pl->pass_gates.emplace_back(applied.begin(), applied.end());
+                // amplitude can only move onto qubits that a gate acts on non-diagonally
+                for (int i : applied) {
+                    QUse u[2];
+                    const int nu = uses_of(gates[i], u);
+                    for (int k = 0; k < nu; ++k)
+                        if (!u[k].diag) support |= 1ull << u[k].q;
+                }
                 break;
             }
             pl->stages.resize(n_st);
@@ -704,7 +719,10 @@ int Circuit::build_plan() {
             return VQG_OK;  // no fused schedule for this size: one kernel per gate
         }
         pl->grid_fwd = occupancy_grid(num_sms, 2, pl->n_tiles);
-        if (has_input) pl->passes[0].from_zero = 0;  // pass 0 reads the input state
+        if (has_input) {  // pass 0 reads the input state; any tile may be non-zero
+            pl->passes[0].from_zero = 0;
+            for (FPass &p : pl->passes) p.n_active = p.n_nontile;
+        }
         plan = pl;
         int st;
         if ((st = upload_plan(pl))) return st;
@@ -1024,12 +1042,15 @@ int Circuit::issue_reverse_fused() {
         const bool write_phi = j > 0 && (pl->ckpt_of_pass[j - 1] < 0 || diag_active), write_lam = j > 0;
         prof_begin(FAM_ADJ_FUSED);
         const int wmask = (write_phi ? 1 : 0) | (write_lam ? 2 : 0);
+        // only the tiles that can hold amplitude (FPass::n_active); all of them when
+        // diagnostics follow lambda's norm through the sweep
+        const uint64_t n_tiles = diag_active ? pl->n_tiles : std::min<uint64_t>(pl->n_tiles, 1ull << pl->passes[j].n_active);
         if (j < (int)pl->spec_rev.size()) {
-            spec_launch_rev(pl, j, src, psi, lam, mats, gpart, nb, wmask, stream);
+            spec_launch_rev(pl, j, src, psi, lam, mats, gpart, nb, wmask, n_tiles, stream);
         } else {
             auto rev = !dbl ? launch_fused_rev_c64 : float_float(dbl, opt) ? launch_fused_rev_df : launch_fused_rev_c128;
             if (!rev(pl->K, pl->Rr, src, psi, lam, pl->d_passes, j, pl->d_stages, pl->d_ops, pl->d_diags,
-                     pl->d_items, pl->d_slot_map, mats, pl->n_tiles, gpart, nb, wmask, stream))
+                     pl->d_items, pl->d_slot_map, mats, n_tiles, gpart, nb, wmask, stream))
                 return set_error(VQG_ERR_UNSUPPORTED, "no reverse kernel for K=%d Rr=%d", pl->K, pl->Rr);
         }
         prof_end();
@@ -1097,6 +1118,31 @@ int group_pauli_terms(int n, int n_terms, const uint64_t *x_mask, const uint64_t
 }
 
 }  // namespace vqg
+
+// One fused pass of the schedule: gates, stages and computed tiles (include/vqg.h).
+extern "C" int vqg_plan_pass(vqg_circuit *c, int pass, vqg_pass_info *info, int max_gates, int32_t *gates) {
+    if (!c) return vqg::set_error(VQG_ERR_INVALID, "circuit is NULL");
+    const vqg::Circuit *cc = reinterpret_cast<const vqg::Circuit *>(c);
+    if (!info || max_gates < 0) return vqg::set_error(VQG_ERR_INVALID, "info is NULL or max_gates < 0");
+    const vqg::Plan *pl = cc->plan;
+    if (!pl || !cc->plan_ok) return vqg::set_error(VQG_ERR_STATE, "the circuit has no fused schedule");
+    if (pass < 0 || pass >= (int)pl->passes.size())
+        return vqg::set_error(VQG_ERR_INVALID, "pass %d outside 0..%d", pass, (int)pl->passes.size() - 1);
+    const vqg::FPass &P = pl->passes[pass];
+    std::memset(info, 0, sizeof *info);
+    info->n_gates = P.n_gates;
+    info->forward_stages = P.n_stage;
+    info->reverse_stages = P.n_rstage;
+    info->from_zero = P.from_zero;
+    info->tiles = pl->n_tiles;
+    info->active_tiles = std::min<uint64_t>(pl->n_tiles, 1ull << P.n_active);
+    info->tile_mask = (1ull << pl->L) - 1ull;
+    for (int i = 0; i < P.n_high; ++i) info->tile_mask |= 1ull << P.high[i];
+    const std::vector<int32_t> &g = pl->pass_gates[pass];
+    if (gates)
+        for (int i = 0; i < std::min(max_gates, (int)g.size()); ++i) gates[i] = g[i];
+    return VQG_OK;
+}
 
 // Host-only planning of a circuit and Hamiltonian: the same schedule a vqg_circuit
 // would use, validated, without touching a GPU.

@@ -77,7 +77,8 @@ enum FDItemType : int16_t {
 
 struct FPass {
     int32_t high[kMaxHigh];        // global qubit at tile position L + i
-    int32_t nontile[kMaxNontile];  // global qubits outside the tile, ascending
+    int32_t nontile[kMaxNontile];  // global qubits outside the tile: the n_active that may hold
+                                   // set bits first, then the rest (each part ascending)
     int32_t n_high, n_nontile;
     int32_t stage0, n_stage;       // forward stages
     int32_t rstage0, n_rstage;     // reverse stages
@@ -87,6 +88,13 @@ struct FPass {
     int32_t n_gates;               // gates applied by this pass
     int32_t diag0, n_diag;         // forward diagonal blocks
     int32_t rdiag0, n_rdiag;       // reverse diagonal blocks
+    // Tiles whose index has a bit set at or above n_active hold only zero amplitudes: the
+    // sweep starts from |0...0> and no gate before this pass moved amplitude onto those
+    // non-tile qubits.  The forward pass writes zeros there without computing; the reverse
+    // pass skips them (phi is zero there, so they add nothing to any gradient, and the
+    // earlier passes never read their lambda).  n_active = n_nontile: every tile computed.
+    int32_t n_active;
+    int32_t n_active_zero;         // host: n_active for a |0...0> start (an input state: all)
 };
 
 struct FStage {

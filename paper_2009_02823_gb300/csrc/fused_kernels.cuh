@@ -862,6 +862,16 @@ struct TileIO {
 #pragma unroll
         for (int i = 0; i < G::CPT; ++i) __stcs(reinterpret_cast<float4 *>(g0 + row_off[G::RSTEP * i]), v[i]);
     }
+    // Zeros at a tile's positions in global memory (a tile that holds no amplitude).
+    template <int NT>
+    static VQG_DEV void store_zero(amp_t<T> *__restrict__ dst, uint64_t base, const uint64_t *row_off, int tid) {
+        using G = Geo<NT>;
+        const int row0 = tid / CPR, col = tid % CPR;
+        amp_t<T> *g0 = dst + ((base | row_off[row0]) + col * CA);
+#pragma unroll
+        for (int i = 0; i < G::CPT; ++i)
+            __stcs(reinterpret_cast<float4 *>(g0 + row_off[G::RSTEP * i]), make_float4(0.f, 0.f, 0.f, 0.f));
+    }
 };
 
 VQG_DEV uint64_t tile_base(uint64_t tile, const int32_t *nontile, int n_nontile) {
@@ -1298,8 +1308,13 @@ __global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
     load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, stages, ops, diags, items, mats, false, tid, NT);
     __syncthreads();
+    const uint64_t n_act = 1ull << P.n_active;  // later tiles hold zeros only (FPass::n_active)
     for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        if (ti + gridDim.x < n_tiles && !P.from_zero)
+        if (ti >= n_act) {
+            TileIO<T, K>::template store_zero<NT>(dst, tile_base(ti, P.nontile, P.n_nontile), row_off, tid);
+            continue;
+        }
+        if (ti + gridDim.x < n_act && !P.from_zero)
             TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid);
         fwd_tile<T, K, R, false>(tile, row_off, pg, P.n_stage, tile_base(ti, P.nontile, P.n_nontile),
                                  P.from_zero != 0, src, dst, tid);
@@ -1802,8 +1817,13 @@ VQG_DEV void fwd_pass_spec(const amp_t<T> *__restrict__ src, amp_t<T> *__restric
     fill_row_offsets<T, K>(P.high, row_off, tid, NT);
     load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, stages, ops, diags, items, mats, false, tid, NT);
     __syncthreads();
+    const uint64_t n_act = 1ull << P.n_active;  // later tiles hold zeros only (FPass::n_active)
     for (uint64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        if (ti + gridDim.x < n_tiles && !P.from_zero)
+        if (ti >= n_act) {
+            TileIO<T, K>::template store_zero<NT>(dst, tile_base(ti, P.nontile, P.n_nontile), row_off, tid);
+            continue;
+        }
+        if (ti + gridDim.x < n_act && !P.from_zero)
             TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid);
         Body::tile(tile, row_off, pg, tile_base(ti, P.nontile, P.n_nontile), P.from_zero != 0, src, dst, tid);
     }

@@ -19,6 +19,7 @@ struct Plan {
     int grid_fwd = 0;
     std::vector<FPass> passes;
     std::vector<FStage> stages;
+    std::vector<std::vector<int32_t>> pass_gates;  // host only: gate indices of each pass, applied order
     std::vector<std::array<int8_t, kMaxRegBits>> stage_reg_q;  // host only: global qubit of each register bit
     std::vector<FOp> ops;
     std::vector<FDiag> diags;
@@ -73,6 +74,6 @@ int spec_build_ham(Plan *pl);
 int spec_launch_ham(const Plan *pl, int h, const void *psi, void *lam, double *partials, int nb, cudaStream_t s);
 int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const void *mats, cudaStream_t s);
 int spec_launch_rev(const Plan *pl, int j, const void *phi_src, void *phi_dst, void *lam, const void *mats,
-                    double *partials, int nb, int wmask, cudaStream_t s);
+                    double *partials, int nb, int wmask, uint64_t n_tiles, cudaStream_t s);
 
 }  // namespace vqg

@@ -797,7 +797,7 @@ int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const voi
 }
 
 int spec_launch_rev(const Plan *pl, int j, const void *phi_src, void *phi_dst, void *lam, const void *mats,
-                    double *partials, int nb, int wmask, cudaStream_t s) {
+                    double *partials, int nb, int wmask, uint64_t n_tiles, cudaStream_t s) {
     const float2 *a0 = (const float2 *)phi_src;
     float2 *a1 = (float2 *)phi_dst;
     float2 *a2 = (float2 *)lam;
@@ -809,7 +809,7 @@ int spec_launch_rev(const Plan *pl, int j, const void *phi_src, void *phi_dst, v
     const FDItem *a8 = pl->d_items;
     const int *a9 = pl->d_slot_map;
     const float *a10 = (const float *)mats;
-    uint64_t a11 = pl->n_tiles;
+    uint64_t a11 = n_tiles;
     double *a12 = partials;
     int a13 = nb, a14 = wmask;
     void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10, &a11, &a12, &a13, &a14};
