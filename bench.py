@@ -135,14 +135,22 @@ FWD_OPS = {"RY": 4, "RX": 8, "U3": 8, "RZ": 4, "CZ": 0, "CNOT": 0}
 REV_OPS = {"RY": 10, "RX": 18, "U3": 24, "RZ": 9, "CZ": 0, "CNOT": 0}
 
 
-def family_alu_ops(fam: str, w) -> float | None:
+def family_alu_ops(fam: str, w, passes=None) -> float | None:
     """Useful FP32 operations of one whole sweep of a kernel family (all its launches in
-    one gradient): per-amplitude counts x 2^n."""
+    one gradient): per-amplitude counts x the amplitudes each gate's pass computes (2^n, or
+    fewer where a fused pass skips tiles that a |0...0> start leaves at zero; passes: the
+    schedule's vqg_plan_pass entries)."""
     amps = float(1 << w.n)
+
+    def swept(table):
+        if not passes:
+            return amps * sum(table.get(g[0], 0) for g in w.gates)  # kinds not listed count 0
+        return sum(amps * p["active_tiles"] / p["tiles"] * sum(table.get(w.gates[i][0], 0) for i in p["gates"])
+                   for p in passes)
     if fam in ("fwd_fused", "fwd_gate"):
-        return amps * sum(FWD_OPS.get(g[0], 0) for g in w.gates)  # kinds not listed count 0
+        return swept(FWD_OPS)
     if fam in ("adj_fused", "adj_gate"):
-        return amps * sum(REV_OPS.get(g[0], 0) for g in w.gates)
+        return swept(REV_OPS)
     if fam in ("ham_fused", "ham_group", "ham_diag"):
         groups = len({tuple(sorted(q for q, l in ops if l in "XY")) for _c, ops in w.terms})
         return amps * (2 * len(w.terms) + 8 * groups)  # sign-weighted sums; complex MAC + energy
@@ -156,9 +164,11 @@ def alu_peak(sm_mhz: float | None, n_sm: int = 152) -> tuple[float, str]:
     return n_sm * 128 * mhz * 1e6 / 1e9, f"{n_sm} SM x 128 FP32 lanes x {mhz:.0f} MHz (sampled)"
 
 
-def family_bytes(fam: str, w, S: int, plan: dict) -> float | None:
+def family_bytes(fam: str, w, S: int, plan: dict, passes=None) -> float | None:
     """Algorithmic bytes per launch of a kernel family (one state traversal = S bytes
-    read or written; Algorithm 1's cost unit, one gate primitive = O(2^n))."""
+    read or written; Algorithm 1's cost unit, one gate primitive = O(2^n)).  Fused passes
+    count the tiles they compute (passes: vqg_plan_pass entries); a forward pass also writes
+    the zeros of the tiles it skips."""
     if fam == "adj_gate":    # read phi, lambda; write phi, lambda
         return 4.0 * S
     if fam == "fwd_gate":    # read + write psi (CNOT/CZ touch part of it; counted whole)
@@ -167,9 +177,17 @@ def family_bytes(fam: str, w, S: int, plan: dict) -> float | None:
         # per reverse tile pass: read phi and lambda; write lambda except after the last
         # pass; write phi only when the next pass does not restart from a checkpoint
         P, C = plan.get("reverse_passes", 1), plan.get("checkpoints", 0)
-        return (2.0 * P + (P - 1) + max(P - 1 - C, 0)) * S / max(P, 1)
+        if not passes:
+            return (2.0 * P + (P - 1) + max(P - 1 - C, 0)) * S / max(P, 1)
+        w_phi = max(P - 1 - C, 0) / max(P - 1, 1)  # share of passes that write phi
+        tot = 0.0
+        for j, p in enumerate(passes):
+            tot += p["active_tiles"] / p["tiles"] * S * (2.0 + ((1.0 + w_phi) if j > 0 else 0.0))
+        return tot / len(passes)
     if fam == "fwd_fused":   # per forward tile pass: read + write psi
-        return 2.0 * S
+        if not passes:
+            return 2.0 * S
+        return sum((0.0 if p["from_zero"] else p["active_tiles"] / p["tiles"]) * S + S for p in passes) / len(passes)
     if fam == "ham_group":   # read psi, read + write lambda
         return 3.0 * S
     if fam == "ham_diag":    # read psi, write lambda
@@ -247,6 +265,7 @@ def run_ours(args, rank, world, dist):
 
     # roofline of the dominant kernel family (per-launch CUDA events inside the timed region)
     plan = circ.plan()
+    passes = circ.plan_passes() if plan.get("tile_qubits") else None
     peak, peak_kind = _peaks()
     fam, (launches, tot_ms) = max(stats.items(), key=lambda kv: kv[1][1])
     roof = None
@@ -255,8 +274,8 @@ def run_ours(args, rank, world, dist):
     for f, (nl, ms) in stats.items():
         if not nl or ms <= 0:
             continue
-        per = family_bytes(f, w, S, plan)
-        ops = family_alu_ops(f, w)
+        per = family_bytes(f, w, S, plan, passes)
+        ops = family_alu_ops(f, w, passes)
         ent = {"launches": nl, "ms": round(ms, 3), "share": round(ms / total_ms, 4)}
         if per is not None:
             ent["hbm_gbs"] = round(per / (ms / nl / 1e3) / 1e9, 1)
@@ -268,10 +287,10 @@ def run_ours(args, rank, world, dist):
         per_family[f] = ent
     if launches:
         avg_s = tot_ms / launches / 1e3
-        per = family_bytes(fam, w, S, plan)
+        per = family_bytes(fam, w, S, plan, passes)
         hbm = per / avg_s / 1e9 if per else None
         fused = fam.endswith("_fused")
-        ops = family_alu_ops(fam, w)
+        ops = family_alu_ops(fam, w, passes)
         if fused and ops:
             apk, apk_src = alu_peak(clk.get("sm_mhz"), n_sm)
             ach = ops * args.steps / (tot_ms / 1e3) / 1e9
@@ -291,8 +310,13 @@ def run_ours(args, rank, world, dist):
     if roof is not None:
         per_amp = NCU_TRAFFIC_PER_AMP_C64.get(fam) if args.dtype == "c64" else None
         if per_amp is not None:
-            roof["traffic"] = round(per_amp * (1 << w.n))
-            roof["traffic_source"] = "ncu dram__bytes_read+write per launch at n=26, scaled by 2^(n-26)"
+            # the capture is of a pass that computes every tile; a launch moves that many
+            # bytes per computed tile, so the average launch scales by the active share
+            act = (sum(p["active_tiles"] / p["tiles"] for p in passes) / len(passes)
+                   if passes and fam in ("adj_fused",) else 1.0)
+            roof["traffic"] = round(per_amp * (1 << w.n) * act)
+            roof["traffic_source"] = ("ncu dram__bytes_read+write per launch at n=26, scaled by 2^(n-26)"
+                                      + (" x the mean share of computed tiles (%.4f)" % act if act < 1 else ""))
     gpu_launches = int(sum(v[0] for v in stats.values()))
 
     extra = {}
@@ -324,19 +348,22 @@ def run_ours(args, rank, world, dist):
             "config": _config(args, w, {"plan": plan, "specialize": spec, "setup_s": round(t_make, 2)}),
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
             "kernel_families": per_family, "energy": e_val,
-            "amplitude_updates": amplitude_updates(w, S, value, peak)}
+            "amplitude_updates": amplitude_updates(w, S, value, peak, passes)}
     if cpu:
         line["cpu_baseline"] = cpu
     line.update(extra)
     return line
 
 
-def amplitude_updates(w, S, grads_per_s, hbm_peak):
+def amplitude_updates(w, S, grads_per_s, hbm_peak, passes=None):
     """Amplitude updates per second, (G + 2G) 2^n per gradient (G gate applications forward,
-    two states un-applied per gate in reverse), against the rate the HBM roofline allows a
-    one-gate-per-pass schedule (each update reads and writes one amplitude)."""
+    two states un-applied per gate in reverse; a fused pass that skips tiles a |0...0> start
+    leaves at zero counts only the tiles it computes), against the rate the HBM roofline
+    allows a one-gate-per-pass schedule (each update reads and writes one amplitude)."""
     amp_bytes = S >> w.n
-    ups = 3 * w.n_gates * (1 << w.n) * grads_per_s
+    applied = (sum(len(p["gates"]) * p["active_tiles"] / p["tiles"] for p in passes) if passes
+               else w.n_gates)
+    ups = 3 * applied * (1 << w.n) * grads_per_s
     roof = hbm_peak * 1e9 / (2 * amp_bytes)
     return {"per_s": ups, "unfused_hbm_roofline_per_s": roof, "ratio_to_unfused_roofline": round(ups / roof, 3)}
 
