@@ -233,7 +233,10 @@ typedef struct vqg_plan_info {
     int32_t diag_blocks;
     int32_t specialized;  /* the specialize level in effect: 0 none, 1 forward (and
                              Hamiltonian), 2 also reverse */
-    int32_t reserved[2];
+    int32_t dense_gates;  /* gates applied by fused passes that compute every tile (the
+                             others skip tiles left at zero, vqg_plan_pass); dry run: for a
+                             |0...0> start */
+    int32_t reserved[1];
 } vqg_plan_info;
 int vqg_plan(vqg_circuit *c, vqg_plan_info *info);
 

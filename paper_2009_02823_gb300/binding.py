@@ -71,7 +71,7 @@ class vqg_plan_info(ctypes.Structure):
                 ("rev_reg_qubits", ctypes.c_int32), ("forward_stages", ctypes.c_int32),
                 ("reverse_stages", ctypes.c_int32), ("stage_ops", ctypes.c_int32),
                 ("diag_blocks", ctypes.c_int32), ("specialized", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("dense_gates", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class vqg_pass_info(ctypes.Structure):

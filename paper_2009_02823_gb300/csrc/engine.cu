@@ -151,6 +151,115 @@ static std::vector<int> choose_high(const std::vector<vqg_gate> &gates, const st
     return high;
 }
 
+// Pass choice for a |0...0> start.  A pass computes only the tiles whose non-tile index
+// bits lie inside the support (the qubits earlier gates acted on non-diagonally; see
+// FPass::n_active), so gates applied while the support is small are cheap, and the order in
+// which the tile sets visit the qubits decides how many gates run on sparse passes.  The
+// planner therefore compares candidate tile sets -- choose_high's, and every window of K - L
+// consecutive qubits above the row qubits -- by a cost model of the passes they lead to:
+// a beam search over the next passes, each sequence completed with choose_high's passes, and
+// the first tile set of the cheapest sequence taken (then searched again from the new state).
+//
+// Cost of one pass, forward plus reverse, in milliseconds of a 2^30-amplitude complex64 state
+// on the measured kernels (only ratios matter): per-gate compute and per-pass memory
+// traffic overlap (max), f = the share of tiles computed; the forward pass also writes the
+// zeros of the other tiles.
+static double pass_cost_model(int gates, double f) {
+    const double fwd = std::max(f * 2.5 + (1.0 - f) * 1.3, gates * f * 0.10) + 0.05;
+    const double rev = std::max(f * 3.8, gates * f * 0.29) + 0.05;
+    return fwd + rev;
+}
+
+namespace {
+struct PassSearch {
+    const std::vector<vqg_gate> &gates;
+    int n, K, L, cap_ops;
+    uint64_t support_of(uint64_t sup, const std::vector<int> &applied) const {
+        for (int i : applied) {
+            QUse u[2];
+            const int nu = uses_of(gates[i], u);
+            for (int k = 0; k < nu; ++k)
+                if (!u[k].diag) sup |= 1ull << u[k].q;
+        }
+        return sup;
+    }
+    uint64_t tile_mask(const std::vector<int> &high) const {
+        uint64_t m = (1ull << L) - 1ull;
+        for (int q : high) m |= 1ull << q;
+        return m;
+    }
+    // applies the pass with tile qubits `high` to (rem, sup); returns its cost
+    double step(const std::vector<int> &high, std::vector<int> &rem, uint64_t &sup, std::vector<int> &applied) const {
+        const uint64_t T = tile_mask(high);
+        std::vector<char> inS(n, 0);
+        for (int q = 0; q < n; ++q) inS[q] = (T >> q) & 1;
+        std::vector<int> left;
+        greedy(gates, rem, inS, n, cap_ops, kMaxPassSlots, applied, left);
+        const int act = __builtin_popcountll(sup & ~T);
+        const double c = pass_cost_model((int)applied.size(), std::ldexp(1.0, act - (n - K)));
+        sup = support_of(sup, applied);
+        rem.swap(left);
+        return c;
+    }
+    double finish(std::vector<int> rem, uint64_t sup) const {
+        double c = 0.0;
+        std::vector<int> applied;
+        while (!rem.empty()) {
+            c += step(choose_high(gates, rem, n, K, L), rem, sup, applied);
+            if (applied.empty()) return 1e30;  // no progress (cannot happen: the first gate fits)
+        }
+        return c;
+    }
+    std::vector<std::vector<int>> candidates(const std::vector<int> &rem) const {
+        std::vector<std::vector<int>> out{choose_high(gates, rem, n, K, L)};
+        for (int a = L; a + (K - L) <= n; ++a) {
+            std::vector<int> h;
+            for (int q = a; q < a + K - L; ++q) h.push_back(q);
+            out.push_back(h);
+        }
+        return out;
+    }
+    std::vector<int> choose(const std::vector<int> &rem0, uint64_t sup0, int width, int depth) const {
+        struct Node {
+            double cost;
+            std::vector<int> rem;
+            uint64_t sup;
+            int first;  // index of the first candidate on the way
+        };
+        const std::vector<std::vector<int>> first_cands = candidates(rem0);
+        std::vector<Node> beam{{0.0, rem0, sup0, -1}};
+        double best = 1e300;
+        int best_first = 0;
+        std::vector<int> applied;
+        for (int d = 0; d < depth && !beam.empty(); ++d) {
+            std::vector<std::pair<double, Node>> next;  // (cost with completion, node)
+            for (const Node &nd : beam) {
+                if (nd.rem.empty()) continue;
+                const std::vector<std::vector<int>> cands = d == 0 ? first_cands : candidates(nd.rem);
+                for (size_t c = 0; c < cands.size(); ++c) {
+                    Node ch{nd.cost, nd.rem, nd.sup, nd.first < 0 ? (int)c : nd.first};
+                    ch.cost += step(cands[c], ch.rem, ch.sup, applied);
+                    if (applied.empty()) continue;
+                    const double tot = ch.cost + finish(ch.rem, ch.sup);
+                    if (tot < best) best = tot, best_first = ch.first;
+                    next.push_back({tot, std::move(ch)});
+                }
+            }
+            std::stable_sort(next.begin(), next.end(),
+                             [](const std::pair<double, Node> &a, const std::pair<double, Node> &b) { return a.first < b.first; });
+            beam.clear();
+            for (auto &e : next) {
+                bool dup = false;  // same remaining gates and support: keep the cheaper
+                for (const Node &b : beam) dup = dup || (b.sup == e.second.sup && b.rem == e.second.rem);
+                if (!dup) beam.push_back(std::move(e.second));
+                if ((int)beam.size() >= width) break;
+            }
+        }
+        return first_cands[best_first];
+    }
+};
+}  // namespace
+
 // Register stages of one pass over `seq` (gates in application order).  Emits stages,
 // ops, diagonal blocks and their items into the plan; reverse stages carry reduction
 // slots.  Within a stage, diagonal gates (RZ, CZ) are gathered into diagonal blocks:
@@ -585,7 +694,7 @@ static int occupancy_grid(int num_sms, int per_sm, uint64_t n_tiles) {
 // off), nullptr with `err` set when the plan fails validation.
 Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
                         int n_gslots, bool dbl, const vqg_options &opt, std::string &err, const PassCaps &caps,
-                        bool single_kernels) {
+                        bool single_kernels, bool zero_start) {
     err.clear();
     const int G = (int)gates.size();
     const bool ff = float_float(dbl, opt);
@@ -611,8 +720,14 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
     std::vector<int> rem(G), applied, left;
     for (int i = 0; i < G; ++i) rem[i] = i;
     uint64_t support = 0;  // qubits on which a |0...0> start may have a set bit before the pass
+    // tile sets chosen for a |0...0> start (PassSearch) on single-circuit plans with more than
+    // a few tiles; the search's cost grows with gates x qubits, so large circuits search less
+    const bool search = zero_start && single_kernels && n - K >= 2;
+    const double work = (double)G * (double)n;
+    const int width = work <= 4e4 ? 12 : work <= 2e5 ? 4 : 0, depth = width ? 8 : 0;
+    const PassSearch ps{gates, n, K, L, caps.ops};
     while (!rem.empty()) {
-        std::vector<int> high = choose_high(gates, rem, n, K, L);
+        std::vector<int> high = search && width ? ps.choose(rem, support, width, depth) : choose_high(gates, rem, n, K, L);
         TileMap tm = make_tilemap(n, K, L, high);
         std::vector<char> inS(n, 0);
         for (int q = 0; q < n; ++q) inS[q] = tm.pos_of[q] >= 0;
@@ -1081,6 +1196,11 @@ void Circuit::fill_plan_info(vqg_plan_info *info) const {
     info->hamiltonian_groups = (int)ham.size();
     info->launches_per_gradient = 1 + info->forward_passes + info->hamiltonian_passes + info->reverse_passes + 2 +
                                   (fused ? 0 : 1 + nck);
+    info->dense_gates = G;
+    if (fused) {
+        info->dense_gates = 0;
+        for (const FPass &p : plan->passes) info->dense_gates += p.n_active == p.n_nontile ? p.n_gates : 0;
+    }
 }
 
 // Group Pauli terms by flip mask x (one pass over pairs (j, j^x) serves a group);
@@ -1200,6 +1320,7 @@ extern "C" int vqg_plan_dry_run(int n_qubits, const vqg_gate *gates, int n_gates
     info->stage_ops = (int)pl->ops.size();  // register-stage ops, both directions
     info->diag_blocks = fd + rd;            // diagonal blocks, both directions
     info->launches_per_gradient = 1 + 2 * info->forward_passes + info->hamiltonian_passes + 2;
+    for (const FPass &p : pl->passes) info->dense_gates += p.n_active_zero == p.n_nontile ? p.n_gates : 0;
     delete pl;
     return VQG_OK;
 }

@@ -50,10 +50,12 @@ struct Plan {
 // Plan the gate passes of one circuit (host only; nullptr + empty err: no fused
 // schedule applies; nullptr + err: the plan failed its checks).  single_kernels: the
 // (K, Rf, Rr) choice must be one the single-circuit launchers compiled; the batched
-// kernel passes false (it has its own instantiations).
+// kernel passes false (it has its own instantiations).  zero_start: the sweep usually starts
+// from |0...0>, so tile sets are chosen for the tiles that start leaves at zero (false for
+// operators applied to a dense state).
 Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<int> &slot_base,
                  int n_gslots, bool dbl, const vqg_options &opt, std::string &err,
-                 const PassCaps &caps = FullCaps::value(), bool single_kernels = true);
+                 const PassCaps &caps = FullCaps::value(), bool single_kernels = true, bool zero_start = true);
 // Hamiltonian tile passes of a plan; false if some group cannot live in one tile.
 bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham, const std::vector<PauliTerm> &host_terms);
 std::string validate_plan(const Plan &pl, int n, int n_gslots, bool dbl);

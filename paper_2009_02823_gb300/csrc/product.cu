@@ -85,7 +85,7 @@ int Circuit::build_product_plans() {
     o.rev_reg_qubits = plan->Rr;
     for (int k = 0; k < n_products; ++k) {
         std::string err;
-        Plan *pp = plan_gates(n, pg, sb, 8 * n, dbl, o, err);
+        Plan *pp = plan_gates(n, pg, sb, 8 * n, dbl, o, err, FullCaps::value(), true, false);
         if (!pp) return set_error(VQG_ERR_UNSUPPORTED, "product operator plan: %s", err.empty() ? "none" : err.c_str());
         pp->grid_fwd = plan->grid_fwd;
         pp->passes[0].from_zero = 0;  // reads psi
