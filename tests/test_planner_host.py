@@ -203,3 +203,17 @@ def test_hamiltonian_cover_restarts(n):
     assert infos[0]["hamiltonian_passes"] <= greedy
     if n == 30:
         assert (greedy, infos[0]["hamiltonian_passes"]) == (11, 10)
+
+
+def test_zero_start_search_keeps_gates_on_sparse_passes():
+    """For a |0...0> start the planner picks tile sets so that most gates run on passes that
+    compute only a few tiles: on the bench recipe at n=30 at most 160 of the 745 gates stay on
+    passes that compute every tile (the plain choice of tile qubits leaves 451 there), and
+    planning stays quick."""
+    import time
+    w = W.config(3)
+    t = time.perf_counter()
+    info = B.plan_dry_run(w.n, w.gates, w.n_params, w.terms, "c64")
+    assert time.perf_counter() - t < 5.0
+    assert 0 < info["dense_gates"] <= 160
+    assert info["forward_passes"] <= 9
