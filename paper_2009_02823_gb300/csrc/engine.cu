@@ -744,6 +744,7 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
             for (int q = 0; q < n; ++q)
                 if (tm.pos_of[q] < 0 && ((support >> q) & 1)) p.nontile[p.n_nontile++] = q;
             p.n_active_zero = p.n_active = p.n_nontile;
+            p.zero_in = p.zero_in_zero = (n >= 64 ? ~0ull : (1ull << n) - 1ull) & ~support;
             for (int q = 0; q < n; ++q)
                 if (tm.pos_of[q] < 0 && !((support >> q) & 1)) p.nontile[p.n_nontile++] = q;
             p.from_zero = pl->passes.empty() ? 1 : 0;
@@ -836,7 +837,7 @@ int Circuit::build_plan() {
         pl->grid_fwd = occupancy_grid(num_sms, 2, pl->n_tiles);
         if (has_input) {  // pass 0 reads the input state; any tile may be non-zero
             pl->passes[0].from_zero = 0;
-            for (FPass &p : pl->passes) p.n_active = p.n_nontile;
+            for (FPass &p : pl->passes) p.n_active = p.n_nontile, p.zero_in = 0;
         }
         plan = pl;
         int st;
@@ -1104,12 +1105,17 @@ int Circuit::issue_forward_fused(bool with_ckpt) {
     for (size_t j = 0; j < pl->passes.size(); ++j) {
         const int k = with_ckpt ? pl->ckpt_of_pass[j] : -1;
         void *out = k >= 0 ? ckpt_buf[k] : psi;
+        // tiles the pass skips need zeros in its output only where a reader takes the whole
+        // state: the last pass (psi) and, with diagnostics, every stored checkpoint; the next
+        // pass does not read them (FPass::zero_in)
+        const bool zero_fill = j + 1 == pl->passes.size() || diag_active;
+        const uint64_t n_tiles = zero_fill ? pl->n_tiles : std::min<uint64_t>(pl->n_tiles, 1ull << pl->passes[j].n_active);
         prof_begin(FAM_FWD_FUSED);
         if (j < pl->spec_fwd.size())
-            spec_launch_fwd(pl, (int)j, in, out, mats, stream);
+            spec_launch_fwd(pl, (int)j, in, out, mats, n_tiles, stream);
         else
             launch_fused_fwd(dbl, float_float(dbl, opt), pl->K, pl->Rf, in, out, pl->d_passes, (int)j, pl->d_stages,
-                             pl->d_ops, pl->d_diags, pl->d_items, mats, pl->n_tiles, pl->grid_fwd, stream);
+                             pl->d_ops, pl->d_diags, pl->d_items, mats, n_tiles, pl->grid_fwd, stream);
         prof_end();
         if (k >= 0)
             if (int st = diag_reduce(out, nullptr, DIAG_STORE, k)) return st;

@@ -95,6 +95,12 @@ struct FPass {
     // earlier passes never read their lambda).  n_active = n_nontile: every tile computed.
     int32_t n_active;
     int32_t n_active_zero;         // host: n_active for a |0...0> start (an input state: all)
+    // Index bits on which the pass's input is zero (qubits outside the support before the
+    // pass, for a |0...0> start; 0 with an input state): the forward pass reads an input
+    // amplitude only where its index has none of these bits and takes zero elsewhere, so the
+    // passes before it need not write the zeros of the tiles they skip.
+    uint64_t zero_in;
+    uint64_t zero_in_zero;         // host: zero_in for a |0...0> start
 };
 
 struct FStage {

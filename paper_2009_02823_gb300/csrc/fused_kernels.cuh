@@ -735,18 +735,23 @@ struct TileIO {
     };
 
     // L2ONLY: bypass L1 (needed when another block of the same launch wrote the data).
+    // zmask: index bits on which the source is known to be zero (FPass::zero_in): such
+    // amplitudes are not read (the memory there need not hold zeros) and enter as zero.
     template <int NT, bool L2ONLY = false>
     static VQG_DEV void load(amp_t<T> *tile, const amp_t<T> *__restrict__ src, uint64_t base,
-                             const uint64_t *row_off, int tid) {
+                             const uint64_t *row_off, int tid, uint64_t zmask = 0) {
         using G = Geo<NT>;
         const int row0 = tid / CPR, col = tid % CPR;
         const uint32_t s0 = swz<AB>((uint32_t)(row0 << L) | (uint32_t)(col * CA));
-        const amp_t<T> *g0 = src + ((base | row_off[row0]) + col * CA);
+        const uint64_t o0 = (base | row_off[row0]) + col * CA;
+        const amp_t<T> *g0 = src + o0;
         float4 v[G::CPT];  // every global load in flight before the first shared store
 #pragma unroll
         for (int i = 0; i < G::CPT; ++i) {
             const float4 *g = reinterpret_cast<const float4 *>(g0 + row_off[G::RSTEP * i]);
-            v[i] = L2ONLY ? __ldcg(g) : __ldcs(g);
+            if ((o0 | row_off[G::RSTEP * i]) & zmask) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            else v[i] = L2ONLY ? __ldcg(g) : __ldcs(g);
+            if (CA == 2 && (zmask & 1ull)) v[i].z = v[i].w = 0.f;  // the chunk's odd amplitude
         }
 #pragma unroll
         for (int i = 0; i < G::CPT; ++i) put_chunk(tile, s0 ^ swz<AB>((uint32_t)i << G::SHI), v[i]);
@@ -778,8 +783,10 @@ struct TileIO {
     // Ask L2 for the rows of a tile (one 128-byte row = one L2 line per request) one tile
     // ahead of its load: the load then hits L2 instead of waiting on HBM.
     template <int NT>
-    static VQG_DEV void prefetch(const amp_t<T> *src, uint64_t base, const uint64_t *row_off, int tid) {
+    static VQG_DEV void prefetch(const amp_t<T> *src, uint64_t base, const uint64_t *row_off, int tid,
+                                 uint64_t zmask = 0) {
         for (int r = tid; r < ROWS; r += NT) {
+            if ((base | row_off[r]) & zmask & ~(uint64_t)((1 << L) - 1)) continue;  // a row known zero
             const amp_t<T> *p = src + (base | row_off[r]);
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
         }
@@ -915,12 +922,12 @@ VQG_DEV uint32_t reg_addr(uint32_t sb, const uint32_t (&w)[R], int j) {
 template <typename T, int K, int R, bool L2ONLY>
 VQG_DEV void fwd_tile(amp_t<T> *tile, const uint64_t *row_off, const Prog<T, R> &pg, int n_stage,
                       uint64_t base, bool from_zero, const amp_t<T> *__restrict__ src,
-                      amp_t<T> *__restrict__ dst, int tid) {
+                      amp_t<T> *__restrict__ dst, int tid, uint64_t zmask = 0) {
     using A = amp_t<T>;
     using IO = TileIO<T, K>;
     constexpr int AB = FT<T>::AB, NT = 1 << (K - R), NA = 1 << R;
     if (from_zero) IO::template zero<NT>(tile, base, tid);
-    else IO::template load<NT, L2ONLY>(tile, src, base, row_off, tid);
+    else IO::template load<NT, L2ONLY>(tile, src, base, row_off, tid, zmask);
     __syncthreads();
     for (int s = 0; s < n_stage; ++s) {
         const FStage &st = pg.st[s];
@@ -1315,9 +1322,10 @@ __global__ void __launch_bounds__(1 << (K - R), (1 << (K - R)) >= 512 ? 1 : 2)
             continue;
         }
         if (ti + gridDim.x < n_act && !P.from_zero)
-            TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid);
+            TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid,
+                                                P.zero_in);
         fwd_tile<T, K, R, false>(tile, row_off, pg, P.n_stage, tile_base(ti, P.nontile, P.n_nontile),
-                                 P.from_zero != 0, src, dst, tid);
+                                 P.from_zero != 0, src, dst, tid, P.zero_in);
     }
 }
 
@@ -1824,8 +1832,10 @@ VQG_DEV void fwd_pass_spec(const amp_t<T> *__restrict__ src, amp_t<T> *__restric
             continue;
         }
         if (ti + gridDim.x < n_act && !P.from_zero)
-            TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid);
-        Body::tile(tile, row_off, pg, tile_base(ti, P.nontile, P.n_nontile), P.from_zero != 0, src, dst, tid);
+            TileIO<T, K>::template prefetch<NT>(src, tile_base(ti + gridDim.x, P.nontile, P.n_nontile), row_off, tid,
+                                                P.zero_in);
+        Body::tile(tile, row_off, pg, tile_base(ti, P.nontile, P.n_nontile), P.from_zero != 0, src, dst, tid,
+                   P.zero_in);
     }
 }
 
@@ -1932,13 +1942,14 @@ VQG_DEV void rev_scatter_global(uint64_t gb, const uint64_t (&gm)[1 << R], bool 
 }
 template <int R>
 VQG_DEV void fwd_gather_global(uint64_t gb, const uint64_t (&gm)[1 << R], bool from_zero,
-                               const float2 *__restrict__ src, float2 (&a)[1 << R]) {
+                               const float2 *__restrict__ src, float2 (&a)[1 << R], uint64_t zmask) {
     if (from_zero) {  // |0...0>
 #pragma unroll
         for (int j = 0; j < (1 << R); ++j) a[j] = make_float2((gb | gm[j]) == 0 ? 1.f : 0.f, 0.f);
-    } else {
+    } else {  // amplitudes known zero (FPass::zero_in) are not read
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) a[j] = __ldcs(src + (gb | gm[j]));
+        for (int j = 0; j < (1 << R); ++j)
+            a[j] = ((gb | gm[j]) & zmask) ? make_float2(0.f, 0.f) : __ldcs(src + (gb | gm[j]));
     }
 }
 template <int R>

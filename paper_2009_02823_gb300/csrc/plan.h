@@ -74,7 +74,8 @@ int spec_compile(const Plan *pl, bool with_rev, std::vector<std::string> &cubins
 int spec_build(Plan *pl, bool with_rev);
 int spec_build_ham(Plan *pl);
 int spec_launch_ham(const Plan *pl, int h, const void *psi, void *lam, double *partials, int nb, cudaStream_t s);
-int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const void *mats, cudaStream_t s);
+int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const void *mats, uint64_t n_tiles,
+                    cudaStream_t s);
 int spec_launch_rev(const Plan *pl, int j, const void *phi_src, void *phi_dst, void *lam, const void *mats,
                     double *partials, int nb, int wmask, uint64_t n_tiles, cudaStream_t s);
 

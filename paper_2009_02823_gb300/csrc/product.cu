@@ -89,7 +89,7 @@ int Circuit::build_product_plans() {
         if (!pp) return set_error(VQG_ERR_UNSUPPORTED, "product operator plan: %s", err.empty() ? "none" : err.c_str());
         pp->grid_fwd = plan->grid_fwd;
         pp->passes[0].from_zero = 0;  // reads psi
-        for (FPass &p : pp->passes) p.n_active = p.n_nontile;  // a dense input: every tile
+        for (FPass &p : pp->passes) p.n_active = p.n_nontile, p.zero_in = 0;  // a dense input: every tile
         prod_plans.push_back(pp);
         int st = upload_plan(pp);
         if (st) return st;
@@ -185,7 +185,10 @@ int Circuit::set_input(const void *state, bool on_device) {
     }
     if (plan && !plan->passes.empty()) {  // pass 0: synthesise |0...0> or read the input
         plan->passes[0].from_zero = has_input ? 0 : 1;
-        for (FPass &p : plan->passes) p.n_active = has_input ? p.n_nontile : p.n_active_zero;
+        for (FPass &p : plan->passes) {
+            p.n_active = has_input ? p.n_nontile : p.n_active_zero;
+            p.zero_in = has_input ? 0 : p.zero_in_zero;
+        }
         if (h2d(plan->d_passes, plan->passes.data(), sizeof(FPass) * plan->passes.size()) != cudaSuccess)
             return set_error(VQG_ERR_CUDA, "plan update failed");
     }

@@ -132,7 +132,8 @@ std::string gen_fwd(const Plan &pl, int pass) {
       << "namespace vqg { namespace spec {\n"
       << "struct Body {\n"
       << "  static VQG_DEV void tile(float2 *tile, const uint64_t *row_off, const Prog<float, " << R
-      << "> &pg, uint64_t base, bool from_zero, const float2 *__restrict__ src, float2 *__restrict__ dst, int tid) {\n"
+      << "> &pg, uint64_t base, bool from_zero, const float2 *__restrict__ src, float2 *__restrict__ dst, int tid, "
+         "uint64_t zin) {\n"
       << "    using T = float; using A = float2; using IO = TileIO<T, " << K << ">;\n"
       << "    constexpr int NT = " << NT << ", NA = " << (1 << R) << "; (void)NA;\n"
       << "    (void)row_off; (void)IO{};\n";
@@ -140,7 +141,7 @@ std::string gen_fwd(const Plan &pl, int pass) {
     const bool dlast = P.n_stage > 0 && direct_io(pl, P.stage0 + P.n_stage - 1, R);
     if (!dfirst)
         o << "    if (from_zero) IO::template zero<NT>(tile, base, tid);\n"
-          << "    else IO::template load<NT, false>(tile, src, base, row_off, tid);\n"
+          << "    else IO::template load<NT, false>(tile, src, base, row_off, tid, zin);\n"
           << "    __syncthreads();\n";
     for (int s = 0; s < P.n_stage; ++s) {
         const FStage &st = pl.stages[P.stage0 + s];
@@ -149,7 +150,7 @@ std::string gen_fwd(const Plan &pl, int pass) {
           << "      StageGeo<T, " << K << ", " << R << "> g; g.init(pg.st[" << s << "], tid, base);\n"
           << "      const uint64_t gb = g.gb; (void)gb;\n";
         if (first || last) o << "      " << gm_decl(pl, P.stage0 + s, R) << "\n";
-        if (first) o << "      A a[NA]; fwd_gather_global<" << R << ">(gb, gm, from_zero, src, a);\n";
+        if (first) o << "      A a[NA]; fwd_gather_global<" << R << ">(gb, gm, from_zero, src, a, zin);\n";
         else o << "      A a[NA]; fwd_gather<T, " << K << ", " << R << ">(g, tile, a);\n";
         o << "      A phase = mk<T>((T)1, (T)0); T kacc = (T)1;\n";
         for (int i = 0; i < st.n_op; ++i) {
@@ -780,7 +781,8 @@ int spec_build(Plan *pl, bool with_rev) {
     return VQG_OK;
 }
 
-int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const void *mats, cudaStream_t s) {
+int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const void *mats, uint64_t n_tiles,
+                    cudaStream_t s) {
     const float2 *a0 = (const float2 *)src;
     float2 *a1 = (float2 *)dst;
     const FPass *a2 = pl->d_passes;
@@ -790,7 +792,7 @@ int spec_launch_fwd(const Plan *pl, int j, const void *src, void *dst, const voi
     const FDiag *a6 = pl->d_diags;
     const FDItem *a7 = pl->d_items;
     const float *a8 = (const float *)mats;
-    uint64_t a9 = pl->n_tiles;
+    uint64_t a9 = n_tiles;
     void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9};
     return cudaLaunchKernel((const void *)pl->spec_fwd[j], dim3(pl->grid_fwd), dim3(1 << (pl->K - pl->Rf)), args,
                             pl->spec_smem_fwd, s) == cudaSuccess ? VQG_OK : VQG_ERR_CUDA;

@@ -1,7 +1,8 @@
 """Tiles that a |0...0> start leaves at zero (vqg_plan_pass): the planner's active-tile
 counts against a support computed here from the gate list, and the results with and
-without the skipping (an input state |0...0> given explicitly turns it off) against each
-other and the CPU oracle (Algorithm 1, Sec. 2.3)."""
+without the skipping (an input state |0...0> given explicitly turns it off; clearing it
+turns it back on, with forward passes that neither write nor read those zeros) against
+each other and the CPU oracle (Algorithm 1, Sec. 2.3)."""
 import numpy as np
 import pytest
 
@@ -54,10 +55,15 @@ def test_active_tiles_follow_the_support(n, K, spec):
         e2, g2 = c.energy_and_gradient(w.theta)
         c.energy(w.theta)
         psi2 = c.get_state()
+        # back to the |0...0> start: the skipping (and the unread zeros) come back
+        c.set_input_state(None)
+        assert c.plan_passes()[0]["active_tiles"] == 1
+        e3, g3 = c.energy_and_gradient(w.theta)
     e_ref, g_ref = oracle.gradient_alg1(w.n, w.gates, w.theta, w.n_params, w.terms)
     assert_parity("c64", e, g, e_ref, g_ref, w.name)
     assert abs(e - e2) <= 1e-6 * max(1.0, abs(e)) and np.max(np.abs(g - g2)) <= 1e-6 * np.max(np.abs(g))
     assert np.max(np.abs(psi - psi2)) <= 1e-6
+    assert e3 == e and np.array_equal(g3, g)
 
 
 def test_active_tiles_complex128():
