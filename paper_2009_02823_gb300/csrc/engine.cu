@@ -162,10 +162,10 @@ static std::vector<int> choose_high(const std::vector<vqg_gate> &gates, const st
 //
 // Cost of one pass, forward plus reverse, in milliseconds of a 2^30-amplitude complex64 state
 // on the measured kernels (only ratios matter): per-gate compute and per-pass memory
-// traffic overlap (max), f = the share of tiles computed; the forward pass also writes the
-// zeros of the other tiles.
+// traffic overlap (max), f = the share of tiles computed (skipped tiles are neither read nor
+// written, FPass::zero_in).
 static double pass_cost_model(int gates, double f) {
-    const double fwd = std::max(f * 2.5 + (1.0 - f) * 1.3, gates * f * 0.10) + 0.05;
+    const double fwd = std::max(f * 2.5, gates * f * 0.10) + 0.05;
     const double rev = std::max(f * 3.8, gates * f * 0.29) + 0.05;
     return fwd + rev;
 }
