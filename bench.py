@@ -168,8 +168,8 @@ def alu_peak(sm_mhz: float | None, n_sm: int = 152) -> tuple[float, str]:
 def family_bytes(fam: str, w, S: int, plan: dict, passes=None) -> float | None:
     """Algorithmic bytes per launch of a kernel family (one state traversal = S bytes
     read or written; Algorithm 1's cost unit, one gate primitive = O(2^n)).  Fused passes
-    count the tiles they compute (passes: vqg_plan_pass entries); a forward pass also writes
-    the zeros of the tiles it skips."""
+    count the tiles they compute (passes: vqg_plan_pass entries); the last forward pass also
+    writes the zeros of the tiles it skips."""
     if fam == "adj_gate":    # read phi, lambda; write phi, lambda
         return 4.0 * S
     if fam == "fwd_gate":    # read + write psi (CNOT/CZ touch part of it; counted whole)
@@ -188,7 +188,13 @@ def family_bytes(fam: str, w, S: int, plan: dict, passes=None) -> float | None:
     if fam == "fwd_fused":   # per forward tile pass: read + write psi
         if not passes:
             return 2.0 * S
-        return sum((0.0 if p["from_zero"] else p["active_tiles"] / p["tiles"]) * S + S for p in passes) / len(passes)
+        # computed tiles are read (at most: amplitudes known zero are skipped) and written;
+        # the last pass also writes the zeros of the tiles it skips
+        tot = 0.0
+        for j, p in enumerate(passes):
+            f = p["active_tiles"] / p["tiles"]
+            tot += (0.0 if p["from_zero"] else f * S) + (S if j + 1 == len(passes) else f * S)
+        return tot / len(passes)
     if fam == "ham_group":   # read psi, read + write lambda
         return 3.0 * S
     if fam == "ham_diag":    # read psi, write lambda
