@@ -147,11 +147,22 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             load_prog<T, R>(pg, P.stage0, P.n_stage, P.diag0, P.n_diag, a.stages, a.ops, a.diags, a.items,
                             a.mats, false, tid, kBNT);
             __syncthreads();
+            // tiles a |0...0> start leaves at zero (FPass::n_active) are skipped; only the last
+            // pass writes their zeros (the Hamiltonian reads the whole state), the others'
+            // inputs are not read there (FPass::zero_in)
+            const int n_act = (int)min((unsigned long long)C.n_tiles, 1ull << P.n_active);
+            const bool last = tk.phase == F - 1;
             for (int ti = t0; ti < t1; ++ti) {
-                if (ti + 1 < t1 && !P.from_zero)
-                    TileIO<T, K>::template prefetch<kBNT>(psi, tile_base(ti + 1, P.nontile, P.n_nontile), row_off, tid);
+                if (ti >= n_act) {
+                    if (last)
+                        TileIO<T, K>::template store_zero<kBNT>(psi, tile_base(ti, P.nontile, P.n_nontile), row_off, tid);
+                    continue;
+                }
+                if (ti + 1 < min(t1, n_act) && !P.from_zero)
+                    TileIO<T, K>::template prefetch<kBNT>(psi, tile_base(ti + 1, P.nontile, P.n_nontile), row_off, tid,
+                                                          P.zero_in);
                 fwd_tile<T, K, R, true>(tile, row_off, pg, P.n_stage, tile_base(ti, P.nontile, P.n_nontile),
-                                        P.from_zero != 0, psi, psi, tid);
+                                        P.from_zero != 0, psi, psi, tid, P.zero_in);
             }
         } else if (ok && tk.phase < F + H) {  // Hamiltonian pass
             const HPass &P = a.hp[C.hpass0 + tk.phase - F];
@@ -197,8 +208,10 @@ __global__ void __launch_bounds__(kBNT) k_batch(BatchArgs a) {
             load_prog<T, R>(pg, P.rstage0, P.n_rstage, P.rdiag0, P.n_rdiag, a.stages, a.ops, a.diags, a.items,
                             a.mats, true, tid, kBNT);
             __syncthreads();
-            for (int ti = t0; ti < t1; ++ti) {
-                if (ti + 1 < t1) {
+            // only the tiles that can hold amplitude (FPass::n_active)
+            const int t1a = min(t1, (int)min((unsigned long long)C.n_tiles, 1ull << P.n_active));
+            for (int ti = t0; ti < t1a; ++ti) {
+                if (ti + 1 < t1a) {
                     const uint64_t next = tile_base(ti + 1, P.nontile, P.n_nontile);
                     TileIO<T, K>::template prefetch<kBNT>(psi, next, row_off, tid);
                     TileIO<T, K>::template prefetch<kBNT>(lam, next, row_off, tid);
