@@ -938,7 +938,15 @@ bool plan_hamiltonian(Plan *pl, int n, const std::vector<HamGroup> &ham,
             if (c.size() < cover.size()) cover.swap(c);
         }
     }
-    // the diagonal group (x = 0) is group 0 (ordered map) and goes in the first pass
+    // The first pass writes lambda instead of adding to it (it reads 16 bytes per amplitude,
+    // the others 24): lead with the pass with the fewest groups, whose time is the memory
+    // traffic, rather than a shared-memory-bound one that would not get faster.
+    if (!cover.empty()) {
+        size_t lightest = 0;
+        for (size_t i = 1; i < cover.size(); ++i)
+            if (cover[i].second.size() < cover[lightest].second.size()) lightest = i;
+        std::rotate(cover.begin(), cover.begin() + lightest, cover.begin() + lightest + 1);
+    }
     bool first = true;
     for (const auto &pass : cover) {
         uint64_t S = pass.first;
