@@ -720,11 +720,13 @@ Plan *plan_gates(int n, const std::vector<vqg_gate> &gates, const std::vector<in
     std::vector<int> rem(G), applied, left;
     for (int i = 0; i < G; ++i) rem[i] = i;
     uint64_t support = 0;  // qubits on which a |0...0> start may have a set bit before the pass
-    // tile sets chosen for a |0...0> start (PassSearch) on single-circuit plans with more than
-    // a few tiles; the search's cost grows with gates x qubits, so large circuits search less
-    const bool search = zero_start && single_kernels && n - K >= 2;
+    // tile sets chosen for a |0...0> start (PassSearch) on plans with more than a few tiles;
+    // the search's cost grows with gates x qubits, so large circuits search less, and the
+    // batched launch (hundreds of circuits planned at once) searches narrowly
+    const bool search = zero_start && n - K >= 2;
     const double work = (double)G * (double)n;
-    const int width = work <= 4e4 ? 12 : work <= 2e5 ? 4 : 0, depth = width ? 8 : 0;
+    const int width = !single_kernels ? 2 : work <= 4e4 ? 12 : work <= 2e5 ? 4 : 0;
+    const int depth = !single_kernels ? 3 : width ? 8 : 0;
     const PassSearch ps{gates, n, K, L, caps.ops};
     while (!rem.empty()) {
         std::vector<int> high = search && width ? ps.choose(rem, support, width, depth) : choose_high(gates, rem, n, K, L);
